@@ -1,0 +1,216 @@
+/*
+ * pff.h -- C-ABI of the GB300 (sm_103a) phase-field fracture library (libpff.so).
+ *
+ * Computes, on one GPU, the hot path of the matrix-free monolithic multigrid solver of
+ * Jodlbauer, Langer, Wick, "Parallel matrix-free higher-order finite element solvers for
+ * phase-field fracture problems": the residual of Eq. (residual), the Jacobian of Eq. (G)
+ * applied matrix-free by sum factorisation (Sec. 3.4), the primal-dual active-set step of
+ * Alg. 1, and the geometric-multigrid preconditioner of Sec. 3.3 (block-diagonal
+ * Chebyshev-Jacobi smoother, nested-mesh transfers, coarse solve) inside flexible GMRES.
+ *
+ * Discretisation. Unit square (dim 2) or cube (dim 3), N^dim cells of edge h = 1/N, Q_p
+ * Lagrange elements on Gauss-Lobatto-Legendre nodes, (p+1)^dim Gauss points per cell.
+ * Nodes are numbered lexicographically over (pN+1)^dim points, x fastest. A global vector
+ * ("DoF vector") is component blocked: [u_1 | ... | u_dim | phi], n_nodes values per block,
+ * n_dofs = (dim+1) n_nodes. Boundary data of the single-edge notched tension test (Sec. 5.1):
+ * every displacement component is fixed on the bottom and top faces (last coordinate 0 and 1).
+ *
+ * Conventions of every entry point:
+ *  - Pointers to vectors are DEVICE pointers owned by the caller, contiguous, in the DoF
+ *    layout above (or one value per node where stated). The library never frees them.
+ *  - Work is enqueued on the CUDA stream passed to pff_setup_mesh and is asynchronous with
+ *    respect to the host unless stated otherwise.
+ *  - The return value is PFF_OK (0) or a negative PFF_ERR_* code; pff_strerror() names it.
+ *    No C++ exception crosses this interface. After PFF_ERR_CUDA the context must be destroyed.
+ *  - The context is not thread safe: one host thread per context.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFF_OK 0
+#define PFF_ERR_INVALID_ARG (-1)   /* bad size, degree, pointer or mode */
+#define PFF_ERR_OOM (-2)           /* device allocation failed */
+#define PFF_ERR_CUDA (-3)          /* a CUDA runtime call or kernel launch failed */
+#define PFF_ERR_NAN (-4)           /* a non-finite value appeared in a norm */
+#define PFF_ERR_NOT_CONVERGED (-5) /* FGMRES reached its iteration cap */
+#define PFF_ERR_BREAKDOWN (-6)     /* Krylov breakdown (zero norm before convergence) */
+#define PFF_ERR_NO_STATE (-7)      /* pff_set_state has not been called */
+
+/* Splits of the elastic energy (Sec. 2.1): none = isotropic model, miehe = spectral split. */
+#define PFF_SPLIT_NONE 0
+#define PFF_SPLIT_MIEHE 1
+
+/* Jacobian modes (low two bits of `mode`). */
+#define PFF_MODE_FULL 0       /* G of Eq. (G) */
+#define PFF_MODE_BLOCKDIAG 1  /* diag(G_uu, G_phiphi): coupling block G_phiu dropped (Sec. 3.3 smoother) */
+#define PFF_MODE_TRANSPOSE 2  /* G^T */
+/* Masking flags (OR-ed into `mode`). Default: rows and columns of Dirichlet DoFs and of the
+ * active set are replaced by the identity (x is zeroed there on input, y = x there on output). */
+#define PFF_MASK_RAW 4        /* no masking at all: the plain sum over cells of Sec. 3.4 */
+#define PFF_MASK_ADJOINT 8    /* x zeroed on Dirichlet DoFs only, output unmasked: d(R)/dU^T v
+                                 for the residual of pff_residual (whose Dirichlet rows are 0) */
+
+/* Node flag bits returned by pff_node_flags. */
+#define PFF_FLAG_FIXED(c) (1u << (c))  /* field c masked: c < dim Dirichlet; c == dim active phi */
+#define PFF_FLAG_TOP 0x10u            /* node on the top face */
+#define PFF_FLAG_BOTTOM 0x20u         /* node on the bottom face */
+#define PFF_FLAG_SLIT 0x40u           /* node on the slit / notch (last coord 1/2, x <= 1/2) */
+
+typedef struct pff_ctx pff_ctx; /* opaque: mesh hierarchy, states, per-point data, workspaces */
+
+typedef struct {
+  int dim;            /* 2 or 3 */
+  int degree;         /* p = 1..4 */
+  int n_cells_1d;     /* N >= 1 cells per direction on the finest mesh */
+  int coarse_min;     /* levels halve N while N is even and N/2 >= coarse_min (default 3) */
+  int split;          /* PFF_SPLIT_NONE or PFF_SPLIT_MIEHE */
+  double lambda, mu;  /* Lame parameters (used where no nodal field is given) */
+  double gc;          /* critical energy release rate G_c (used where no nodal field is given) */
+  double eps;         /* phase-field length scale epsilon */
+  double kappa;       /* degradation regularisation: g(phi) = (1 - kappa) phi^2 + kappa */
+  double as_c;        /* constant c of the active-set rule of Alg. 1 (default 1) */
+  int mg_precision;   /* 64: FP64 multigrid; 32: FP32 levels, smoothers, transfers (coarse solve FP64) */
+  int cheb_degree;    /* Chebyshev-Jacobi smoother degree (paper: 5) */
+  double cheb_lo;     /* smoothing interval [cheb_lo, cheb_hi] * lambda_max (paper: 0.24, 1.2) */
+  double cheb_hi;
+  int eig_iters;      /* CG-Lanczos iterations for lambda_max (default 15) */
+  unsigned long long eig_seed; /* SplitMix64 seed of the CG start vector */
+  int gmres_restart;  /* FGMRES restart length (default 50) */
+  int gmres_max_iters;/* FGMRES iteration cap per linear solve (default 500) */
+  double lin_rtol;    /* FGMRES relative tolerance (paper: 1e-6) */
+} pff_params;
+
+typedef struct {
+  double res_norm;       /* ||R~||: residual with Dirichlet and active rows zeroed, before the update */
+  double gmres_rel;      /* final relative residual of the linear solve */
+  int gmres_iters;       /* FGMRES iterations */
+  int n_active;          /* |A_k| */
+  int n_changed;         /* phase-field DoFs whose active flag changed against A_{k-1} */
+  int status;            /* PFF_OK or the error of the linear solve */
+  double t_residual_ms, t_setup_ms, t_solve_ms; /* host wall time of the phases */
+} pff_report;
+
+/* Defaults: the paper's tension test (lambda 121.15, mu 80.77, G_c 2.7e-3, kappa 1e-10), split none,
+ * dim 2, p 1, N 32, eps 2/N, c 1, FP32 multigrid, Chebyshev degree 5 on [0.24, 1.2] lambda_max,
+ * 15 eigen iterations, restart 50, relative tolerance 1e-6 (Sec. 5.1, Sec. 6.2). Never fails. */
+void pff_default_params(pff_params* p);
+
+/* Builds the mesh hierarchy and allocates per-level storage (Sec. 3.3 nested meshes).
+ * `stream` is a cudaStream_t (NULL = legacy default stream). On success *out owns the context.
+ * Errors: INVALID_ARG (dim, degree, N, tolerances out of range), OOM, CUDA. */
+int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream);
+
+/* Frees everything the context owns (synchronises its stream first). NULL is allowed. */
+void pff_destroy(pff_ctx* ctx);
+
+/* Sizes of level 0 (finest) and the number of levels. Host pointers, any may be NULL. */
+int pff_sizes(const pff_ctx* ctx, long long* n_dofs, long long* n_nodes, int* n_levels);
+
+/* Sizes of level `level` (0 = finest): nodes and cells per direction. Host pointers. */
+int pff_level_sizes(const pff_ctx* ctx, int level, long long* n_nodes, int* n_cells_1d);
+
+/* Per-node flags of the finest mesh (PFF_FLAG_*), one byte per node, device pointer. The
+ * active bit reflects the active set of the last pff_set_state / Newton step. */
+int pff_node_flags(pff_ctx* ctx, int level, unsigned char* flags);
+
+/* Sets the Newton state (Alg. 1, Eq. (residual)):
+ *   U        DoF vector [u | phi] with the Dirichlet values already lifted in (required);
+ *   phi_old  previous load step's phase field, one per node (required): bound phi <= phi_old;
+ *   phi_tilde extrapolated phase field used in g(phi~) of the u-equation (NULL: phi_old);
+ *   active   one byte per node, nonzero = phase-field DoF in the active set A (NULL: the set is
+ *            computed by the rule of Alg. 1 from the residual at U and phi is reset to phi_old on it);
+ *   gc_field, lambda_field, mu_field: nodal material fields (NULL: the constants of the params).
+ * Copies every input. Computes the per-quadrature-point tangent data of the finest level in FP64
+ * (and FP32 when mg_precision is 32). Multigrid level data are built lazily by the first
+ * pff_vcycle / pff_solve_newton_step after it. Errors: NO_STATE never; INVALID_ARG on NULL U/phi_old. */
+int pff_set_state(pff_ctx* ctx, const double* U, const double* phi_old, const double* phi_tilde,
+                  const unsigned char* active, const double* gc_field, const double* lambda_field,
+                  const double* mu_field);
+
+/* Current Newton state U (DoF vector) into `U_out` (device). */
+int pff_get_state(pff_ctx* ctx, double* U_out);
+
+/* Active set of the current state, one byte per node (1 = active), device pointer. */
+int pff_get_active(pff_ctx* ctx, unsigned char* active_out);
+
+/* y = G x on level `level` (0 = finest) with G of Eq. (G) at the current state, matrix free
+ * (Sec. 3.4). precision 64: x, y are double*; 32: float* (tangent data rounded to FP32, FP32
+ * accumulation). mode: PFF_MODE_* | PFF_MASK_* (see above). x and y must not alias.
+ * Level > 0 builds the multigrid data first if needed. Errors: NO_STATE, INVALID_ARG. */
+int pff_apply_jacobian(pff_ctx* ctx, int level, const void* x, void* y, int precision, int mode);
+
+/* r = R(U) of Eq. (residual) at the current state, FP64, rows of Dirichlet DoFs set to 0. */
+int pff_residual(pff_ctx* ctx, double* r);
+
+/* Diagonal of the masked block-diagonal operator diag(G_uu, G_phiphi) on `level` (masked rows 1),
+ * the Jacobi scaling of the smoother (Sec. 3.3). precision 64 or 32. */
+int pff_diagonal(pff_ctx* ctx, int level, void* diag, int precision);
+
+/* lambda_max estimates of D^{-1} G_uu and D^{-1} G_phiphi on `level` (host double[2]). */
+int pff_lambda_max(pff_ctx* ctx, int level, double* lam2);
+
+/* Multigrid state of `level`: the Newton state carried to that mesh (DoF vector of the level). */
+int pff_level_state(pff_ctx* ctx, int level, double* U_level);
+
+/* Prolongation from level+1 (coarse) to level (fine): y_fine = Z P x_coarse, Z zeroing masked
+ * fine rows. Restriction: y_coarse = Z_c P^T x_fine (transpose, masked coarse rows zeroed).
+ * precision 64 or 32, vectors in the layout of their level. */
+int pff_prolongate(pff_ctx* ctx, int level, const void* x_coarse, void* y_fine, int precision);
+int pff_restrict(pff_ctx* ctx, int level, const void* x_fine, void* y_coarse, int precision);
+
+/* One application of the block-diagonal Chebyshev-Jacobi smoother on `level` with zero initial
+ * guess: x = S(G_uu, G_phiphi) f (Sec. 3.3). */
+int pff_smooth(pff_ctx* ctx, int level, const void* f, void* x, int precision);
+
+/* Coarse-level solve (FP64): z = G_c^{-1} r by block forward substitution over the block lower
+ * triangular coarse matrix (Sec. 3.3), r and z in the coarsest level's layout. */
+int pff_coarse_solve(pff_ctx* ctx, const double* r, double* z);
+
+/* One V-cycle of GMG(G) (Sec. 3.3) on the finest level: z = M^{-1} r, FP64 in and out; inside it
+ * runs in the params' mg_precision. */
+int pff_vcycle(pff_ctx* ctx, const double* r, double* z);
+
+/* Solves G dU = b by right-preconditioned flexible GMRES with the V-cycle (FP64 outer). Host
+ * pointers iters/rel may be NULL. Synchronises the stream once per iteration. */
+int pff_solve_linear(pff_ctx* ctx, const double* b, double* x, int* iters, double* rel);
+
+/* One primal-dual active-set iteration (Alg. 1) from the current state: residual, active set,
+ * reset phi to phi_old on it, level setup, FGMRES + GMG solve of G dU = -R on the inactive DoFs,
+ * update U += dU. The context's state becomes the new iterate; it is also copied to U_out when
+ * non-NULL. `rep` (host, may be NULL) receives the report. Synchronous. */
+int pff_solve_newton_step(pff_ctx* ctx, double* U_out, pff_report* rep);
+
+/* Parameter gradients of the residual (not in the paper; needed for adjoints): for a test vector v
+ * (DoF layout), g_gc = (dR/dG_c)^T v, g_lambda = (dR/dlambda)^T v, g_mu = (dR/dmu)^T v with the
+ * material parameters as nodal fields, one value per node each, at the current state. Entries of v
+ * on Dirichlet DoFs are ignored (those rows of the residual are zero). Any output may be NULL;
+ * outputs are overwritten. */
+int pff_param_grad(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda, double* g_mu);
+
+/* Device timing of one kernel family with CUDA events recorded on the context's stream around
+ * each launch of that family (for throughput and roofline figures; off by default):
+ *   PFF_PROF_OFF, PFF_PROF_JAC64_L0 / PFF_PROF_JAC32_L0 (FP64 / FP32 Jacobian kernels on the finest
+ *   level, any mode), PFF_PROF_JAC64 / PFF_PROF_JAC32 (any level), PFF_PROF_RESIDUAL.
+ * pff_profile resets the counters; pff_profile_result synchronises the stream and returns the
+ * number of timed launches and their summed device time in milliseconds (at most 16384 launches
+ * are timed; later ones are not). */
+#define PFF_PROF_OFF 0
+#define PFF_PROF_JAC64_L0 1
+#define PFF_PROF_JAC32_L0 2
+#define PFF_PROF_JAC64 3
+#define PFF_PROF_JAC32 4
+#define PFF_PROF_RESIDUAL 5
+int pff_profile(pff_ctx* ctx, int family);
+int pff_profile_result(pff_ctx* ctx, int* launches, double* total_ms);
+
+/* Human-readable name of a status code. */
+const char* pff_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_H */

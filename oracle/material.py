@@ -17,11 +17,16 @@ Readings taken where the paper is silent or garbled (all documented in the desig
   Theta_ij = H(l_i) for l_i == l_j, with H(x) = 1 for x >= 0 (Alg. 2 takes d lambda^+ = d lambda at
   lambda = 0). ``alg2_dplus`` is Alg. 2 itself; the tests check both agree for distinct eigenvalues.
 * The trace switch of d sigma^+ uses tr(e) < 0 -> 0, else 1 (as printed).
+* Eigenvalues and the trace whose magnitude is at most ZERO_TOL times the largest eigenvalue
+  magnitude are taken as exactly 0 before any switch or positive part is evaluated: where a strain
+  component is rounding noise (e.g. a displacement constant along a direction), the sign of such an
+  eigenvalue is noise and would flip H and the tangent.
 """
 import numpy as np
 
 SPLIT_NONE = 0
 SPLIT_MIEHE = 1
+ZERO_TOL = 1e-12
 
 
 def g(phi, kappa):
@@ -54,9 +59,23 @@ def eye_like(a):
     return np.broadcast_to(np.eye(d), a.shape)
 
 
+def eig_snapped(e):
+    """numpy.linalg.eigh with eigenvalues of magnitude <= ZERO_TOL * max|lambda| set to 0."""
+    lam, V = np.linalg.eigh(e)
+    scale = np.max(np.abs(lam), axis=-1, keepdims=True)
+    return np.where(np.abs(lam) <= ZERO_TOL * scale, 0.0, lam), V
+
+
+def snapped_trace(e):
+    """tr(e), set to 0 when its magnitude is at most ZERO_TOL * max|lambda|."""
+    tr = trace(e)
+    scale = np.max(np.abs(np.linalg.eigvalsh(e)), axis=-1)
+    return np.where(np.abs(tr) <= ZERO_TOL * scale, 0.0, tr)
+
+
 def positive_part(e):
     """e_+ = sum_i max(0, lambda_i) v_i v_i^T (eigen-decomposition by numpy.linalg.eigh)."""
-    lam, V = np.linalg.eigh(e)
+    lam, V = eig_snapped(e)
     return np.einsum("...ik,...k,...jk->...ij", V, np.maximum(lam, 0.0), V)
 
 
@@ -71,7 +90,7 @@ def stress_energy(e, lam, mu, split):
     if split == SPLIT_NONE:
         return sig, np.zeros_like(sig), Es, Es
     ep = positive_part(e)
-    trp = np.maximum(tr, 0.0)
+    trp = np.maximum(snapped_trace(e), 0.0)[..., None, None]
     sigp = lam * trp * I + 2.0 * mu * ep
     Esp = (0.5 * lam * trp ** 2)[..., 0, 0] + mu[..., 0, 0] * np.einsum("...ij,...ij->...", ep, ep)
     return sigp, sig - sigp, Esp, Es
@@ -115,7 +134,7 @@ def theta_matrix(lam):
 
 def dplus(e, de):
     """d(e_+)[de] in divided-difference form (equal to Alg. 2 for distinct eigenvalues)."""
-    lam, V = np.linalg.eigh(e)
+    lam, V = eig_snapped(e)
     Th = theta_matrix(lam)
     W = np.einsum("...ki,...kl,...lj->...ij", V, de, V)
     return np.einsum("...ik,...kl,...jl->...ij", V, Th * W, V)
@@ -130,7 +149,7 @@ def dstress(e, de, lam, mu, split):
     dsig = lam * trd * I + 2.0 * mu * de
     if split == SPLIT_NONE:
         return dsig, np.zeros_like(dsig)
-    Ht = heaviside(trace(e))[..., None, None]
+    Ht = heaviside(snapped_trace(e))[..., None, None]
     dsigp = lam * Ht * trd * I + 2.0 * mu * dplus(e, de)
     return dsigp, dsig - dsigp
 

@@ -1,0 +1,12 @@
+"""GB300-native matrix-free phase-field fracture solver (sm_103a CUDA behind a C-ABI).
+
+Public entry points mirror the C library ``libpff`` (include/pff.h): ``setup_mesh`` returns a
+``Context`` whose methods are ``set_state``, ``apply_jacobian``, ``residual``, ``vcycle``,
+``solve_newton_step`` and friends, and ``ResidualFunction`` wraps the residual in
+``torch.autograd`` with the hand-written adjoint. The CUDA library is loaded on first use;
+there is no CPU fallback.
+"""
+from .pff import (  # noqa: F401
+    PFF_FLAG_BOTTOM, PFF_FLAG_SLIT, PFF_FLAG_TOP, PFF_MASK_ADJOINT, PFF_MASK_RAW, PFF_MODE_BLOCKDIAG,
+    PFF_MODE_FULL, PFF_MODE_TRANSPOSE, PFF_SPLIT_MIEHE, PFF_SPLIT_NONE, Context, PFFError, ResidualFunction,
+    default_params, load_library, setup_mesh)

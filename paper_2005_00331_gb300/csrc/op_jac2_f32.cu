@@ -1,0 +1,39 @@
+// Explicit instantiations of the 2D Jacobian operator kernels, float arithmetic.
+#include "pff_launch.h"
+#include "pff_op.cuh"
+
+namespace pff {
+
+template <int P, int SPLIT>
+static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
+                             const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
+  constexpr size_t smem = op2d_smem<P, float>();
+  static bool attr = false;
+  auto kern = k_op2d<P, float, PWJac<2, float, SPLIT>>;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  PWJac<2, float, SPLIT> pw;
+  pw.qp = qp;
+  pw.qpt = g.qpt;
+  pw.tstride = (long long)qp_nv(2, SPLIT) * g.qpt;
+  pw.mode = mode;
+  OpArgs oa{inmask, outmask};
+  if (g.ntiles > 0) kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags, const Geom& g,
+                       const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
+  if (dim != 2) return cudaErrorInvalidValue;
+#define PFF_CASE(PP, SS) \
+  if (p == PP && split == SS) return run_jac2<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s);
+  PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
+  PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
+#undef PFF_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pff

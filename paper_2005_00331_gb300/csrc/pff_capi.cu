@@ -1,0 +1,1062 @@
+// pff_capi.cu -- context, host orchestration and the C-ABI of libpff (see include/pff.h).
+//
+// The host side only builds meshes and tables, allocates, launches kernels on the caller's
+// stream and keeps the scalar bookkeeping of the Krylov solver (Hessenberg matrix, Givens
+// rotations). Every vector operation of the hot path runs in the kernels of this library.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pff.h"
+#include "pff_kernels.h"
+#include "pff_launch.h"
+
+using namespace pff;
+
+namespace {
+
+// ---- 1D bases (closed forms for p <= 4) ----------------------------------------------------
+void gll_nodes(int p, double* x) {
+  const double s5 = 1.0 / std::sqrt(5.0), s37 = std::sqrt(3.0 / 7.0);
+  switch (p) {
+    case 1: x[0] = 0; x[1] = 1; break;
+    case 2: x[0] = 0; x[1] = 0.5; x[2] = 1; break;
+    case 3: x[0] = 0; x[1] = 0.5 * (1 - s5); x[2] = 0.5 * (1 + s5); x[3] = 1; break;
+    default: x[0] = 0; x[1] = 0.5 * (1 - s37); x[2] = 0.5; x[3] = 0.5 * (1 + s37); x[4] = 1; break;
+  }
+}
+void gll_weights(int p, double* w) {
+  switch (p) {
+    case 1: w[0] = w[1] = 0.5; break;
+    case 2: w[0] = w[2] = 1.0 / 6; w[1] = 2.0 / 3; break;
+    case 3: w[0] = w[3] = 1.0 / 12; w[1] = w[2] = 5.0 / 12; break;
+    default: w[0] = w[4] = 1.0 / 20; w[1] = w[3] = 49.0 / 180; w[2] = 32.0 / 90; break;
+  }
+}
+// n-point Gauss-Legendre on [0, 1] (closed forms of the roots of P_n).
+void gauss(int n, double* x, double* w) {
+  double t[5], v[5];
+  switch (n) {
+    case 1: t[0] = 0; v[0] = 2; break;
+    case 2: t[0] = -1 / std::sqrt(3.0); t[1] = -t[0]; v[0] = v[1] = 1; break;
+    case 3:
+      t[0] = -std::sqrt(0.6); t[1] = 0; t[2] = -t[0];
+      v[0] = v[2] = 5.0 / 9; v[1] = 8.0 / 9; break;
+    case 4: {
+      const double a = std::sqrt(3.0 / 7 - 2.0 / 7 * std::sqrt(6.0 / 5)), b = std::sqrt(3.0 / 7 + 2.0 / 7 * std::sqrt(6.0 / 5));
+      t[0] = -b; t[1] = -a; t[2] = a; t[3] = b;
+      v[1] = v[2] = (18 + std::sqrt(30.0)) / 36; v[0] = v[3] = (18 - std::sqrt(30.0)) / 36; break;
+    }
+    default: {
+      const double a = std::sqrt(5 - 2 * std::sqrt(10.0 / 7)) / 3, b = std::sqrt(5 + 2 * std::sqrt(10.0 / 7)) / 3;
+      t[0] = -b; t[1] = -a; t[2] = 0; t[3] = a; t[4] = b;
+      v[2] = 128.0 / 225; v[1] = v[3] = (322 + 13 * std::sqrt(70.0)) / 900; v[0] = v[4] = (322 - 13 * std::sqrt(70.0)) / 900;
+      break;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    x[i] = 0.5 * (t[i] + 1);
+    w[i] = 0.5 * v[i];
+  }
+}
+double lag(const double* nd, int nn, int k, double x) {
+  double v = 1;
+  for (int m = 0; m < nn; ++m)
+    if (m != k) v *= (x - nd[m]) / (nd[k] - nd[m]);
+  return v;
+}
+double dlag(const double* nd, int nn, int k, double x) {
+  double s = 0;
+  for (int j = 0; j < nn; ++j) {
+    if (j == k) continue;
+    double t = 1 / (nd[k] - nd[j]);
+    for (int m = 0; m < nn; ++m)
+      if (m != k && m != j) t *= (x - nd[m]) / (nd[k] - nd[m]);
+    s += t;
+  }
+  return s;
+}
+
+const char* g_last_cuda = "";
+
+}  // namespace
+
+// ---- context --------------------------------------------------------------------------------
+struct LevelData {
+  int N = 0;
+  long long nn = 0, nd = 0;
+  double h = 0;
+  Geom g{};
+  Tab<double> t64{};
+  Tab<float> t32{};
+  unsigned char* flags = nullptr;
+  double* U = nullptr;      // state DoF vector
+  double* phit = nullptr;   // phi~ (follows U in memory so one interpolation covers both)
+  double* fields = nullptr; // 3 nodal fields (G_c, lambda, mu) when given
+  double* qp64 = nullptr;
+  float* qp32 = nullptr;
+  double* st64 = nullptr;
+  double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
+  double* di64 = nullptr;   // its inverse (Jacobi scaling)
+  float* di32 = nullptr;
+  double* lam = nullptr;    // device [lmax_u, lmax_phi, lmin_u, lmin_phi]
+  // multigrid work vectors, per precision: r, e, t, res, dv, s
+  double* w64[6] = {};
+  float* w32[6] = {};
+};
+
+struct pff_ctx {
+  pff_params prm{};
+  cudaStream_t s = nullptr;
+  int dim = 2, p = 1, nlev = 0, nv = 0;
+  std::vector<LevelData> lv;
+  XferTab xt{};
+  bool has_state = false, qp_valid = false, mg_ready = false, has_fields = false;
+  double* phi_old = nullptr;
+  double* mass = nullptr;
+  double* R = nullptr;
+  double* rhs = nullptr;
+  double* dU = nullptr;
+  double* scratch = nullptr;   // 4 fine-sized FP64 vectors (CG-Lanczos, residual checks)
+  double* partial = nullptr;   // reduction partials
+  double* dres = nullptr;      // small device results
+  double* hist = nullptr;      // CG alpha/beta histories
+  int* cnt = nullptr;
+  double* pinned = nullptr;    // host pinned scalars
+  double* pgrad_tmp = nullptr;
+  // coarse dense blocks
+  double *Au = nullptr, *Ap = nullptr, *Bc = nullptr, *gjbuf = nullptr, *cr = nullptr, *ce = nullptr, *ct = nullptr;
+  // FGMRES
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *hdev = nullptr, *ydev = nullptr;
+  std::vector<void*> allocs;
+  // kernel-family timing (pff_profile)
+  int prof = 0;
+  std::vector<cudaEvent_t> ev;
+  int nev = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(pff_ctx* c, T** p, long long n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  void* q = nullptr;
+  if (cudaMalloc(&q, sizeof(T) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    return PFF_ERR_OOM;
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return PFF_OK;
+}
+
+#define CK(...)                                 \
+  do {                                          \
+    cudaError_t e_ = (__VA_ARGS__);             \
+    if (e_ != cudaSuccess) {                    \
+      g_last_cuda = cudaGetErrorString(e_);     \
+      return PFF_ERR_CUDA;                      \
+    }                                           \
+  } while (0)
+#define CR(...)               \
+  do {                        \
+    int r_ = (__VA_ARGS__);   \
+    if (r_ != PFF_OK) return r_; \
+  } while (0)
+
+void make_geom(LevelData& L, int dim, int p) {
+  Geom& g = L.g;
+  g.dim = dim;
+  g.p = p;
+  g.N = L.N;
+  g.n1 = p * L.N + 1;
+  g.nn = L.nn;
+  int t[3];
+  tile_shape(dim, p, t);
+  for (int i = 0; i < 3; ++i) {
+    g.tdim[i] = t[i];
+    g.ntile[i] = (i < dim) ? (L.N + t[i] - 1) / t[i] : 1;
+  }
+  g.qpx = t[0] * (p + 1);
+  g.qpy = t[1] * (p + 1);
+  g.qpz = dim == 3 ? t[2] * (p + 1) : 1;
+  g.qpt = (long long)g.qpx * g.qpy * g.qpz;
+  g.ntiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
+}
+
+void make_tabs(LevelData& L, int dim, int p) {
+  const int n = p + 1;
+  double xn[MAXN], xq[MAXN], wq[MAXN];
+  gll_nodes(p, xn);
+  gauss(n, xq, wq);
+  std::memset(&L.t64, 0, sizeof(L.t64));
+  std::memset(&L.t32, 0, sizeof(L.t32));
+  for (int q = 0; q < n; ++q) {
+    for (int k = 0; k < n; ++k) {
+      L.t64.S[q][k] = lag(xn, n, k, xq[q]);
+      L.t64.D[q][k] = dlag(xn, n, k, xq[q]) / L.h;
+      L.t32.S[q][k] = (float)L.t64.S[q][k];
+      L.t32.D[q][k] = (float)L.t64.D[q][k];
+    }
+    L.t64.W[q] = wq[q];
+    L.t32.W[q] = (float)wq[q];
+  }
+  L.t64.hd = std::pow(L.h, dim);
+  L.t32.hd = (float)L.t64.hd;
+}
+
+void make_xfer(XferTab& xt, int p) {
+  double xn[MAXN];
+  gll_nodes(p, xn);
+  const int n = p + 1;
+  std::memset(&xt, 0, sizeof(xt));
+  for (int o = 0; o <= 2 * p; ++o) {
+    const int fc = (o == 2 * p) ? 1 : o / p;
+    const int j = o - fc * p;
+    const double xi = 0.5 * (fc + xn[j]);
+    for (int k = 0; k < n; ++k) {
+      double v = lag(xn, n, k, xi);
+      if (std::fabs(v) < 1e-15) v = 0.0;
+      xt.E[o][k] = v;
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    const int fc = xn[k] < 0.5 ? 0 : 1;
+    const double t = 2 * xn[k] - fc;
+    xt.FC[k] = fc;
+    xt.COL[k] = -1;
+    for (int m = 0; m < n; ++m) {
+      double v = lag(xn, n, m, t);
+      if (std::fabs(v) < 1e-15) v = 0.0;
+      xt.F[k][m] = v;
+      if (std::fabs(t - xn[m]) < 1e-12) xt.COL[k] = fc * p + m;
+    }
+  }
+}
+
+// Node flags of a level (tension test: Dirichlet faces, slit), computed on the host.
+std::vector<unsigned char> host_flags(int dim, int p, int N) {
+  const int n1 = p * N + 1;
+  double xn[MAXN];
+  gll_nodes(p, xn);
+  std::vector<double> x1(n1);
+  for (int i = 0; i < n1; ++i) {
+    int c = i / p, k = i % p;
+    if (c == N) {
+      c = N - 1;
+      k = p;
+    }
+    x1[i] = (c + xn[k]) / N;
+  }
+  long long nn = 1;
+  for (int t = 0; t < dim; ++t) nn *= n1;
+  std::vector<unsigned char> fl(nn, 0);
+  for (long long i = 0; i < nn; ++i) {
+    long long rem = i;
+    int ijk[3] = {0, 0, 0};
+    for (int t = 0; t < dim; ++t) {
+      ijk[t] = int(rem % n1);
+      rem /= n1;
+    }
+    const int vert = ijk[dim - 1];
+    unsigned char f = 0;
+    if (vert == 0) f |= PFF_FLAG_BOTTOM;
+    if (vert == n1 - 1) f |= PFF_FLAG_TOP;
+    if (vert == 0 || vert == n1 - 1)
+      for (int c = 0; c < dim; ++c) f |= (unsigned char)(1u << c);
+    if (std::fabs(x1[vert] - 0.5) <= 1e-12 && x1[ijk[0]] <= 0.5 + 1e-12) f |= PFF_FLAG_SLIT;
+    fl[i] = f;
+  }
+  return fl;
+}
+
+template <typename Real> Real* qp_of(LevelData& L);
+template <> double* qp_of<double>(LevelData& L) { return L.qp64; }
+template <> float* qp_of<float>(LevelData& L) { return L.qp32; }
+template <typename Real> const Tab<Real>& tab_of(LevelData& L);
+template <> const Tab<double>& tab_of<double>(LevelData& L) { return L.t64; }
+template <> const Tab<float>& tab_of<float>(LevelData& L) { return L.t32; }
+template <typename Real> Real* dinv_of(LevelData& L);
+template <> double* dinv_of<double>(LevelData& L) { return L.di64; }
+template <> float* dinv_of<float>(LevelData& L) { return L.di32; }
+template <typename Real> Real** work_of(LevelData& L);
+template <> double** work_of<double>(LevelData& L) { return L.w64; }
+template <> float** work_of<float>(LevelData& L) { return L.w32; }
+
+template <typename Real>
+int ensure_work(pff_ctx* c, int l) {
+  LevelData& L = c->lv[l];
+  Real** w = work_of<Real>(L);
+  if (w[0]) return PFF_OK;
+  for (int i = 0; i < 6; ++i) CR(dalloc(c, &w[i], L.nd));
+  return PFF_OK;
+}
+
+constexpr int PROF_MAX_LAUNCHES = 16384;
+
+bool prof_on(pff_ctx* c, int family) { return c->prof == family && c->nev + 2 <= (int)c->ev.size(); }
+int prof_mark(pff_ctx* c) {
+  CK(cudaEventRecord(c->ev[c->nev++], c->s));
+  return PFF_OK;
+}
+
+// Is a Jacobian launch of this precision on level l in the profiled family?
+template <typename Real>
+bool prof_jac(pff_ctx* c, int l) {
+  const bool d = sizeof(Real) == 8;
+  return prof_on(c, d ? PFF_PROF_JAC64 : PFF_PROF_JAC32) ||
+         (l == 0 && prof_on(c, d ? PFF_PROF_JAC64_L0 : PFF_PROF_JAC32_L0));
+}
+
+// y = G x on level l (y zeroed first).
+template <typename Real>
+int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask, int outmask) {
+  LevelData& L = c->lv[l];
+  CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
+  const bool timed = prof_jac<Real>(c, l);
+  if (timed) CR(prof_mark(c));
+  CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
+                outmask, c->s));
+  if (timed) CR(prof_mark(c));
+  return PFF_OK;
+}
+
+int qp_setup_level(pff_ctx* c, int l) {
+  LevelData& L = c->lv[l];
+  MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+  const double* F = L.fields;
+  CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
+                     c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
+                     L.qp64, L.qp32, L.st64, c->s));
+  return PFF_OK;
+}
+
+int ensure_qp(pff_ctx* c) {
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  if (!c->qp_valid) {
+    CR(qp_setup_level(c, 0));
+    c->qp_valid = true;
+  }
+  return PFF_OK;
+}
+
+int residual_into(pff_ctx* c, double* r) {
+  CR(ensure_qp(c));
+  LevelData& L = c->lv[0];
+  CK(cudaMemsetAsync(r, 0, sizeof(double) * L.nd, c->s));
+  const bool timed = prof_on(c, PFF_PROF_RESIDUAL);
+  if (timed) CR(prof_mark(c));
+  CK(launch_res(c->dim, c->p, c->prm.split, L.U, r, L.flags, L.g, L.t64, L.st64, c->prm.eps, c->prm.kappa, c->s));
+  if (timed) CR(prof_mark(c));
+  return PFF_OK;
+}
+
+// lambda_max of D^{-1} G_uu and D^{-1} G_phiphi on level l by CG-Lanczos (FP64).
+int eig_estimate(pff_ctx* c, int l) {
+  LevelData& L = c->lv[l];
+  const long long n = L.nd, nu = c->dim * L.nn;
+  double *r = c->scratch, *z = r + c->lv[0].nd, *pv = z + c->lv[0].nd, *Ap = pv + c->lv[0].nd;
+  double* scal = c->dres + 8;  // 12 doubles
+  const int it_max = c->prm.eig_iters;
+  double* ah = c->hist;
+  double* bh = c->hist + 2 * it_max;
+  CK(cudaMemsetAsync(scal, 0, 12 * sizeof(double), c->s));
+  CK(cudaMemsetAsync(c->hist, 0, 4 * it_max * sizeof(double), c->s));
+  CK(launch_cg_init(n, nu, c->prm.eig_seed, L.flags, c->dim, L.nn, L.di64, r, z, pv, c->s));
+  CK(launch_dot2(n, nu, r, z, c->partial, scal + 0, c->s));
+  for (int it = 0; it < it_max; ++it) {
+    CR(apply_level<double>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
+    CK(launch_dot2(n, nu, pv, Ap, c->partial, scal + 2, c->s));
+    CK(launch_cg_scalars(0, it, it_max, scal, ah, bh, c->s));
+    CK(launch_cg_update(n, nu, Ap, L.di64, scal, r, z, c->s));
+    CK(launch_dot2(n, nu, r, z, c->partial, scal + 8, c->s));
+    CK(launch_cg_scalars(1, it, it_max, scal, ah, bh, c->s));
+    CK(launch_cg_pupdate(n, nu, z, scal, pv, c->s));
+  }
+  CK(launch_tridiag_eig(it_max, ah, bh, L.lam, c->s));
+  return PFF_OK;
+}
+
+
+int mg_setup(pff_ctx* c) {
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  if (c->mg_ready) return PFF_OK;
+  CR(ensure_qp(c));
+  const int nf_state = c->dim + 2;  // U (dim+1 fields) and phi~ are contiguous
+  for (int l = 1; l < c->nlev; ++l) {
+    LevelData &F = c->lv[l - 1], &L = c->lv[l];
+    CK(launch_state_interp(c->dim, c->p, F.U, L.U, nf_state, F.g, L.g, c->xt, c->s));
+    if (c->has_fields) CK(launch_state_interp(c->dim, c->p, F.fields, L.fields, 3, F.g, L.g, c->xt, c->s));
+    CK(launch_coarse_active(c->dim, c->p, F.flags, L.flags, F.g, L.g, c->xt, c->s));
+    CR(qp_setup_level(c, l));
+  }
+  for (int l = 0; l < c->nlev; ++l) {
+    LevelData& L = c->lv[l];
+    CK(launch_diagonal(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, nullptr, c->s));
+    CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
+    if (l < c->nlev - 1) CR(eig_estimate(c, l));
+  }
+  // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
+  LevelData& C = c->lv[c->nlev - 1];
+  const int nn = (int)C.nn, nu = c->dim * nn;
+  CK(launch_coarse_assemble(c->dim, c->p, c->prm.split, C.qp64, C.flags, C.g, C.t64, c->Au, c->Ap, c->Bc, c->s));
+  CK(launch_gj_inverse(c->Au, nu, c->gjbuf, c->s));
+  CK(launch_gj_inverse(c->Ap, nn, c->gjbuf, c->s));
+  c->mg_ready = true;
+  return PFF_OK;
+}
+
+// z = G_c^{-1} r on the coarsest level (FP64): z_u = Au^{-1} r_u, z_phi = Ap^{-1} (r_phi - B z_u).
+int coarse_solve64(pff_ctx* c, const double* r, double* z) {
+  LevelData& C = c->lv[c->nlev - 1];
+  const int nn = (int)C.nn, nu = c->dim * nn;
+  CK(launch_gemv(c->Au, nu, nu, r, z, 1.0, 0.0, c->s));
+  CK(cudaMemcpyAsync(c->ct, r + nu, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+  CK(launch_gemv(c->Bc, nn, nu, z, c->ct, -1.0, 1.0, c->s));
+  CK(launch_gemv(c->Ap, nn, nn, c->ct, z + nu, 1.0, 0.0, c->s));
+  return PFF_OK;
+}
+
+template <typename Real>
+int coarse_solve(pff_ctx* c, const Real* r, Real* z);
+template <>
+int coarse_solve<double>(pff_ctx* c, const double* r, double* z) {
+  return coarse_solve64(c, r, z);
+}
+template <>
+int coarse_solve<float>(pff_ctx* c, const float* r, float* z) {
+  const long long n = c->lv[c->nlev - 1].nd;
+  CK(launch_cast<float, double>(n, r, c->cr, c->s));
+  CR(coarse_solve64(c, c->cr, c->ce));
+  CK(launch_cast<double, float>(n, c->ce, z, c->s));
+  return PFF_OK;
+}
+
+// x = S f: block-diagonal Chebyshev-Jacobi of degree cheb_degree with zero initial guess.
+template <typename Real>
+int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
+  LevelData& L = c->lv[l];
+  const long long n = L.nd, nu = c->dim * L.nn;
+  const double lo = c->prm.cheb_lo, hi = c->prm.cheb_hi;
+  const double sigma = (hi + lo) / (hi - lo);
+  double rho = 1.0 / sigma;
+  CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, L.lam, lo, hi, 0.0, 0.0, c->s));
+  for (int k = 1; k < c->prm.cheb_degree; ++k) {
+    CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, L.lam, lo, hi, rho_new * rho, rho_new, c->s));
+    rho = rho_new;
+  }
+  return PFF_OK;
+}
+
+// e = V-cycle(r) from level l down (Sec. 3.3): pre-smooth, residual, restrict, recurse,
+// prolongate, post-smooth on the residual.
+template <typename Real>
+int vcycle_level(pff_ctx* c, int l, const Real* r, Real* e) {
+  if (l == c->nlev - 1) return coarse_solve<Real>(c, r, e);
+  CR(ensure_work<Real>(c, l));
+  CR(ensure_work<Real>(c, l + 1));
+  LevelData &L = c->lv[l], &Lc = c->lv[l + 1];
+  Real** w = work_of<Real>(L);
+  Real** wc = work_of<Real>(Lc);
+  Real *t = w[2], *res = w[3], *dv = w[4], *sx = w[5];
+  CR(smooth<Real>(c, l, r, e, t, dv));
+  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
+  CK(cudaMemcpyAsync(res, r, sizeof(Real) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  CK(launch_axpby<Real>(L.nd, -1.0, t, 1.0, res, c->s));
+  CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s));
+  CR(vcycle_level<Real>(c, l + 1, wc[0], wc[1]));
+  CK(launch_prolong<Real>(c->dim, c->p, wc[1], e, L.flags, Lc.g, L.g, c->xt, true, c->s));
+  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
+  CK(cudaMemcpyAsync(res, r, sizeof(Real) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  CK(launch_axpby<Real>(L.nd, -1.0, t, 1.0, res, c->s));
+  CR(smooth<Real>(c, l, res, sx, t, dv));
+  CK(launch_axpby<Real>(L.nd, 1.0, sx, 1.0, e, c->s));
+  return PFF_OK;
+}
+
+// FP64 in/out; inside in mg_precision.
+int precondition(pff_ctx* c, const double* r, double* z) {
+  CR(mg_setup(c));
+  if (c->prm.mg_precision == 32) {
+    CR(ensure_work<float>(c, 0));
+    LevelData& L = c->lv[0];
+    CK(launch_cast<double, float>(L.nd, r, L.w32[0], c->s));
+    CR(vcycle_level<float>(c, 0, L.w32[0], L.w32[1]));
+    CK(launch_cast<float, double>(L.nd, L.w32[1], z, c->s));
+  } else {
+    CR(vcycle_level<double>(c, 0, r, z));
+  }
+  return PFF_OK;
+}
+
+// ||x||^2 over both blocks, synchronising (host result).
+int norm2_host(pff_ctx* c, const double* x, long long n, double* out) {
+  CK(launch_dot2<double>(n, n, x, x, c->partial, c->dres, c->s));
+  CK(cudaMemcpyAsync(c->pinned, c->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  *out = c->pinned[0] + c->pinned[1];
+  return PFF_OK;
+}
+
+// Right-preconditioned flexible GMRES(m), x0 = 0, CGS2 orthogonalisation in FP64.
+int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
+  CR(mg_setup(c));
+  LevelData& L = c->lv[0];
+  const long long n = L.nd;
+  const int m = c->prm.gmres_restart;
+  const double tol = c->prm.lin_rtol;
+  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, c->s));
+  double b2;
+  CR(norm2_host(c, b, n, &b2));
+  if (!std::isfinite(b2)) return PFF_ERR_NAN;
+  const double beta0 = std::sqrt(b2);
+  if (iters_out) *iters_out = 0;
+  if (rel_out) *rel_out = 0.0;
+  if (beta0 == 0.0) return PFF_OK;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int its = 0;
+  double rel = 1.0;
+  int status = PFF_OK;
+  double* r = c->w;  // residual of the current cycle
+  bool first = true;
+  while (true) {
+    if (first) {
+      CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+    } else {
+      CR(apply_level<double>(c, 0, x, r, JM_FULL, IN_ALL, OUT_IDENTITY));
+      CK(launch_axpby<double>(n, 1.0, b, -1.0, r, c->s));
+    }
+    first = false;
+    double r2;
+    CR(norm2_host(c, r, n, &r2));
+    const double beta = std::sqrt(r2);
+    rel = beta / beta0;
+    if (!std::isfinite(beta)) return PFF_ERR_NAN;
+    if (rel <= tol || its >= c->prm.gmres_max_iters) break;
+    CK(launch_axpby<double>(n, 1.0 / beta, r, 0.0, c->V, c->s));
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = c->V + (long long)j * n;
+      double* Zj = c->Z + (long long)j * n;
+      double* wv = c->V + (long long)(j + 1) * n;
+      CR(precondition(c, Vj, Zj));
+      CR(apply_level<double>(c, 0, Zj, wv, JM_FULL, IN_ALL, OUT_IDENTITY));
+      CK(launch_mdot(n, j + 1, c->V, wv, c->partial, c->hdev, c->s));
+      CK(launch_maxpy(n, j + 1, c->V, c->hdev, wv, c->s));
+      CK(launch_mdot(n, j + 1, c->V, wv, c->partial, c->hdev + (m + 1), c->s));
+      CK(launch_maxpy(n, j + 1, c->V, c->hdev + (m + 1), wv, c->s));
+      CK(launch_dot2<double>(n, n, wv, wv, c->partial, c->hdev + 2 * (m + 1), c->s));
+      CK(cudaMemcpyAsync(c->pinned, c->hdev, sizeof(double) * (2 * (m + 1) + 2), cudaMemcpyDeviceToHost, c->s));
+      CK(cudaStreamSynchronize(c->s));
+      const double* hh = c->pinned;
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
+      const double nw2 = hh[2 * (m + 1)] + hh[2 * (m + 1) + 1];
+      if (!std::isfinite(nw2)) return PFF_ERR_NAN;
+      const double nw = std::sqrt(nw2);
+      H[(j + 1) * m + j] = nw;
+      if (nw > 0.0) CK(launch_normalize(n, wv, c->hdev + 2 * (m + 1), wv, c->s));
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = std::hypot(H[j * m + j], H[(j + 1) * m + j]);
+      if (den == 0.0) {
+        status = PFF_ERR_BREAKDOWN;
+        stop = true;
+        break;
+      }
+      cs[j] = H[j * m + j] / den;
+      sn[j] = H[(j + 1) * m + j] / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      k = j + 1;
+      ++its;
+      rel = std::fabs(gv[j + 1]) / beta0;
+      if (rel <= tol || its >= c->prm.gmres_max_iters || nw == 0.0) {
+        stop = true;
+        break;
+      }
+    }
+    if (k > 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int jj = i + 1; jj < k; ++jj) s -= H[i * m + jj] * y[jj];
+        y[i] = s / H[i * m + i];
+      }
+      std::memcpy(c->pinned, y.data(), sizeof(double) * k);
+      CK(cudaMemcpyAsync(c->ydev, c->pinned, sizeof(double) * k, cudaMemcpyHostToDevice, c->s));
+      CK(launch_zupdate(n, k, c->Z, c->ydev, x, c->s));
+      CK(cudaStreamSynchronize(c->s));
+    }
+    if (stop && status != PFF_OK) break;
+    if (stop && its >= c->prm.gmres_max_iters) {
+      // final true residual below
+    }
+    if (stop && rel > tol && its < c->prm.gmres_max_iters) continue;
+    if (stop) {
+      // verify with the true residual
+      CR(apply_level<double>(c, 0, x, r, JM_FULL, IN_ALL, OUT_IDENTITY));
+      CK(launch_axpby<double>(n, 1.0, b, -1.0, r, c->s));
+      double rr;
+      CR(norm2_host(c, r, n, &rr));
+      rel = std::sqrt(rr) / beta0;
+      break;
+    }
+  }
+  if (iters_out) *iters_out = its;
+  if (rel_out) *rel_out = rel;
+  if (status != PFF_OK) return status;
+  if (rel > tol) return PFF_ERR_NOT_CONVERGED;
+  return PFF_OK;
+}
+
+bool valid_prec(int p) { return p == 32 || p == 64; }
+
+}  // namespace
+
+// =============================================================================================
+// C-ABI
+extern "C" {
+
+void pff_default_params(pff_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->degree = 1;
+  p->n_cells_1d = 32;
+  p->coarse_min = 3;
+  p->split = PFF_SPLIT_NONE;
+  p->lambda = 121.15;
+  p->mu = 80.77;
+  p->gc = 2.7e-3;
+  p->eps = 2.0 / 32;
+  p->kappa = 1e-10;
+  p->as_c = 1.0;
+  p->mg_precision = 32;
+  p->cheb_degree = 5;
+  p->cheb_lo = 0.24;
+  p->cheb_hi = 1.2;
+  p->eig_iters = 15;
+  p->eig_seed = 0;
+  p->gmres_restart = 50;
+  p->gmres_max_iters = 500;
+  p->lin_rtol = 1e-6;
+}
+
+const char* pff_strerror(int st) {
+  switch (st) {
+    case PFF_OK: return "ok";
+    case PFF_ERR_INVALID_ARG: return "invalid argument";
+    case PFF_ERR_OOM: return "out of device memory";
+    case PFF_ERR_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+    case PFF_ERR_NAN: return "non-finite value";
+    case PFF_ERR_NOT_CONVERGED: return "linear solver did not converge";
+    case PFF_ERR_BREAKDOWN: return "Krylov breakdown";
+    case PFF_ERR_NO_STATE: return "no state set";
+    default: return "unknown status";
+  }
+}
+
+void pff_destroy(pff_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (void* q : c->allocs) cudaFree(q);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+static int setup_impl(pff_ctx* c) {
+  const pff_params& P = c->prm;
+  c->dim = P.dim;
+  c->p = P.degree;
+  std::vector<int> sizes{P.n_cells_1d};
+  while (sizes.back() % 2 == 0 && sizes.back() / 2 >= P.coarse_min) sizes.push_back(sizes.back() / 2);
+  c->nlev = (int)sizes.size();
+  c->lv.resize(c->nlev);
+  make_xfer(c->xt, c->p);
+  for (int l = 0; l < c->nlev; ++l) {
+    LevelData& L = c->lv[l];
+    L.N = sizes[l];
+    L.h = 1.0 / L.N;
+    long long n1 = (long long)c->p * L.N + 1;
+    L.nn = c->dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    L.nd = (c->dim + 1) * L.nn;
+    make_geom(L, c->dim, c->p);
+    make_tabs(L, c->dim, c->p);
+    const int nv = qp_nv(c->dim, P.split);
+    CR(dalloc(c, &L.flags, L.nn));
+    CR(dalloc(c, &L.U, L.nd + L.nn));  // U and phi~ contiguous
+    L.phit = L.U + L.nd;
+    CR(dalloc(c, &L.fields, 3 * L.nn));
+    const long long nqp = L.g.ntiles * L.g.qpt;
+    CR(dalloc(c, &L.qp64, nv * nqp));
+    CR(dalloc(c, &L.qp32, nv * nqp));
+    CK(cudaMemsetAsync(L.qp64, 0, sizeof(double) * nv * nqp, c->s));
+    CK(cudaMemsetAsync(L.qp32, 0, sizeof(float) * nv * nqp, c->s));
+    if (l == 0) {
+      CR(dalloc(c, &L.st64, ST_NV * nqp));
+      CK(cudaMemsetAsync(L.st64, 0, sizeof(double) * ST_NV * nqp, c->s));
+    }
+    CR(dalloc(c, &L.d64, L.nd));
+    CR(dalloc(c, &L.di64, L.nd));
+    CR(dalloc(c, &L.di32, L.nd));
+    CR(dalloc(c, &L.lam, 4));
+    std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N);
+    CK(cudaMemcpyAsync(L.flags, fl.data(), fl.size(), cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
+  }
+  LevelData& F = c->lv[0];
+  CR(dalloc(c, &c->phi_old, F.nn));
+  CR(dalloc(c, &c->mass, F.nn));
+  CR(dalloc(c, &c->R, F.nd));
+  CR(dalloc(c, &c->rhs, F.nd));
+  CR(dalloc(c, &c->dU, F.nd));
+  CR(dalloc(c, &c->scratch, 4 * F.nd));
+  const int m = P.gmres_restart;
+  CR(dalloc(c, &c->partial, std::max<long long>(2 * 152 * 2, (long long)(m + 2) * 152)));
+  CR(dalloc(c, &c->dres, 32));
+  CR(dalloc(c, &c->hist, 4 * P.eig_iters));
+  CR(dalloc(c, &c->cnt, 2));
+  CR(dalloc(c, &c->V, (long long)(m + 1) * F.nd));
+  CR(dalloc(c, &c->Z, (long long)m * F.nd));
+  CR(dalloc(c, &c->w, F.nd));
+  CR(dalloc(c, &c->hdev, 3 * (m + 1) + 4));
+  CR(dalloc(c, &c->ydev, m + 1));
+  if (cudaMallocHost(&c->pinned, sizeof(double) * (4 * (m + 2) + 64)) != cudaSuccess) return PFF_ERR_OOM;
+  LevelData& C = c->lv[c->nlev - 1];
+  const long long nnc = C.nn, nuc = c->dim * C.nn;
+  CR(dalloc(c, &c->Au, nuc * nuc));
+  CR(dalloc(c, &c->Ap, nnc * nnc));
+  CR(dalloc(c, &c->Bc, nnc * nuc));
+  CR(dalloc(c, &c->gjbuf, 2 * nuc));
+  CR(dalloc(c, &c->cr, C.nd));
+  CR(dalloc(c, &c->ce, C.nd));
+  CR(dalloc(c, &c->ct, C.nd));
+  // lumped phase-field mass: 1D sums of GLL weights times h
+  {
+    const int n1 = c->p * F.N + 1;
+    double wg[MAXN];
+    gll_weights(c->p, wg);
+    std::vector<double> w1(n1, 0.0);
+    for (int cc = 0; cc < F.N; ++cc)
+      for (int k = 0; k <= c->p; ++k) w1[cc * c->p + k] += wg[k] * F.h;
+    double* dw1;
+    CR(dalloc(c, &dw1, n1));
+    CK(cudaMemcpyAsync(dw1, w1.data(), sizeof(double) * n1, cudaMemcpyHostToDevice, c->s));
+    CK(launch_lumped_mass(c->dim, F.nn, n1, dw1, c->mass, c->s));
+    CK(cudaStreamSynchronize(c->s));
+  }
+  return PFF_OK;
+}
+
+int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream) {
+  if (!out || !p) return PFF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if ((p->dim != 2 && p->dim != 3) || p->degree < 1 || p->degree > MAXP || p->n_cells_1d < 1 ||
+      p->coarse_min < 1 || (p->split != PFF_SPLIT_NONE && p->split != PFF_SPLIT_MIEHE) ||
+      !valid_prec(p->mg_precision) || p->cheb_degree < 1 || !(p->cheb_hi > p->cheb_lo) || !(p->cheb_lo > 0) ||
+      p->eig_iters < 1 || p->eig_iters > 64 || p->gmres_restart < 1 || p->gmres_max_iters < 1 ||
+      !(p->lin_rtol > 0) || !(p->eps > 0))
+    return PFF_ERR_INVALID_ARG;
+  pff_ctx* c = new (std::nothrow) pff_ctx();
+  if (!c) return PFF_ERR_OOM;
+  c->prm = *p;
+  c->s = static_cast<cudaStream_t>(stream);
+  const int st = setup_impl(c);
+  if (st != PFF_OK) {
+    pff_destroy(c);
+    return st;
+  }
+  *out = c;
+  return PFF_OK;
+}
+
+int pff_sizes(const pff_ctx* c, long long* n_dofs, long long* n_nodes, int* n_levels) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  if (n_dofs) *n_dofs = c->lv[0].nd;
+  if (n_nodes) *n_nodes = c->lv[0].nn;
+  if (n_levels) *n_levels = c->nlev;
+  return PFF_OK;
+}
+
+int pff_level_sizes(const pff_ctx* c, int level, long long* n_nodes, int* n_cells_1d) {
+  if (!c || level < 0 || level >= c->nlev) return PFF_ERR_INVALID_ARG;
+  if (n_nodes) *n_nodes = c->lv[level].nn;
+  if (n_cells_1d) *n_cells_1d = c->lv[level].N;
+  return PFF_OK;
+}
+
+int pff_node_flags(pff_ctx* c, int level, unsigned char* flags) {
+  if (!c || !flags || level < 0 || level >= c->nlev) return PFF_ERR_INVALID_ARG;
+  if (level > 0 && c->has_state) CR(mg_setup(c));
+  CK(cudaMemcpyAsync(flags, c->lv[level].flags, c->lv[level].nn, cudaMemcpyDeviceToDevice, c->s));
+  return PFF_OK;
+}
+
+int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const double* phi_tilde,
+                  const unsigned char* active, const double* gc_field, const double* lambda_field,
+                  const double* mu_field) {
+  if (!c || !U || !phi_old) return PFF_ERR_INVALID_ARG;
+  LevelData& L = c->lv[0];
+  CK(cudaMemcpyAsync(L.U, U, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaMemcpyAsync(c->phi_old, phi_old, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaMemcpyAsync(L.phit, phi_tilde ? phi_tilde : phi_old, sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, c->s));
+  c->has_fields = gc_field || lambda_field || mu_field;
+  if (c->has_fields) {
+    // missing fields of a partial set take the constants
+    const double* src[3] = {gc_field, lambda_field, mu_field};
+    const double cst[3] = {c->prm.gc, c->prm.lambda, c->prm.mu};
+    for (int k = 0; k < 3; ++k) {
+      if (src[k]) {
+        CK(cudaMemcpyAsync(L.fields + k * L.nn, src[k], sizeof(double) * L.nn, cudaMemcpyDeviceToDevice, c->s));
+      } else {
+        std::vector<double> h(L.nn, cst[k]);
+        CK(cudaMemcpyAsync(L.fields + k * L.nn, h.data(), sizeof(double) * L.nn, cudaMemcpyHostToDevice, c->s));
+        CK(cudaStreamSynchronize(c->s));
+      }
+    }
+  }
+  c->has_state = true;
+  c->qp_valid = false;
+  c->mg_ready = false;
+  if (active) {
+    CK(launch_set_active(c->dim, L.nn, active, L.flags, c->s));
+  } else {
+    std::vector<unsigned char> none(L.nn, 0);
+    unsigned char* dz = reinterpret_cast<unsigned char*>(c->scratch);
+    CK(cudaMemcpyAsync(dz, none.data(), L.nn, cudaMemcpyHostToDevice, c->s));
+    CK(launch_set_active(c->dim, L.nn, dz, L.flags, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    CR(residual_into(c, c->R));
+    CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
+    c->qp_valid = false;
+  }
+  CR(ensure_qp(c));
+  return PFF_OK;
+}
+
+int pff_get_state(pff_ctx* c, double* U_out) {
+  if (!c || !U_out) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  CK(cudaMemcpyAsync(U_out, c->lv[0].U, sizeof(double) * c->lv[0].nd, cudaMemcpyDeviceToDevice, c->s));
+  return PFF_OK;
+}
+
+int pff_get_active(pff_ctx* c, unsigned char* a) {
+  if (!c || !a) return PFF_ERR_INVALID_ARG;
+  CK(launch_get_active(c->dim, c->lv[0].nn, c->lv[0].flags, a, c->s));
+  return PFF_OK;
+}
+
+int pff_apply_jacobian(pff_ctx* c, int level, const void* x, void* y, int precision, int mode) {
+  if (!c || !x || !y || level < 0 || level >= c->nlev || !valid_prec(precision) || x == y) return PFF_ERR_INVALID_ARG;
+  const int jm = mode & 3;
+  if (jm > 2 || (mode & ~15) || ((mode & PFF_MASK_RAW) && (mode & PFF_MASK_ADJOINT))) return PFF_ERR_INVALID_ARG;
+  CR(ensure_qp(c));
+  if (level > 0) CR(mg_setup(c));
+  int inm = IN_ALL, outm = OUT_IDENTITY;
+  if (mode & PFF_MASK_RAW) {
+    inm = IN_RAW;
+    outm = OUT_RAW;
+  } else if (mode & PFF_MASK_ADJOINT) {
+    inm = IN_DIRICHLET;
+    outm = OUT_RAW;
+  }
+  if (precision == 64)
+    return apply_level<double>(c, level, static_cast<const double*>(x), static_cast<double*>(y), jm, inm, outm);
+  return apply_level<float>(c, level, static_cast<const float*>(x), static_cast<float*>(y), jm, inm, outm);
+}
+
+int pff_residual(pff_ctx* c, double* r) {
+  if (!c || !r) return PFF_ERR_INVALID_ARG;
+  return residual_into(c, r);
+}
+
+int pff_diagonal(pff_ctx* c, int level, void* diag, int precision) {
+  if (!c || !diag || level < 0 || level >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  LevelData& L = c->lv[level];
+  if (precision == 64)
+    CK(cudaMemcpyAsync(diag, L.d64, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  else
+    CK(launch_cast<double, float>(L.nd, L.d64, static_cast<float*>(diag), c->s));
+  return PFF_OK;
+}
+
+int pff_lambda_max(pff_ctx* c, int level, double* lam2) {
+  if (!c || !lam2 || level < 0 || level >= c->nlev) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  CK(cudaMemcpyAsync(c->pinned, c->lv[level].lam, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  lam2[0] = c->pinned[0];
+  lam2[1] = c->pinned[1];
+  return PFF_OK;
+}
+
+int pff_level_state(pff_ctx* c, int level, double* U_level) {
+  if (!c || !U_level || level < 0 || level >= c->nlev) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  CK(cudaMemcpyAsync(U_level, c->lv[level].U, sizeof(double) * c->lv[level].nd, cudaMemcpyDeviceToDevice, c->s));
+  return PFF_OK;
+}
+
+int pff_prolongate(pff_ctx* c, int level, const void* xc, void* yf, int precision) {
+  if (!c || !xc || !yf || level < 0 || level + 1 >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  LevelData &L = c->lv[level], &Lc = c->lv[level + 1];
+  if (precision == 64)
+    CK(launch_prolong<double>(c->dim, c->p, static_cast<const double*>(xc), static_cast<double*>(yf), L.flags, Lc.g,
+                              L.g, c->xt, false, c->s));
+  else
+    CK(launch_prolong<float>(c->dim, c->p, static_cast<const float*>(xc), static_cast<float*>(yf), L.flags, Lc.g,
+                             L.g, c->xt, false, c->s));
+  return PFF_OK;
+}
+
+int pff_restrict(pff_ctx* c, int level, const void* xf, void* yc, int precision) {
+  if (!c || !xf || !yc || level < 0 || level + 1 >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  LevelData &L = c->lv[level], &Lc = c->lv[level + 1];
+  if (precision == 64)
+    CK(launch_restrict<double>(c->dim, c->p, static_cast<const double*>(xf), static_cast<double*>(yc), L.flags,
+                               Lc.flags, L.g, Lc.g, c->xt, c->s));
+  else
+    CK(launch_restrict<float>(c->dim, c->p, static_cast<const float*>(xf), static_cast<float*>(yc), L.flags,
+                              Lc.flags, L.g, Lc.g, c->xt, c->s));
+  return PFF_OK;
+}
+
+int pff_smooth(pff_ctx* c, int level, const void* f, void* x, int precision) {
+  if (!c || !f || !x || level < 0 || level >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  if (precision == 64) {
+    CR(ensure_work<double>(c, level));
+    LevelData& L = c->lv[level];
+    return smooth<double>(c, level, static_cast<const double*>(f), static_cast<double*>(x), L.w64[2], L.w64[4]);
+  }
+  CR(ensure_work<float>(c, level));
+  LevelData& L = c->lv[level];
+  return smooth<float>(c, level, static_cast<const float*>(f), static_cast<float*>(x), L.w32[2], L.w32[4]);
+}
+
+int pff_coarse_solve(pff_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z) return PFF_ERR_INVALID_ARG;
+  CR(mg_setup(c));
+  return coarse_solve64(c, r, z);
+}
+
+int pff_vcycle(pff_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z || r == z) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  return precondition(c, r, z);
+}
+
+int pff_solve_linear(pff_ctx* c, const double* b, double* x, int* iters, double* rel) {
+  if (!c || !b || !x || b == x) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  return fgmres(c, b, x, iters, rel);
+}
+
+int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  using clk = std::chrono::steady_clock;
+  auto ms = [](clk::time_point a, clk::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+  };
+  LevelData& L = c->lv[0];
+  pff_report r{};
+  CK(cudaStreamSynchronize(c->s));
+  const auto t0 = clk::now();
+  // Alg. 1: residual, active set (phi reset to phi_old on it), residual of the projected state
+  CR(residual_into(c, c->R));
+  CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
+  c->qp_valid = false;
+  c->mg_ready = false;
+  CR(residual_into(c, c->R));
+  CK(launch_newton_rhs(c->dim, L.nn, c->R, L.flags, c->rhs, c->s));
+  double r2;
+  CR(norm2_host(c, c->rhs, L.nd, &r2));
+  int cnt[2];
+  CK(cudaMemcpy(cnt, c->cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  r.res_norm = std::sqrt(r2);
+  r.n_active = cnt[0];
+  r.n_changed = cnt[1];
+  const auto t1 = clk::now();
+  CR(mg_setup(c));
+  CK(cudaStreamSynchronize(c->s));
+  const auto t2 = clk::now();
+  r.status = fgmres(c, c->rhs, c->dU, &r.gmres_iters, &r.gmres_rel);
+  if (r.status == PFF_OK || r.status == PFF_ERR_NOT_CONVERGED) {
+    CK(launch_axpby<double>(L.nd, 1.0, c->dU, 1.0, L.U, c->s));
+    c->qp_valid = false;
+    c->mg_ready = false;
+    if (U_out) CK(cudaMemcpyAsync(U_out, L.U, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  }
+  CK(cudaStreamSynchronize(c->s));
+  const auto t3 = clk::now();
+  r.t_residual_ms = ms(t0, t1);
+  r.t_setup_ms = ms(t1, t2);
+  r.t_solve_ms = ms(t2, t3);
+  if (rep) *rep = r;
+  return r.status;
+}
+
+int pff_param_grad(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
+  if (!c || !v) return PFF_ERR_INVALID_ARG;
+  CR(ensure_qp(c));
+  LevelData& L = c->lv[0];
+  if (!c->pgrad_tmp) {
+    const long long ncell = c->dim == 2 ? (long long)L.N * L.N : (long long)L.N * L.N * L.N;
+    const int nq = c->dim == 2 ? (c->p + 1) * (c->p + 1) : (c->p + 1) * (c->p + 1) * (c->p + 1);
+    CR(dalloc(c, &c->pgrad_tmp, 3 * ncell * nq));
+  }
+  MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+  // Dirichlet rows of the residual are identically zero: their test values do not enter
+  double* vm = c->scratch;
+  CK(launch_masked_copy(c->dim, L.nn, 1.0, v, L.flags, (1u << c->dim) - 1u, vm, c->s));
+  CK(launch_param_grad(c->dim, c->p, c->prm.split, L.U, vm, L.st64, L.g, L.t64, mc, c->pgrad_tmp, g_gc, g_lambda,
+                       g_mu, c->s));
+  return PFF_OK;
+}
+
+int pff_profile(pff_ctx* c, int family) {
+  if (!c || family < PFF_PROF_OFF || family > PFF_PROF_RESIDUAL) return PFF_ERR_INVALID_ARG;
+  if (family != PFF_PROF_OFF && c->ev.empty()) {
+    c->ev.resize(2 * PROF_MAX_LAUNCHES);
+    for (auto& e : c->ev) CK(cudaEventCreate(&e));
+  }
+  c->prof = family;
+  c->nev = 0;
+  return PFF_OK;
+}
+
+int pff_profile_result(pff_ctx* c, int* launches, double* total_ms) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->s));
+  double tot = 0.0;
+  for (int i = 0; i + 1 < c->nev; i += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    tot += ms;
+  }
+  if (launches) *launches = c->nev / 2;
+  if (total_ms) *total_ms = tot;
+  return PFF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// pff_common.cuh -- shared device definitions of the phase-field fracture library.
+//
+// Tables of the 1D Q_p basis at the Gauss points, the tile geometry of the cell-batched
+// operator kernels, the Mandel (orthonormal Voigt) representation of symmetric tensors, and
+// the pointwise constitutive laws of Sec. 2.1 (degradation g, Miehe split) and of the
+// eigen-derivative of Sec. 3.5 used by the tangent.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pff {
+
+constexpr int MAXP = 4;
+constexpr int MAXN = MAXP + 1;
+
+// Masking of inputs/outputs of the cell operator kernels.
+enum InMask { IN_RAW = 0, IN_ALL = 1, IN_DIRICHLET = 2 };
+enum OutMask { OUT_RAW = 0, OUT_IDENTITY = 1, OUT_ZERO_DIRICHLET = 2 };
+enum JacMode { JM_FULL = 0, JM_BLOCKDIAG = 1, JM_TRANSPOSE = 2 };
+
+// 1D tables on the unit interval: S[q][k] = l_k(x_q), D[q][k] = l_k'(x_q) / h at the Gauss
+// points x_q of the level, W[q] Gauss weights; JxW(q) = hd * prod_t W[q_t].
+template <typename Real>
+struct Tab {
+  Real S[MAXN][MAXN];
+  Real D[MAXN][MAXN];
+  Real W[MAXN];
+  Real hd;
+};
+
+// Tile shapes (cells per CTA) of the operator kernels, per dimension and degree.
+template <int DIM, int P>
+struct TileCfg;
+template <> struct TileCfg<2, 1> { static constexpr int TX = 8, TY = 8, TZ = 1; };
+template <> struct TileCfg<2, 2> { static constexpr int TX = 8, TY = 8, TZ = 1; };
+template <> struct TileCfg<2, 3> { static constexpr int TX = 4, TY = 4, TZ = 1; };
+template <> struct TileCfg<2, 4> { static constexpr int TX = 4, TY = 4, TZ = 1; };
+template <> struct TileCfg<3, 1> { static constexpr int TX = 4, TY = 4, TZ = 2; };
+template <> struct TileCfg<3, 2> { static constexpr int TX = 4, TY = 2, TZ = 2; };
+template <> struct TileCfg<3, 3> { static constexpr int TX = 2, TY = 2, TZ = 2; };
+template <> struct TileCfg<3, 4> { static constexpr int TX = 2, TY = 2, TZ = 1; };
+
+// Host-visible copy of the tile shapes (same numbers as TileCfg).
+inline void tile_shape(int dim, int p, int* t) {
+  static const int t2[4][3] = {{8, 8, 1}, {8, 8, 1}, {4, 4, 1}, {4, 4, 1}};
+  static const int t3[4][3] = {{4, 4, 2}, {4, 2, 2}, {2, 2, 2}, {2, 2, 1}};
+  const int(*tt)[3] = dim == 2 ? t2 : t3;
+  t[0] = tt[p - 1][0];
+  t[1] = tt[p - 1][1];
+  t[2] = tt[p - 1][2];
+}
+
+// Geometry of one level as the kernels see it.
+struct Geom {
+  int dim, p, N, n1;
+  long long nn;            // nodes
+  int tdim[3];             // cells per tile in x, y, z
+  int ntile[3];            // tiles per direction
+  int qpx, qpy, qpz;       // quadrature points of a tile per direction
+  long long qpt;           // quadrature points per tile
+  long long ntiles;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Mandel representation: a symmetric d x d tensor as an orthonormal vector of NM components,
+// 2D (11, 22, 12), 3D (11, 22, 33, 23, 13, 12), shear components scaled by sqrt(2).
+template <int DIM> struct Mandel;
+template <> struct Mandel<2> {
+  static constexpr int NM = 3;
+  __host__ __device__ static constexpr int ia(int m) { return m == 0 ? 0 : (m == 1 ? 1 : 0); }
+  __host__ __device__ static constexpr int ib(int m) { return m == 0 ? 0 : 1; }
+};
+template <> struct Mandel<3> {
+  static constexpr int NM = 6;
+  __host__ __device__ static constexpr int ia(int m) { return m < 3 ? m : (m == 3 ? 1 : 0); }
+  __host__ __device__ static constexpr int ib(int m) { return m < 3 ? m : (m == 5 ? 1 : 2); }
+};
+__host__ __device__ constexpr int sym_index(int nm, int i, int j) { return i * nm - i * (i - 1) / 2 + (j - i); }
+
+// Number of stored per-quadrature-point values of the Jacobian (all multiplied by JxW):
+//   split none : g(phi~) lambda, g(phi~) mu, b (NM), c, k
+//   split miehe: C (NM(NM+1)/2 upper triangle), b (NM), c, k
+// with b = g'(phi) sigma^+ (Mandel), c = g''(phi) E_s^+ + G_c / eps, k = G_c eps.
+__host__ __device__ constexpr int qp_nv(int dim, int split) {
+  return split == 0 ? (2 + (dim == 2 ? 3 : 6) + 2)
+                    : ((dim == 2 ? 6 : 21) + (dim == 2 ? 3 : 6) + 2);
+}
+constexpr int ST_NV = 4;  // per-point state for the residual: g(phi~), G_c, lambda, mu
+
+// ---------------------------------------------------------------------------------------------
+// Degradation (Sec. 2.1): g = (1 - kappa) phi^2 + kappa.
+__host__ __device__ inline double deg_g(double phi, double kappa) { return (1.0 - kappa) * phi * phi + kappa; }
+__host__ __device__ inline double deg_dg(double phi, double kappa) { return 2.0 * (1.0 - kappa) * phi; }
+__host__ __device__ inline double deg_ddg(double kappa) { return 2.0 * (1.0 - kappa); }
+__host__ __device__ inline double heav(double x) { return x >= 0.0 ? 1.0 : 0.0; }
+__host__ __device__ inline double pos(double x) { return x > 0.0 ? x : 0.0; }
+
+// Divided difference of x -> max(x, 0) at (a, b); H(a) when a == b.
+__device__ inline double theta_dd(double a, double b) {
+  return a == b ? heav(a) : (pos(a) - pos(b)) / (a - b);
+}
+
+// Eigen-decomposition of a symmetric 2x2 [[a, b], [b, c]]: l[0] >= l[1], columns of V.
+__device__ inline void eig_sym2(double a, double b, double c, double l[2], double V[2][2]) {
+  const double m = 0.5 * (a + c), dd = 0.5 * (a - c);
+  const double r = hypot(dd, b);
+  l[0] = m + r;
+  l[1] = m - r;
+  double cs = 1.0, sn = 0.0;
+  if (r > 0.0) {
+    // half-angle of (cos 2t, sin 2t) = (dd, b) / r
+    const double c2 = dd / r, s2 = b / r;
+    if (c2 >= 0.0) {
+      cs = sqrt(0.5 * (1.0 + c2));
+      sn = s2 / (2.0 * cs);
+    } else {
+      sn = sqrt(0.5 * (1.0 - c2));
+      if (s2 < 0.0) sn = -sn;
+      cs = s2 / (2.0 * sn);
+    }
+  }
+  V[0][0] = cs;  V[1][0] = sn;   // v1
+  V[0][1] = -sn; V[1][1] = cs;   // v2
+}
+
+// Eigen-decomposition of a symmetric 3x3 by cyclic Jacobi rotations (A is overwritten).
+// Columns of V are the eigenvectors, l the eigenvalues (unsorted).
+__device__ inline void eig_sym3(double A[3][3], double l[3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off == 0.0 || off <= 1e-36 * dia) break;
+    for (int pi = 0; pi < 3; ++pi) {
+      const int p = pi == 2 ? 1 : 0;
+      const int q = pi == 0 ? 1 : 2;
+      const double apq = A[p][q];
+      if (apq == 0.0) continue;
+      const double th = (A[q][q] - A[p][p]) / (2.0 * apq);
+      double t;
+      if (fabs(th) > 1e150) t = 0.5 / th;
+      else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+      A[p][p] -= t * apq;
+      A[q][q] += t * apq;
+      A[p][q] = A[q][p] = 0.0;
+      const int r = 3 - p - q;
+      const double arp = A[r][p], arq = A[r][q];
+      A[r][p] = A[p][r] = c * arp - s * arq;
+      A[r][q] = A[q][r] = s * arp + c * arq;
+      for (int k = 0; k < 3; ++k) {
+        const double vp = V[k][p], vq = V[k][q];
+        V[k][p] = c * vp - s * vq;
+        V[k][q] = s * vp + c * vq;
+      }
+    }
+  }
+  l[0] = A[0][0];
+  l[1] = A[1][1];
+  l[2] = A[2][2];
+}
+
+// Eigen system of a symmetric strain given as a full d x d array.
+template <int DIM>
+__device__ inline void eig_sym(const double e[DIM][DIM], double l[DIM], double V[DIM][DIM]) {
+  if constexpr (DIM == 2) {
+    eig_sym2(e[0][0], 0.5 * (e[0][1] + e[1][0]), e[1][1], l, V);
+  } else {
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A[i][j] = 0.5 * (e[i][j] + e[j][i]);
+    eig_sym3(A, l, V);
+  }
+}
+
+// Eigenvalues (and the trace) of magnitude at most 1e-12 times the largest eigenvalue magnitude
+// are set to exactly 0: their sign is rounding noise and must not flip H or the tangent.
+template <int DIM>
+__device__ inline void snap_zero(double l[DIM], double& tr) {
+  double sc = 0.0;
+  for (int t = 0; t < DIM; ++t) sc = fmax(sc, fabs(l[t]));
+  const double tol = 1e-12 * sc;
+  for (int t = 0; t < DIM; ++t)
+    if (fabs(l[t]) <= tol) l[t] = 0.0;
+  if (fabs(tr) <= tol) tr = 0.0;
+}
+
+// Mandel vector of (a b^T + b a^T)/2 scaled: E_ii for a == b, E_ij = (a b^T + b a^T)/sqrt2.
+template <int DIM>
+__device__ inline void mandel_dyad(const double* a, const double* b, bool same, double* out) {
+  constexpr int NM = Mandel<DIM>::NM;
+  const double S2 = 1.4142135623730951;
+  for (int m = 0; m < NM; ++m) {
+    const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+    if (same) {
+      out[m] = (i == j) ? a[i] * a[i] : S2 * a[i] * a[j];
+    } else {
+      out[m] = (i == j) ? S2 * a[i] * b[i] : (a[i] * b[j] + a[j] * b[i]);
+    }
+  }
+}
+
+}  // namespace pff

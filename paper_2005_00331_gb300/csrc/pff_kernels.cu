@@ -1,0 +1,1299 @@
+// pff_kernels.cu -- per-point setup, diagonal, parameter gradient, coarse assembly, transfers,
+// vector, Chebyshev, CG-Lanczos and Newton-step kernels of libpff.
+#include <cstdint>
+#include "pff_kernels.h"
+#include "pff_op.cuh"
+
+namespace pff {
+
+namespace {
+
+constexpr int BLK = 256;
+constexpr double RS2 = 0.70710678118654752440;
+
+inline unsigned grid_for(long long n, int blk = BLK) {
+  long long g = (n + blk - 1) / blk;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <int DIM>
+__host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
+
+// Cell, quadrature-point and tile bookkeeping shared by the direct (one thread per point) kernels.
+template <int DIM, int P>
+struct CellQP {
+  int c[3], q[3];
+  long long tile, qidx;
+  __device__ void set(long long cell, int qq, const Geom& g) {
+    constexpr int n = P + 1;
+    c[0] = int(cell % g.N);
+    c[1] = int((cell / g.N) % g.N);
+    c[2] = DIM == 3 ? int(cell / ((long long)g.N * g.N)) : 0;
+    q[0] = qq % n;
+    q[1] = (qq / n) % n;
+    q[2] = DIM == 3 ? qq / (n * n) : 0;
+    const int TX = TileCfg<DIM, P>::TX, TY = TileCfg<DIM, P>::TY, TZ = TileCfg<DIM, P>::TZ;
+    const int tx = c[0] / TX, ty = c[1] / TY, tz = c[2] / TZ;
+    const int lx = c[0] % TX, ly = c[1] % TY, lz = c[2] % TZ;
+    tile = tx + (long long)g.ntile[0] * (ty + (long long)g.ntile[1] * tz);
+    qidx = ((long long)(lz * n + q[2]) * g.qpy + (ly * n + q[1])) * g.qpx + (lx * n + q[0]);
+  }
+  __device__ long long node(int a, const Geom& g) const {
+    constexpr int n = P + 1;
+    const int ax = a % n, ay = (a / n) % n, az = DIM == 3 ? a / (n * n) : 0;
+    long long nd = (c[0] * P + ax) + (long long)g.n1 * (c[1] * P + ay);
+    if (DIM == 3) nd += (long long)g.n1 * g.n1 * (c[2] * P + az);
+    return nd;
+  }
+  // N_a and grad N_a at this point
+  __device__ void shape(int a, const Tab<double>& tb, double& N, double dN[DIM]) const {
+    constexpr int n = P + 1;
+    const int aa[3] = {a % n, (a / n) % n, DIM == 3 ? a / (n * n) : 0};
+    N = 1.0;
+    for (int t = 0; t < DIM; ++t) dN[t] = 1.0;
+    for (int s = 0; s < DIM; ++s) {
+      const double Sv = tb.S[q[s]][aa[s]], Dv = tb.D[q[s]][aa[s]];
+      N *= Sv;
+      for (int t = 0; t < DIM; ++t) dN[t] *= (t == s ? Dv : Sv);
+    }
+  }
+  __device__ double jxw(const Tab<double>& tb) const {
+    double w = tb.hd;
+    for (int s = 0; s < DIM; ++s) w *= tb.W[q[s]];
+    return w;
+  }
+};
+
+// Evaluates a DoF vector (u, phi) at the point: grad u, phi, grad phi.
+template <int DIM, int P>
+__device__ void eval_state(const CellQP<DIM, P>& cq, const double* U, const Geom& g, const Tab<double>& tb,
+                           double gu[DIM][DIM], double& ph, double gph[DIM]) {
+  constexpr int NA = ipow<DIM>(P + 1);
+  for (int k = 0; k < DIM; ++k)
+    for (int j = 0; j < DIM; ++j) gu[k][j] = 0.0;
+  ph = 0.0;
+  for (int j = 0; j < DIM; ++j) gph[j] = 0.0;
+  for (int a = 0; a < NA; ++a) {
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    const long long nd = cq.node(a, g);
+    for (int k = 0; k < DIM; ++k) {
+      const double uk = U[k * g.nn + nd];
+      for (int j = 0; j < DIM; ++j) gu[k][j] += uk * dN[j];
+    }
+    const double pv = U[DIM * g.nn + nd];
+    ph += pv * N;
+    for (int j = 0; j < DIM; ++j) gph[j] += pv * dN[j];
+  }
+}
+
+template <int DIM, int P>
+__device__ double eval_scalar(const CellQP<DIM, P>& cq, const double* f, const Geom& g, const Tab<double>& tb) {
+  constexpr int NA = ipow<DIM>(P + 1);
+  double v = 0.0;
+  for (int a = 0; a < NA; ++a) {
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    v += f[cq.node(a, g)] * N;
+  }
+  return v;
+}
+
+}  // namespace
+
+// ===========================================================================================
+// Per-point data of the Jacobian: tangent of g(phi~) sigma^+ + sigma^- (Sec. 2.1, 3.5), the
+// coupling g'(phi) sigma^+ and the phase-field coefficients, times JxW (see qp_nv).
+template <int DIM, int P, int SPLIT>
+__global__ void k_qp_setup(const double* __restrict__ U, const double* __restrict__ phit,
+                           const double* __restrict__ gcf, const double* __restrict__ lamf,
+                           const double* __restrict__ muf, Geom g, Tab<double> tb, MatConst mc,
+                           double* __restrict__ qp64, float* __restrict__ qp32, double* __restrict__ st64) {
+  constexpr int NQ = ipow<DIM>(P + 1);
+  constexpr int NM = Mandel<DIM>::NM;
+  constexpr int NV = qp_nv(DIM, SPLIT);
+  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell * NQ) return;
+  CellQP<DIM, P> cq;
+  cq.set(t / NQ, int(t % NQ), g);
+  double gu[DIM][DIM], ph, gph[DIM];
+  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
+  const double pt = eval_scalar<DIM, P>(cq, phit, g, tb);
+  const double gc = gcf ? eval_scalar<DIM, P>(cq, gcf, g, tb) : mc.gc;
+  const double lam = lamf ? eval_scalar<DIM, P>(cq, lamf, g, tb) : mc.lambda;
+  const double mu = muf ? eval_scalar<DIM, P>(cq, muf, g, tb) : mc.mu;
+  const double jxw = cq.jxw(tb);
+  const double gt = deg_g(pt, mc.kappa), dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
+
+  double e[DIM][DIM], tr = 0.0;
+  for (int i = 0; i < DIM; ++i) {
+    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
+    tr += e[i][i];
+  }
+  double em[NM];
+  for (int m = 0; m < NM; ++m) {
+    const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+    em[m] = (i == j) ? e[i][i] : e[i][j] / RS2;
+  }
+  double vals[NV];
+  if constexpr (SPLIT == 0) {
+    double ee = 0.0;
+    for (int m = 0; m < NM; ++m) ee += em[m] * em[m];
+    const double Es = 0.5 * lam * tr * tr + mu * ee;
+    vals[0] = gt * lam * jxw;
+    vals[1] = gt * mu * jxw;
+    for (int m = 0; m < NM; ++m) vals[2 + m] = dgp * (2.0 * mu * em[m] + (m < DIM ? lam * tr : 0.0)) * jxw;
+    vals[2 + NM] = (ddg * Es + gc / mc.eps) * jxw;
+    vals[3 + NM] = gc * mc.eps * jxw;
+  } else {
+    double l[DIM], V[DIM][DIM];
+    eig_sym<DIM>(e, l, V);
+    double trs = tr;
+    snap_zero<DIM>(l, trs);
+    const double H = heav(trs), trp = pos(trs);
+    double sl2 = 0.0;
+    for (int t2 = 0; t2 < DIM; ++t2) sl2 += pos(l[t2]) * pos(l[t2]);
+    const double Esp = 0.5 * lam * trp * trp + mu * sl2;
+    // P+ = sum_i H(l_i) E_ii E_ii^T + sum_{i<j} theta_ij E_ij E_ij^T (orthonormal Mandel basis)
+    double Pp[NM][NM];
+    for (int a = 0; a < NM; ++a)
+      for (int b = 0; b < NM; ++b) Pp[a][b] = 0.0;
+    double epm[NM];
+    for (int m = 0; m < NM; ++m) epm[m] = 0.0;
+    for (int i = 0; i < DIM; ++i) {
+      for (int j = i; j < DIM; ++j) {
+        double vi[DIM], vj[DIM], Em[NM];
+        for (int k = 0; k < DIM; ++k) {
+          vi[k] = V[k][i];
+          vj[k] = V[k][j];
+        }
+        mandel_dyad<DIM>(vi, vj, i == j, Em);
+        const double th = (i == j) ? heav(l[i]) : theta_dd(l[i], l[j]);
+        for (int a = 0; a < NM; ++a)
+          for (int b = 0; b < NM; ++b) Pp[a][b] += th * Em[a] * Em[b];
+        if (i == j)
+          for (int m = 0; m < NM; ++m) epm[m] += pos(l[i]) * Em[m];
+      }
+    }
+    const double aH = gt * H + 1.0 - H;
+    int o = 0;
+    for (int a = 0; a < NM; ++a)
+      for (int b = a; b < NM; ++b) {
+        double Cab = 2.0 * mu * ((a == b ? 1.0 : 0.0) + (gt - 1.0) * Pp[a][b]);
+        if (a < DIM && b < DIM) Cab += lam * aH;
+        vals[o++] = Cab * jxw;
+      }
+    for (int m = 0; m < NM; ++m) vals[o + m] = dgp * (2.0 * mu * epm[m] + (m < DIM ? lam * trp : 0.0)) * jxw;
+    vals[o + NM] = (ddg * Esp + gc / mc.eps) * jxw;
+    vals[o + NM + 1] = gc * mc.eps * jxw;
+  }
+  const long long base = cq.tile * NV * g.qpt + cq.qidx;
+  for (int v = 0; v < NV; ++v) {
+    qp64[base + v * g.qpt] = vals[v];
+    if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
+  }
+  if (st64) {
+    const long long sb = cq.tile * ST_NV * g.qpt + cq.qidx;
+    st64[sb] = gt;
+    st64[sb + g.qpt] = gc;
+    st64[sb + 2 * g.qpt] = lam;
+    st64[sb + 3 * g.qpt] = mu;
+  }
+}
+
+cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
+                            const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
+                            const MatConst& mc, double* qp64, float* qp32, double* st64, cudaStream_t s) {
+  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
+  const unsigned gr = grid_for(tot, 128);
+#define PFF_CASE(DD, PP, SS)                                                                          \
+  if (dim == DD && p == PP && split == SS) {                                                          \
+    k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, st64); \
+    return cudaGetLastError();                                                                        \
+  }
+  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
+  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
+  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
+  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
+#undef PFF_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ===========================================================================================
+// Diagonal of diag(G_uu, G_phiphi): for a basis function N_a e_k the quadratic form
+// e(N_a e_k) : C_eff : e(N_a e_k), and c N_a^2 + k |grad N_a|^2 for the phase field.
+template <int DIM, int P, int SPLIT>
+__global__ void k_diagonal(const double* __restrict__ qp64, Geom g, Tab<double> tb, double* __restrict__ d64) {
+  constexpr int NA = ipow<DIM>(P + 1), NQ = NA;
+  constexpr int NM = Mandel<DIM>::NM;
+  constexpr int NV = qp_nv(DIM, SPLIT);
+  constexpr int OFFB = SPLIT == 0 ? 2 : NM * (NM + 1) / 2;
+  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell * NA) return;
+  const long long cell = t / NA;
+  const int a = int(t % NA);
+  double acc[DIM + 1];
+  for (int f = 0; f <= DIM; ++f) acc[f] = 0.0;
+  CellQP<DIM, P> cq;
+  long long nd = 0;
+  for (int q = 0; q < NQ; ++q) {
+    cq.set(cell, q, g);
+    if (q == 0) nd = cq.node(a, g);
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    const double* v = qp64 + cq.tile * NV * g.qpt + cq.qidx;
+    for (int k = 0; k < DIM; ++k) {
+      double em[NM];
+      for (int m = 0; m < NM; ++m) {
+        const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+        if (i == j) em[m] = (i == k) ? dN[k] : 0.0;
+        else em[m] = (i == k ? dN[j] : (j == k ? dN[i] : 0.0)) * RS2;
+      }
+      double val = 0.0;
+      if constexpr (SPLIT == 0) {
+        double ee = 0.0;
+        for (int m = 0; m < NM; ++m) ee += em[m] * em[m];
+        val = v[0] * dN[k] * dN[k] + 2.0 * v[g.qpt] * ee;
+      } else {
+        for (int i = 0; i < NM; ++i)
+          for (int j = i; j < NM; ++j) {
+            const double cij = v[sym_index(NM, i, j) * g.qpt];
+            val += (i == j ? 1.0 : 2.0) * cij * em[i] * em[j];
+          }
+      }
+      acc[k] += val;
+    }
+    double gg = 0.0;
+    for (int j = 0; j < DIM; ++j) gg += dN[j] * dN[j];
+    acc[DIM] += v[(OFFB + NM) * g.qpt] * N * N + v[(OFFB + NM + 1) * g.qpt] * gg;
+  }
+  for (int f = 0; f <= DIM; ++f) atomicAdd(d64 + f * g.nn + nd, acc[f]);
+}
+
+__global__ void k_diag_finish(long long n, long long nn, const unsigned char* __restrict__ flags,
+                              double* __restrict__ d64, float* __restrict__ d32) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int f = int(e / nn);
+  const long long nd = e % nn;
+  double v = d64[e];
+  if ((flags[nd] >> f) & 1u) v = 1.0;
+  d64[e] = v;
+  if (d32) d32[e] = (float)v;
+}
+
+cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const unsigned char* flags,
+                            const Geom& g, const Tab<double>& tb, double* d64, float* d32, cudaStream_t s) {
+  const long long n = (dim + 1) * g.nn;
+  cudaError_t e = cudaMemsetAsync(d64, 0, sizeof(double) * n, s);
+  if (e != cudaSuccess) return e;
+  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
+  const unsigned gr = grid_for(tot, 128);
+  bool done = false;
+#define PFF_CASE(DD, PP, SS)                                                   \
+  if (!done && dim == DD && p == PP && split == SS) {                         \
+    k_diagonal<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, d64);              \
+    done = true;                                                               \
+  }
+  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
+  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
+  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
+  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
+#undef PFF_CASE
+  if (!done) return cudaErrorInvalidValue;
+  k_diag_finish<<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d64, d32);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Parameter gradients: per point the partial derivatives of the residual's pointwise terms with
+// respect to G_c, lambda, mu, contracted with the test function v; then integrated against N_a.
+template <int DIM, int P, int SPLIT>
+__global__ void k_pgrad_qp(const double* __restrict__ U, const double* __restrict__ v,
+                           const double* __restrict__ st64, Geom g, Tab<double> tb, MatConst mc,
+                           double* __restrict__ tmp) {
+  constexpr int NQ = ipow<DIM>(P + 1);
+  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell * NQ) return;
+  CellQP<DIM, P> cq;
+  cq.set(t / NQ, int(t % NQ), g);
+  double gu[DIM][DIM], ph, gph[DIM], gv[DIM][DIM], vph, gvph[DIM];
+  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
+  eval_state<DIM, P>(cq, v, g, tb, gv, vph, gvph);
+  const double gt = st64[cq.tile * ST_NV * g.qpt + cq.qidx];
+  const double jxw = cq.jxw(tb);
+  const double dgp = deg_dg(ph, mc.kappa);
+  double e[DIM][DIM], tr = 0.0, divv = 0.0;
+  for (int i = 0; i < DIM; ++i) {
+    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
+    tr += e[i][i];
+    divv += gv[i][i];
+  }
+  double gpgv = 0.0;
+  for (int j = 0; j < DIM; ++j) gpgv += gph[j] * gvph[j];
+  const double s_gc = -(1.0 - ph) / mc.eps * vph + mc.eps * gpgv;
+  double ep[DIM][DIM];
+  double trp;
+  if constexpr (SPLIT == 0) {
+    trp = tr;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) ep[i][j] = e[i][j];
+  } else {
+    double l[DIM], V[DIM][DIM];
+    eig_sym<DIM>(e, l, V);
+    double trs = tr;
+    snap_zero<DIM>(l, trs);
+    trp = pos(trs);
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < DIM; ++k) s += pos(l[k]) * V[i][k] * V[j][k];
+        ep[i][j] = s;
+      }
+  }
+  // lambda: sigma+ = trp I, sigma- = (tr - trp) I, E+ = trp^2/2
+  const double s_lam = (gt * trp + (tr - trp)) * divv + dgp * 0.5 * trp * trp * vph;
+  // mu: sigma+ = 2 e+, sigma- = 2 (e - e+), E+ = e+ : e+
+  double s_mu = 0.0, epep = 0.0;
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) {
+      s_mu += (gt * 2.0 * ep[i][j] + 2.0 * (e[i][j] - ep[i][j])) * gv[i][j];
+      epep += ep[i][j] * ep[i][j];
+    }
+  s_mu += dgp * epep * vph;
+  tmp[t] = s_gc * jxw;
+  tmp[ncell * NQ + t] = s_lam * jxw;
+  tmp[2 * ncell * NQ + t] = s_mu * jxw;
+}
+
+template <int DIM, int P>
+__global__ void k_pgrad_int(const double* __restrict__ tmp, Geom g, Tab<double> tb, double* __restrict__ o0,
+                            double* __restrict__ o1, double* __restrict__ o2) {
+  constexpr int NA = ipow<DIM>(P + 1), NQ = NA;
+  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell * NA) return;
+  const long long cell = t / NA;
+  const int a = int(t % NA);
+  double acc[3] = {0.0, 0.0, 0.0};
+  CellQP<DIM, P> cq;
+  long long nd = 0;
+  for (int q = 0; q < NQ; ++q) {
+    cq.set(cell, q, g);
+    if (q == 0) nd = cq.node(a, g);
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    for (int k = 0; k < 3; ++k) acc[k] += N * tmp[k * ncell * NQ + cell * NQ + q];
+  }
+  if (o0) atomicAdd(o0 + nd, acc[0]);
+  if (o1) atomicAdd(o1 + nd, acc[1]);
+  if (o2) atomicAdd(o2 + nd, acc[2]);
+}
+
+cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const double* v, const double* st64,
+                              const Geom& g, const Tab<double>& tb, const MatConst& mc, double* tmp,
+                              double* out_gc, double* out_lam, double* out_mu, cudaStream_t s) {
+  for (double* o : {out_gc, out_lam, out_mu}) {
+    if (o) {
+      cudaError_t e = cudaMemsetAsync(o, 0, sizeof(double) * g.nn, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
+  const unsigned gr = grid_for(tot, 128);
+  bool done = false;
+#define PFF_CASE(DD, PP, SS)                                                                  \
+  if (!done && dim == DD && p == PP && split == SS) {                                        \
+    k_pgrad_qp<DD, PP, SS><<<gr, 128, 0, s>>>(U, v, st64, g, tb, mc, tmp);                   \
+    k_pgrad_int<DD, PP><<<gr, 128, 0, s>>>(tmp, g, tb, out_gc, out_lam, out_mu);             \
+    done = true;                                                                              \
+  }
+  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
+  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
+  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
+  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
+#undef PFF_CASE
+  return done ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+// ===========================================================================================
+// Dense coarse operator: element matrices from the stored per-point data, one thread per
+// (cell, test DoF, trial DoF), accumulated into the u-u, phi-phi and phi-u blocks.
+template <int DIM, int P, int SPLIT>
+__global__ void k_coarse_asm(const double* __restrict__ qp64, Geom g, Tab<double> tb, double* __restrict__ Au,
+                             double* __restrict__ Ap, double* __restrict__ B) {
+  constexpr int NA = ipow<DIM>(P + 1), NQ = NA, NL = (DIM + 1) * NA;
+  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncell * NL * NL) return;
+  const long long cell = t / (NL * NL);
+  const int i = int((t / NL) % NL), j = int(t % NL);
+  const int fi = i / NA, a = i % NA, fj = j / NA, b = j % NA;
+  if (fi < DIM && fj == DIM) return;  // G_uphi = 0
+  PWJac<DIM, double, SPLIT> pw;
+  pw.qp = qp64;
+  pw.qpt = g.qpt;
+  pw.tstride = (long long)qp_nv(DIM, SPLIT) * g.qpt;
+  pw.mode = JM_FULL;
+  CellQP<DIM, P> cq;
+  double val = 0.0;
+  long long na_ = 0, nb_ = 0;
+  for (int q = 0; q < NQ; ++q) {
+    cq.set(cell, q, g);
+    if (q == 0) {
+      na_ = cq.node(a, g);
+      nb_ = cq.node(b, g);
+    }
+    double Na, dNa[DIM], Nb, dNb[DIM];
+    cq.shape(a, tb, Na, dNa);
+    cq.shape(b, tb, Nb, dNb);
+    QPIn<DIM, double> in;
+    for (int k = 0; k < DIM; ++k)
+      for (int m = 0; m < DIM; ++m) in.gu[k][m] = (k == fj) ? dNb[m] : 0.0;
+    in.ph = (fj == DIM) ? Nb : 0.0;
+    for (int m = 0; m < DIM; ++m) in.gph[m] = (fj == DIM) ? dNb[m] : 0.0;
+    QPOut<DIM, double> o;
+    pw(cq.tile, cq.qidx, in, o);
+    if (fi < DIM) {
+      for (int m = 0; m < DIM; ++m) val += o.cu[fi][m] * dNa[m];
+    } else {
+      val += o.cv * Na;
+      for (int m = 0; m < DIM; ++m) val += o.cg[m] * dNa[m];
+    }
+  }
+  const long long nn = g.nn, nu = DIM * nn;
+  if (fi < DIM && fj < DIM) atomicAdd(Au + (fi * nn + na_) * nu + (fj * nn + nb_), val);
+  else if (fi == DIM && fj == DIM) atomicAdd(Ap + na_ * nn + nb_, val);
+  else atomicAdd(B + na_ * nu + (fj * nn + nb_), val);
+}
+
+__global__ void k_coarse_mask(int dim, long long nn, const unsigned char* __restrict__ flags, double* Au, double* Ap,
+                              double* B) {
+  const long long nu = dim * nn;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // rows/cols of Au
+  if (t < nu * nu) {
+    const long long r = t / nu, c = t % nu;
+    const bool mr = (flags[r % nn] >> (r / nn)) & 1u, mc = (flags[c % nn] >> (c / nn)) & 1u;
+    if (mr || mc) Au[t] = (r == c) ? 1.0 : 0.0;
+  }
+  if (t < nn * nn) {
+    const long long r = t / nn, c = t % nn;
+    const bool mr = (flags[r] >> dim) & 1u, mc = (flags[c] >> dim) & 1u;
+    if (mr || mc) Ap[t] = (r == c) ? 1.0 : 0.0;
+  }
+  if (t < nn * nu) {
+    const long long r = t / nu, c = t % nu;
+    const bool mr = (flags[r] >> dim) & 1u, mc = (flags[c % nn] >> (c / nn)) & 1u;
+    if (mr || mc) B[t] = 0.0;
+  }
+}
+
+cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64, const unsigned char* flags,
+                                   const Geom& g, const Tab<double>& tb, double* Au, double* Ap, double* B,
+                                   cudaStream_t s) {
+  const long long nn = g.nn, nu = dim * nn;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(Au, 0, sizeof(double) * nu * nu, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(Ap, 0, sizeof(double) * nn * nn, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(B, 0, sizeof(double) * nn * nu, s)) != cudaSuccess) return e;
+  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
+  const int na = dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
+  const long long nl = (dim + 1) * na;
+  const unsigned gr = grid_for(ncell * nl * nl, 128);
+  bool done = false;
+#define PFF_CASE(DD, PP, SS)                                             \
+  if (!done && dim == DD && p == PP && split == SS) {                   \
+    k_coarse_asm<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, Au, Ap, B); \
+    done = true;                                                         \
+  }
+  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
+  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
+  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
+  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
+#undef PFF_CASE
+  if (!done) return cudaErrorInvalidValue;
+  k_coarse_mask<<<grid_for(nu * nu), BLK, 0, s>>>(dim, nn, flags, Au, Ap, B);
+  return cudaGetLastError();
+}
+
+// In-place Gauss-Jordan inversion, one elimination step per pair of launches.
+__global__ void k_gj_save(double* __restrict__ A, int n, int k, double* __restrict__ buf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  buf[i] = A[(long long)i * n + k];
+  buf[n + i] = A[(long long)k * n + i];
+}
+__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ buf) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double piv = buf[n + k];
+  double* aij = A + (long long)i * n + j;
+  if (i == k) *aij = (j == k) ? 1.0 / piv : buf[n + j] / piv;
+  else if (j == k) *aij = -buf[i] / piv;
+  else *aij -= buf[i] * buf[n + j] / piv;
+}
+
+cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s) {
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  for (int k = 0; k < n; ++k) {
+    k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, k, buf);
+    k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf);
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_gemv(const double* __restrict__ A, int n, int m, const double* __restrict__ x,
+                       double* __restrict__ y, double alpha, double beta) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = A + (long long)warp * m;
+  double s = 0.0;
+  for (int j = lane; j < m; j += 32) s += row[j] * x[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[warp] = (beta == 0.0 ? 0.0 : beta * y[warp]) + alpha * s;
+}
+
+cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
+                        cudaStream_t s) {
+  k_gemv<<<grid_for((long long)n * 32), BLK, 0, s>>>(A, n, m, x, y, alpha, beta);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Transfers between a coarse level (Nc cells) and its fine level (2 Nc cells), same degree.
+template <int DIM, int P, typename Real>
+__global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, const unsigned char* __restrict__ flf,
+                          Geom gc, Geom gf, XferTab xt, int accumulate) {
+  const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (nd >= gf.nn) return;
+  long long rem = nd;
+  int C[3] = {0, 0, 0}, o[3] = {0, 0, 0};
+  for (int t = 0; t < DIM; ++t) {
+    const int i = int(rem % gf.n1);
+    rem /= gf.n1;
+    int c = i / (2 * P);
+    if (c > gc.N - 1) c = gc.N - 1;
+    C[t] = c;
+    o[t] = i - 2 * P * c;
+  }
+  const unsigned char fl = flf[nd];
+  for (int f = 0; f <= DIM; ++f) {
+    double v = 0.0;
+    if (!((fl >> f) & 1u)) {
+      if constexpr (DIM == 2) {
+        for (int ky = 0; ky <= P; ++ky) {
+          const double wy = xt.E[o[1]][ky];
+          if (wy == 0.0) continue;
+          const Real* row = xc + f * gc.nn + (long long)(C[1] * P + ky) * gc.n1 + C[0] * P;
+          double sx = 0.0;
+          for (int kx = 0; kx <= P; ++kx) sx += xt.E[o[0]][kx] * (double)row[kx];
+          v += wy * sx;
+        }
+      } else {
+        for (int kz = 0; kz <= P; ++kz) {
+          const double wz = xt.E[o[2]][kz];
+          if (wz == 0.0) continue;
+          for (int ky = 0; ky <= P; ++ky) {
+            const double wy = xt.E[o[1]][ky];
+            if (wy == 0.0) continue;
+            const Real* row = xc + f * gc.nn + ((long long)(C[2] * P + kz) * gc.n1 + (C[1] * P + ky)) * gc.n1 + C[0] * P;
+            double sx = 0.0;
+            for (int kx = 0; kx <= P; ++kx) sx += xt.E[o[0]][kx] * (double)row[kx];
+            v += wz * wy * sx;
+          }
+        }
+      }
+    }
+    Real* y = yf + f * gf.nn + nd;
+    *y = accumulate ? Real((double)*y + v) : Real(v);
+  }
+}
+
+template <int DIM, int P, typename Real>
+__global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
+                           const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt) {
+  const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (nd >= gc.nn) return;
+  constexpr int MAXL = 2 * (2 * P + 1);
+  int fi[3][MAXL];
+  double fw[3][MAXL];
+  int cnt[3] = {0, 0, 0};
+  long long rem = nd;
+  for (int t = 0; t < DIM; ++t) {
+    const int J = int(rem % gc.n1);
+    rem /= gc.n1;
+    int clo = (J % P == 0) ? J / P - 1 : J / P, chi = J / P;
+    if (clo < 0) clo = 0;
+    if (chi > gc.N - 1) chi = gc.N - 1;
+    for (int c = clo; c <= chi; ++c) {
+      const int k = J - c * P;
+      for (int o = 0; o <= 2 * P; ++o) {
+        if (o == 2 * P && c != gc.N - 1) continue;  // owned by the next coarse cell
+        const double w = xt.E[o][k];
+        if (w == 0.0) continue;
+        fi[t][cnt[t]] = 2 * P * c + o;
+        fw[t][cnt[t]] = w;
+        ++cnt[t];
+      }
+    }
+  }
+  const unsigned char fc = flc[nd];
+  for (int f = 0; f <= DIM; ++f) {
+    double v = 0.0;
+    if (!((fc >> f) & 1u)) {
+      if constexpr (DIM == 2) {
+        for (int b = 0; b < cnt[1]; ++b)
+          for (int a = 0; a < cnt[0]; ++a) {
+            const long long fn = fi[0][a] + (long long)gf.n1 * fi[1][b];
+            if (!((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * (double)xf[f * gf.nn + fn];
+          }
+      } else {
+        for (int c = 0; c < cnt[2]; ++c)
+          for (int b = 0; b < cnt[1]; ++b)
+            for (int a = 0; a < cnt[0]; ++a) {
+              const long long fn = fi[0][a] + (long long)gf.n1 * (fi[1][b] + (long long)gf.n1 * fi[2][c]);
+              if (!((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * fw[2][c] * (double)xf[f * gf.nn + fn];
+            }
+      }
+    }
+    yc[f * gc.nn + nd] = Real(v);
+  }
+}
+
+template <typename Real>
+cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f, const Geom& gc,
+                           const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s) {
+  const unsigned gr = grid_for(gf.nn);
+#define PFF_CASE(DD, PP)                                                                            \
+  if (dim == DD && p == PP) {                                                                       \
+    k_prolong<DD, PP, Real><<<gr, BLK, 0, s>>>(xc, yf, flags_f, gc, gf, xt, accumulate ? 1 : 0); \
+    return cudaGetLastError();                                                                      \
+  }
+  PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
+  PFF_CASE(3, 1) PFF_CASE(3, 2) PFF_CASE(3, 3) PFF_CASE(3, 4)
+#undef PFF_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
+                            const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
+                            cudaStream_t s) {
+  const unsigned gr = grid_for(gc.nn, 128);
+#define PFF_CASE(DD, PP)                                                                  \
+  if (dim == DD && p == PP) {                                                             \
+    k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt);  \
+    return cudaGetLastError();                                                            \
+  }
+  PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
+  PFF_CASE(3, 1) PFF_CASE(3, 2) PFF_CASE(3, 3) PFF_CASE(3, 4)
+#undef PFF_CASE
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_prolong<double>(int, int, const double*, double*, const unsigned char*, const Geom&,
+                                            const Geom&, const XferTab&, bool, cudaStream_t);
+template cudaError_t launch_prolong<float>(int, int, const float*, float*, const unsigned char*, const Geom&,
+                                           const Geom&, const XferTab&, bool, cudaStream_t);
+template cudaError_t launch_restrict<double>(int, int, const double*, double*, const unsigned char*,
+                                             const unsigned char*, const Geom&, const Geom&, const XferTab&,
+                                             cudaStream_t);
+template cudaError_t launch_restrict<float>(int, int, const float*, float*, const unsigned char*,
+                                            const unsigned char*, const Geom&, const Geom&, const XferTab&,
+                                            cudaStream_t);
+
+// Fine FE function evaluated at the coarse nodes (carries the state to coarse levels).
+__global__ void k_state_interp(int dim, int p, const double* __restrict__ xf, double* __restrict__ yc, int nfields,
+                               Geom gf, Geom gc, XferTab xt) {
+  const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (nd >= gc.nn) return;
+  int base[3] = {0, 0, 0}, k[3] = {0, 0, 0};
+  long long rem = nd;
+  for (int t = 0; t < dim; ++t) {
+    const int J = int(rem % gc.n1);
+    rem /= gc.n1;
+    int c = J / p;
+    if (c > gc.N - 1) c = gc.N - 1;
+    k[t] = J - c * p;
+    base[t] = (2 * c + xt.FC[k[t]]) * p;  // first fine node of the fine cell holding the coarse node
+  }
+  for (int f = 0; f < nfields; ++f) {
+    const double* x = xf + (long long)f * gf.nn;
+    double v = 0.0;
+    const int mz = dim == 3 ? p : 0;
+    for (int cz = 0; cz <= mz; ++cz) {
+      const double wz = dim == 3 ? xt.F[k[2]][cz] : 1.0;
+      if (wz == 0.0) continue;
+      for (int cy = 0; cy <= p; ++cy) {
+        const double wy = xt.F[k[1]][cy];
+        if (wy == 0.0) continue;
+        for (int cx = 0; cx <= p; ++cx) {
+          const double wx = xt.F[k[0]][cx];
+          if (wx == 0.0) continue;
+          long long fn = (base[0] + cx) + (long long)gf.n1 * (base[1] + cy);
+          if (dim == 3) fn += (long long)gf.n1 * gf.n1 * (base[2] + cz);
+          v += wz * wy * wx * x[fn];
+        }
+      }
+    }
+    yc[(long long)f * gc.nn + nd] = v;
+  }
+}
+
+cudaError_t launch_state_interp(int dim, int p, const double* xf, double* yc, int nfields, const Geom& gf,
+                                const Geom& gc, const XferTab& xt, cudaStream_t s) {
+  k_state_interp<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, xf, yc, nfields, gf, gc, xt);
+  return cudaGetLastError();
+}
+
+__global__ void k_coarse_active(int dim, int p, const unsigned char* __restrict__ flf, unsigned char* __restrict__ flc,
+                                Geom gf, Geom gc, XferTab xt) {
+  const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (nd >= gc.nn) return;
+  long long rem = nd, fn = 0, stride = 1;
+  bool col = true;
+  for (int t = 0; t < dim; ++t) {
+    const int J = int(rem % gc.n1);
+    rem /= gc.n1;
+    int c = J / p;
+    if (c > gc.N - 1) c = gc.N - 1;
+    const int k = J - c * p;
+    if (xt.COL[k] < 0) col = false;
+    else fn += stride * (2 * p * c + xt.COL[k]);
+    stride *= gf.n1;
+  }
+  const unsigned char bit = (unsigned char)(1u << dim);
+  unsigned char fl = flc[nd] & (unsigned char)~bit;
+  if (col && (flf[fn] & bit)) fl |= bit;
+  flc[nd] = fl;
+}
+
+cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, unsigned char* flags_c,
+                                 const Geom& gf, const Geom& gc, const XferTab& xt, cudaStream_t s) {
+  k_coarse_active<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, flags_f, flags_c, gf, gc, xt);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Vector kernels.
+template <typename Real>
+__global__ void k_axpby(long long n, double a, const Real* __restrict__ x, double b, Real* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = Real(a * (double)x[e] + (b == 0.0 ? 0.0 : b * (double)y[e]));
+}
+template <>
+__global__ void k_axpby<float>(long long n, double a, const float* __restrict__ x, double b, float* __restrict__ y) {
+  const float af = (float)a, bf = (float)b;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = af * x[e] + (bf == 0.0f ? 0.0f : bf * y[e]);
+}
+
+template <typename Real>
+cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_axpby<Real><<<(unsigned)g, BLK, 0, s>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
+template cudaError_t launch_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
+
+template <typename Ti, typename To>
+__global__ void k_cast(long long n, const Ti* __restrict__ x, To* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = To(x[e]);
+}
+template <typename Ti, typename To>
+cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_cast<Ti, To><<<(unsigned)g, BLK, 0, s>>>(n, x, y);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cast<double, float>(long long, const double*, float*, cudaStream_t);
+template cudaError_t launch_cast<float, double>(long long, const float*, double*, cudaStream_t);
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+constexpr int DOT_GRID = 152 * 2;
+
+template <typename Real>
+__global__ void k_dot2_part(long long n, long long nu, const Real* __restrict__ x, const Real* __restrict__ y,
+                            double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)x[e] * (double)y[e];
+    if (e < nu) s0 += v;
+    else s1 += v;
+  }
+  const double r0 = block_sum(s0, sh);
+  const double r1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r0;
+    part[2 * blockIdx.x + 1] = r1;
+  }
+}
+__global__ void k_dot2_final(int nb, const double* __restrict__ part, double* __restrict__ res) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    s0 += part[2 * b];
+    s1 += part[2 * b + 1];
+  }
+  const double r0 = block_sum(s0, sh);
+  const double r1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    res[0] = r0;
+    res[1] = r1;
+  }
+}
+
+template <typename Real>
+cudaError_t launch_dot2(long long n, long long nu, const Real* x, const Real* y, double* partial, double* res,
+                        cudaStream_t s) {
+  k_dot2_part<Real><<<DOT_GRID, BLK, 0, s>>>(n, nu, x, y, partial);
+  k_dot2_final<<<1, BLK, 0, s>>>(DOT_GRID, partial, res);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dot2<double>(long long, long long, const double*, const double*, double*, double*,
+                                         cudaStream_t);
+template cudaError_t launch_dot2<float>(long long, long long, const float*, const float*, double*, double*,
+                                        cudaStream_t);
+
+// Multi-dot h_i = <V_i, w>: blockIdx.y selects a group of 4 basis vectors.
+__global__ void k_mdot_part(long long n, int k, const double* __restrict__ V, const double* __restrict__ w,
+                            double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int i0 = blockIdx.y * 4;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double we = w[e];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i0 + j < k) s[j] += V[(long long)(i0 + j) * n + e] * we;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double r = block_sum(s[j], sh);
+    if (threadIdx.x == 0 && i0 + j < k) part[(long long)(i0 + j) * gridDim.x + blockIdx.x] = r;
+  }
+}
+__global__ void k_mdot_final(int nb, const double* __restrict__ part, double* __restrict__ h) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(long long)blockIdx.x * nb + b];
+  const double r = block_sum(s, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = r;
+}
+
+cudaError_t launch_mdot(long long n, int k, const double* V, const double* w, double* partial, double* h,
+                        cudaStream_t s) {
+  const int nb = 152;
+  dim3 grd(nb, (k + 3) / 4);
+  k_mdot_part<<<grd, BLK, 0, s>>>(n, k, V, w, partial);
+  k_mdot_final<<<k, BLK, 0, s>>>(nb, partial, h);
+  return cudaGetLastError();
+}
+
+__global__ void k_maxpy(long long n, int k, const double* __restrict__ V, const double* __restrict__ h,
+                        double* __restrict__ w, double sign) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += V[(long long)i * n + e] * h[i];
+    w[e] += sign * acc;
+  }
+}
+
+cudaError_t launch_maxpy(long long n, int k, const double* V, const double* h, double* w, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 8) g = 152 * 8;
+  k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, V, h, w, -1.0);
+  return cudaGetLastError();
+}
+cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y, double* x, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 8) g = 152 * 8;
+  k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, Z, y, x, 1.0);
+  return cudaGetLastError();
+}
+
+__global__ void k_normalize(long long n, const double* __restrict__ x, const double* __restrict__ nrm2,
+                            double* __restrict__ y) {
+  const double inv = 1.0 / sqrt(nrm2[0] + nrm2[1]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = x[e] * inv;
+}
+cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, nrm2, y);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Chebyshev-Jacobi step on the two diagonal blocks (Sec. 3.3), interval [lo, hi] * lambda_max.
+template <typename Real>
+__global__ void k_cheb(int step, long long n, long long nu, const Real* __restrict__ f, const Real* __restrict__ Ax,
+                       const Real* __restrict__ dinv, Real* __restrict__ d, Real* __restrict__ x,
+                       const double* __restrict__ lam_max, double lo, double hi, double c1, double rho_k) {
+  const double l0 = lam_max[0], l1 = lam_max[1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double lm = e < nu ? l0 : l1;
+    const double a = lo * lm, b = hi * lm;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+    const bool ok = lm > 0.0 && lm < 1e300;
+    if (step == 0) {
+      const Real de = ok ? Real((double)dinv[e] * (double)f[e] / theta) : Real(0);
+      d[e] = de;
+      x[e] = de;
+    } else {
+      const double r = (double)dinv[e] * ((double)f[e] - (double)Ax[e]);
+      const Real de = ok ? Real(c1 * (double)d[e] + (2.0 * rho_k / delta) * r) : Real(0);
+      d[e] = de;
+      x[e] += de;
+    }
+  }
+}
+template <>
+__global__ void k_cheb<float>(int step, long long n, long long nu, const float* __restrict__ f,
+                              const float* __restrict__ Ax, const float* __restrict__ dinv, float* __restrict__ d,
+                              float* __restrict__ x, const double* __restrict__ lam_max, double lo, double hi,
+                              double c1, double rho_k) {
+  __shared__ float coef[2][3];
+  if (threadIdx.x < 2) {
+    const double lm = lam_max[threadIdx.x];
+    const double a = lo * lm, b = hi * lm;
+    const bool ok = lm > 0.0 && lm < 1e300;
+    coef[threadIdx.x][0] = ok ? float(2.0 / (b + a)) : 0.0f;                  // 1 / theta
+    coef[threadIdx.x][1] = ok ? float(2.0 * rho_k / (0.5 * (b - a))) : 0.0f;  // 2 rho_k / delta
+    coef[threadIdx.x][2] = ok ? float(c1) : 0.0f;
+  }
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int bk = e < nu ? 0 : 1;
+    if (step == 0) {
+      const float de = dinv[e] * f[e] * coef[bk][0];
+      d[e] = de;
+      x[e] = de;
+    } else {
+      const float de = coef[bk][2] * d[e] + coef[bk][1] * (dinv[e] * (f[e] - Ax[e]));
+      d[e] = de;
+      x[e] += de;
+    }
+  }
+}
+
+template <typename Real>
+cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, const Real* Ax, const Real* dinv, Real* d,
+                        Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
+                        cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_cheb<Real><<<(unsigned)g, BLK, 0, s>>>(step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1, rho_k);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb<double>(int, long long, long long, const double*, const double*, const double*,
+                                         double*, double*, const double*, double, double, double, double,
+                                         cudaStream_t);
+template cudaError_t launch_cheb<float>(int, long long, long long, const float*, const float*, const float*, float*,
+                                        float*, const double*, double, double, double, double, cudaStream_t);
+
+// ---- CG-Lanczos -------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_cg_init(long long n, unsigned long long seed, const unsigned char* __restrict__ flags, long long nn,
+                          const double* __restrict__ dinv, double* __restrict__ r, double* __restrict__ z,
+                          double* __restrict__ pv) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int f = int(e / nn);
+    const bool masked = (flags[e % nn] >> f) & 1u;
+    const double v = masked ? 0.0 : (double)(splitmix64(seed, (uint64_t)e) >> 11) * 0x1.0p-53 - 0.5;
+    r[e] = v;
+    const double zz = dinv[e] * v;
+    z[e] = zz;
+    pv[e] = zz;
+  }
+}
+cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags, int dim,
+                           long long nn, const double* dinv, double* r, double* z, double* pv, cudaStream_t s) {
+  (void)nu;
+  (void)dim;
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_cg_init<<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
+  return cudaGetLastError();
+}
+
+__global__ void k_cg_update(long long n, long long nu, const double* __restrict__ Ap, const double* __restrict__ dinv,
+                            const double* __restrict__ scal, double* __restrict__ r, double* __restrict__ z) {
+  const double a0 = scal[4], a1 = scal[5];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double al = e < nu ? a0 : a1;
+    const double rr = r[e] - al * Ap[e];
+    r[e] = rr;
+    z[e] = dinv[e] * rr;
+  }
+}
+cudaError_t launch_cg_update(long long n, long long nu, const double* Ap, const double* dinv, const double* scal,
+                             double* r, double* z, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_cg_update<<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
+  return cudaGetLastError();
+}
+__global__ void k_cg_pupdate(long long n, long long nu, const double* __restrict__ z, const double* __restrict__ scal,
+                             double* __restrict__ pv) {
+  const double b0 = scal[6], b1 = scal[7];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    pv[e] = z[e] + (e < nu ? b0 : b1) * pv[e];
+}
+cudaError_t launch_cg_pupdate(long long n, long long nu, const double* z, const double* scal, double* pv,
+                              cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_cg_pupdate<<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
+  return cudaGetLastError();
+}
+
+// scal: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1]
+__global__ void k_cg_scalars(int phase, int it, int iters, double* scal, double* ah, double* bh) {
+  const int b = threadIdx.x;
+  if (b >= 2) return;
+  double* dead = scal + 10;
+  if (phase == 0) {
+    const double rz = scal[b], pAp = scal[2 + b];
+    double al = 0.0;
+    if (dead[b] == 0.0 && pAp > 0.0 && rz > 0.0 && pAp < 1e300) al = rz / pAp;
+    else dead[b] = 1.0;
+    scal[4 + b] = al;
+    ah[b * iters + it] = al;
+  } else {
+    const double rzn = scal[8 + b], rz = scal[b];
+    double be = 0.0;
+    if (dead[b] == 0.0) {
+      be = rzn / rz;
+      if (!(rzn > 0.0)) dead[b] = 1.0;
+    }
+    scal[6 + b] = be;
+    bh[b * iters + it] = be;
+    scal[b] = rzn;
+  }
+}
+cudaError_t launch_cg_scalars(int phase, int it, int iters, double* scal, double* alpha_hist, double* beta_hist,
+                              cudaStream_t s) {
+  k_cg_scalars<<<1, 32, 0, s>>>(phase, it, iters, scal, alpha_hist, beta_hist);
+  return cudaGetLastError();
+}
+
+// lambda_max / lambda_min of the Lanczos tridiagonal by bisection with Sturm counts.
+__device__ int sturm_count(int k, const double* a, const double* b2, double x) {
+  int cnt = 0;
+  double d = a[0] - x;
+  if (d < 0.0) ++cnt;
+  for (int j = 1; j < k; ++j) {
+    if (d == 0.0) d = 1e-300;
+    d = a[j] - x - b2[j - 1] / d;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+__global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const double* __restrict__ bh,
+                              double* __restrict__ lam) {
+  const int b = threadIdx.x;
+  if (b >= 2) return;
+  double a[64], b2[64];
+  int k = 0;
+  while (k < iters && k < 64 && ah[b * iters + k] > 0.0) ++k;
+  if (k == 0) {
+    lam[b] = 1.0;
+    lam[2 + b] = 1.0;
+    return;
+  }
+  for (int j = 0; j < k; ++j) {
+    const double al = ah[b * iters + j];
+    a[j] = 1.0 / al + (j > 0 ? bh[b * iters + j - 1] / ah[b * iters + j - 1] : 0.0);
+    if (j + 1 < k) {
+      const double off = sqrt(bh[b * iters + j]) / al;
+      b2[j] = off * off;
+    }
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < k; ++j) {
+    double r = 0.0;
+    if (j > 0) r += sqrt(b2[j - 1]);
+    if (j + 1 < k) r += sqrt(b2[j]);
+    lo = fmin(lo, a[j] - r);
+    hi = fmax(hi, a[j] + r);
+  }
+  // largest eigenvalue: count(x) < k  <=>  x <= lambda_max
+  double l = lo, h = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (l + h);
+    if (m <= l || m >= h) break;
+    if (sturm_count(k, a, b2, m) >= k) h = m;
+    else l = m;
+  }
+  lam[b] = h;
+  l = lo;
+  h = hi;
+  for (int it = 0; it < 200; ++it) {
+    const double m = 0.5 * (l + h);
+    if (m <= l || m >= h) break;
+    if (sturm_count(k, a, b2, m) >= 1) h = m;
+    else l = m;
+  }
+  lam[2 + b] = l;
+}
+cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
+                               cudaStream_t s) {
+  k_tridiag_eig<<<1, 32, 0, s>>>(iters, alpha_hist, beta_hist, lam);
+  return cudaGetLastError();
+}
+
+__global__ void k_inv_diag(long long n, const double* __restrict__ d, double* __restrict__ di64,
+                           float* __restrict__ di32) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d[e];
+    di64[e] = v;
+    di32[e] = (float)v;
+  }
+}
+cudaError_t launch_inv_diag(long long n, const double* d, double* di64, float* di32, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  k_inv_diag<<<(unsigned)g, BLK, 0, s>>>(n, d, di64, di32);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Newton step helpers.
+__global__ void k_active_set(int dim, long long nn, const double* __restrict__ R, const double* __restrict__ mass,
+                             const double* __restrict__ phi_old, double c, double* __restrict__ U,
+                             unsigned char* __restrict__ flags, int* __restrict__ cnt) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool act = false, chg = false;
+  if (i < nn) {
+    const double phi = U[dim * nn + i];
+    const double crit = -R[dim * nn + i] / mass[i] + c * (phi - phi_old[i]);
+    act = crit > 0.0;
+    const unsigned char bit = (unsigned char)(1u << dim);
+    const unsigned char fl = flags[i];
+    chg = act != ((fl & bit) != 0);
+    flags[i] = act ? (unsigned char)(fl | bit) : (unsigned char)(fl & ~bit);
+    if (act) U[dim * nn + i] = phi_old[i];
+  }
+  const unsigned ba = __ballot_sync(0xffffffffu, act), bc = __ballot_sync(0xffffffffu, chg);
+  if ((threadIdx.x & 31) == 0) {
+    if (ba) atomicAdd(cnt, __popc(ba));
+    if (bc) atomicAdd(cnt + 1, __popc(bc));
+  }
+}
+cudaError_t launch_active_set(int dim, long long nn, const double* R, const double* mass, const double* phi_old,
+                              double c, double* U, unsigned char* flags, int* cnt, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_active_set<<<grid_for(nn), BLK, 0, s>>>(dim, nn, R, mass, phi_old, c, U, flags, cnt);
+  return cudaGetLastError();
+}
+
+__global__ void k_newton_rhs(int dim, long long nn, const double* __restrict__ R,
+                             const unsigned char* __restrict__ flags, double* __restrict__ rhs) {
+  const long long n = (dim + 1) * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int f = int(e / nn);
+    rhs[e] = ((flags[e % nn] >> f) & 1u) ? 0.0 : -R[e];
+  }
+}
+cudaError_t launch_newton_rhs(int dim, long long nn, const double* R, const unsigned char* flags, double* rhs,
+                              cudaStream_t s) {
+  long long g = ((dim + 1) * nn + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_newton_rhs<<<(unsigned)g, BLK, 0, s>>>(dim, nn, R, flags, rhs);
+  return cudaGetLastError();
+}
+
+__global__ void k_masked_copy(int dim, long long nn, double scale, const double* __restrict__ x,
+                              const unsigned char* __restrict__ flags, unsigned bits, double* __restrict__ out) {
+  const long long n = (dim + 1) * nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int f = int(e / nn);
+    out[e] = (((flags[e % nn] & bits) >> f) & 1u) ? 0.0 : scale * x[e];
+  }
+}
+cudaError_t launch_masked_copy(int dim, long long nn, double scale, const double* x, const unsigned char* flags,
+                               unsigned bits, double* out, cudaStream_t s) {
+  long long g = ((dim + 1) * nn + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  k_masked_copy<<<(unsigned)g, BLK, 0, s>>>(dim, nn, scale, x, flags, bits, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_active(int dim, long long nn, const unsigned char* __restrict__ a, unsigned char* __restrict__ fl) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const unsigned char bit = (unsigned char)(1u << dim);
+  fl[i] = a[i] ? (unsigned char)(fl[i] | bit) : (unsigned char)(fl[i] & ~bit);
+}
+cudaError_t launch_set_active(int dim, long long nn, const unsigned char* active, unsigned char* flags,
+                              cudaStream_t s) {
+  k_set_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, active, flags);
+  return cudaGetLastError();
+}
+__global__ void k_get_active(int dim, long long nn, const unsigned char* __restrict__ fl, unsigned char* __restrict__ a) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  a[i] = (fl[i] >> dim) & 1u;
+}
+cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags, unsigned char* active,
+                              cudaStream_t s) {
+  k_get_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, flags, active);
+  return cudaGetLastError();
+}
+
+__global__ void k_lumped_mass(int dim, long long nn, int n1, const double* __restrict__ w1, double* __restrict__ m) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  long long rem = i;
+  double v = 1.0;
+  for (int t = 0; t < dim; ++t) {
+    v *= w1[rem % n1];
+    rem /= n1;
+  }
+  m[i] = v;
+}
+cudaError_t launch_lumped_mass(int dim, long long nn, int n1, const double* w1, double* mass, cudaStream_t s) {
+  k_lumped_mass<<<grid_for(nn), BLK, 0, s>>>(dim, nn, n1, w1, mass);
+  return cudaGetLastError();
+}
+
+}  // namespace pff

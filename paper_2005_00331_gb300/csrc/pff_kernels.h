@@ -1,0 +1,118 @@
+// pff_kernels.h -- host launchers of the non-operator kernels of libpff (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include "pff_common.cuh"
+
+namespace pff {
+
+struct MatConst {
+  double lambda, mu, gc, eps, kappa;
+};
+
+// Per-point data of the Jacobian (FP64 and optionally an FP32 copy) and of the residual.
+cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
+                            const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
+                            const MatConst& mc, double* qp64, float* qp32, double* st64, cudaStream_t s);
+// diag(G_uu, G_phiphi) of a level into d64 (zeroed here), masked rows set to 1; FP32 copy if d32.
+cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const unsigned char* flags,
+                            const Geom& g, const Tab<double>& tb, double* d64, float* d32, cudaStream_t s);
+// (dR/dparam)^T v, three nodal outputs (zeroed here); tmp has 3 * n_cells * n^dim doubles.
+cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const double* v, const double* st64,
+                              const Geom& g, const Tab<double>& tb, const MatConst& mc, double* tmp,
+                              double* out_gc, double* out_lam, double* out_mu, cudaStream_t s);
+// Dense coarse blocks: Au (nu x nu), Ap (nn x nn), B (nn x nu), masked rows/cols -> identity / 0.
+cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64, const unsigned char* flags,
+                                   const Geom& g, const Tab<double>& tb, double* Au, double* Ap, double* B,
+                                   cudaStream_t s);
+// In-place Gauss-Jordan inverse of an n x n matrix (no pivoting; SPD input); buf: 2n doubles.
+cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s);
+// y = A x (dense, row major, n rows, m cols); y = beta * y + alpha * A x.
+cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
+                        cudaStream_t s);
+
+// Transfer tables of one degree (fine/coarse pair with ratio 2).
+struct XferTab {
+  double E[2 * MAXP + 1][MAXN];  // coarse basis k at the fine node o of a coarse cell
+  double F[MAXN][MAXN];          // fine basis m at the coarse node k (inside fine cell FC[k])
+  int FC[MAXN];
+  int COL[MAXN];                 // fine offset co-located with coarse node k, or -1
+};
+template <typename Real>
+cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f,
+                           const Geom& gc, const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
+                            const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
+                            cudaStream_t s);
+// Evaluates `nfields` fine nodal fields (each nn_f long, consecutive) at the coarse nodes.
+cudaError_t launch_state_interp(int dim, int p, const double* xf, double* yc, int nfields, const Geom& gf,
+                                const Geom& gc, const XferTab& xt, cudaStream_t s);
+// Coarse active bits from fine active bits at co-located nodes (the bit of field dim).
+cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, unsigned char* flags_c,
+                                 const Geom& gf, const Geom& gc, const XferTab& xt, cudaStream_t s);
+
+// ---- vectors ---------------------------------------------------------------------------
+template <typename Real>
+cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y, cudaStream_t s);
+template <typename Ti, typename To>
+cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s);
+// Two-block dot products of x and y over [0, nu) and [nu, n): result res[0], res[1] (device, FP64).
+template <typename Real>
+cudaError_t launch_dot2(long long n, long long nu, const Real* x, const Real* y, double* partial, double* res,
+                        cudaStream_t s);
+// h[i] = <V_i, w> for i < k, V row-major (k x n); partial >= k * 2 * 152 doubles.
+cudaError_t launch_mdot(long long n, int k, const double* V, const double* w, double* partial, double* h,
+                        cudaStream_t s);
+// w -= sum_i V_i h[i]
+cudaError_t launch_maxpy(long long n, int k, const double* V, const double* h, double* w, cudaStream_t s);
+// x += sum_i Z_i y[i]
+cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y, double* x, cudaStream_t s);
+// y = x / sqrt(nrm2[0])
+cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s);
+
+// ---- Chebyshev-Jacobi and eigenvalue estimation -----------------------------------------
+// step 0: x = d = dinv f / theta_b; step k: d = c1 d + (2 rho_k / delta_b) dinv (f - Ax), x += d.
+template <typename Real>
+cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, const Real* Ax, const Real* dinv,
+                        Real* d, Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
+                        cudaStream_t s);
+// CG-Lanczos on the two diagonal blocks (FP64 vectors).
+cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags,
+                           int dim, long long nn, const double* dinv, double* r, double* z, double* pv,
+                           cudaStream_t s);
+cudaError_t launch_cg_update(long long n, long long nu, const double* Ap, const double* dinv, const double* scal,
+                             double* r, double* z, cudaStream_t s);
+cudaError_t launch_cg_pupdate(long long n, long long nu, const double* z, const double* scal, double* pv,
+                              cudaStream_t s);
+// scalar bookkeeping (single thread): phase 0 after <p,Ap>: alpha = rz/pAp; phase 1 after <r,z>_new:
+// beta = rz_new/rz, rz = rz_new. scal layout: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1
+// dead0 dead1]; the histories are [2][iters].
+cudaError_t launch_cg_scalars(int phase, int it, int iters, double* scal, double* alpha_hist, double* beta_hist,
+                              cudaStream_t s);
+// lam_max[b] from the Lanczos tridiagonal of the first k_valid CG steps of each block.
+cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
+                               cudaStream_t s);
+
+// di = 1 / d (FP64 and FP32 copies): the Jacobi scaling of the smoother.
+cudaError_t launch_inv_diag(long long n, const double* d, double* di64, float* di32, cudaStream_t s);
+
+// ---- Newton step helpers ----------------------------------------------------------------
+// Active set of Alg. 1 on the phase-field block: sets/clears the active bit (field dim), resets
+// phi := phi_old on it, counts |A| and changes (cnt[0], cnt[1], device ints zeroed here).
+cudaError_t launch_active_set(int dim, long long nn, const double* R, const double* mass, const double* phi_old,
+                              double c, double* U, unsigned char* flags, int* cnt, cudaStream_t s);
+// rhs = -R on unmasked rows, 0 on masked rows (all flag bits).
+cudaError_t launch_newton_rhs(int dim, long long nn, const double* R, const unsigned char* flags, double* rhs,
+                              cudaStream_t s);
+// out = 0 where the node's flag bit of the field is set in `bits`, scale * x elsewhere.
+cudaError_t launch_masked_copy(int dim, long long nn, double scale, const double* x, const unsigned char* flags,
+                               unsigned bits, double* out, cudaStream_t s);
+// Copies the active bit (field dim) from a byte array (nonzero = active) into the flags.
+cudaError_t launch_set_active(int dim, long long nn, const unsigned char* active, unsigned char* flags,
+                              cudaStream_t s);
+cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags, unsigned char* active,
+                              cudaStream_t s);
+// Lumped phase-field mass: int psi_i over the mesh (tensor product of 1D GLL weight sums).
+cudaError_t launch_lumped_mass(int dim, long long nn, int n1, const double* w1, double* mass, cudaStream_t s);
+
+}  // namespace pff

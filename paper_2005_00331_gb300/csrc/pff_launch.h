@@ -1,0 +1,33 @@
+// pff_launch.h -- host-side launchers of the operator kernels (internal to libpff).
+#pragma once
+#include <cuda_runtime.h>
+#include "pff_common.cuh"
+
+namespace pff {
+
+// y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be
+// zeroed by the caller (seam nodes are accumulated atomically). mode: JM_*; masks: In/OutMask.
+cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                       const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask,
+                       int outmask, cudaStream_t s);
+cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
+                       const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
+                       cudaStream_t s);
+cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                          const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s);
+cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
+                          const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s);
+cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                          const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s);
+cudaError_t launch_jac_d3(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
+                          const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s);
+// r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu.
+cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
+                       const Geom& g, const Tab<double>& tb, const double* st, double eps, double kappa,
+                       cudaStream_t s);
+
+}  // namespace pff

@@ -1,0 +1,542 @@
+// pff_op.cuh -- cell-batched, sum-factorised operator kernels (2D and 3D).
+//
+// One CTA owns a tile of TX x TY (x TZ) cells. It stages the tile's node patch of every field
+// in shared memory and evaluates the fields at all Gauss points of the tile with patch-wide 1D
+// contractions (sum factorisation, Sec. 3.4 and its reference KrKo12): a node row shared by
+// two cells is contracted once. A pointwise functor turns the evaluated source (gradients of
+// the displacement components, phase-field value and gradient) into test coefficients; the
+// transposed contractions integrate them back to the node patch. Nodes strictly inside the
+// tile are written with plain stores; nodes on a seam between tiles are accumulated with
+// atomics into an output the caller has zeroed. Rows masked on output (Dirichlet DoFs, the
+// active set) are written once, by the tile that owns the node.
+#pragma once
+#include "pff_common.cuh"
+
+namespace pff {
+
+// Gradient/value bundle handed to the pointwise functors.
+template <int DIM, typename Real>
+struct QPIn {
+  Real gu[DIM][DIM];  // gu[k][j] = d u_k / d x_j
+  Real ph;            // phase field value
+  Real gph[DIM];      // phase field gradient
+};
+template <int DIM, typename Real>
+struct QPOut {
+  Real cu[DIM][DIM];  // coefficient of d w_k / d x_j in the u-test
+  Real cv;            // coefficient of psi
+  Real cg[DIM];       // coefficient of d psi / d x_j
+};
+
+// -------------------------------------------------------------------------------------------
+// Pointwise Jacobian of Eq. (G) from stored per-point data (already multiplied by JxW).
+// Full mode: u-test  tau = C_eff[e(du)],  phi-test  b : e(du) + c dphi,  k grad dphi;
+// block-diagonal mode drops b : e(du); transpose mode moves the coupling to the u-test,
+// tau += b dphi.
+template <int DIM, typename Real, int SPLIT>
+struct PWJac {
+  const Real* qp;   // [tile][nv][qpt]
+  long long tstride;
+  long long qpt;
+  int mode;
+  __device__ __forceinline__ void operator()(long long tile, long long qi, const QPIn<DIM, Real>& in,
+                                             QPOut<DIM, Real>& out) const {
+    constexpr int NM = Mandel<DIM>::NM;
+    constexpr Real RS2 = Real(0.70710678118654752440);
+    const Real* a = qp + tile * tstride + qi;
+    Real em[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+      em[m] = (i == j) ? in.gu[i][i] : (in.gu[i][j] + in.gu[j][i]) * RS2;
+    }
+    Real tau[NM];
+    int off;
+    if constexpr (SPLIT == 0) {
+      const Real gl = a[0], gm2 = Real(2) * a[qpt];
+      Real tr = 0;
+#pragma unroll
+      for (int t = 0; t < DIM; ++t) tr += em[t];
+#pragma unroll
+      for (int m = 0; m < NM; ++m) tau[m] = gm2 * em[m] + (m < DIM ? gl * tr : Real(0));
+      off = 2;
+    } else {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) tau[m] = 0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+#pragma unroll
+        for (int j = i; j < NM; ++j) {
+          const Real cij = a[sym_index(NM, i, j) * qpt];
+          tau[i] += cij * em[j];
+          if (j != i) tau[j] += cij * em[i];
+        }
+      }
+      off = NM * (NM + 1) / 2;
+    }
+    const Real c = a[(off + NM) * qpt], k = a[(off + NM + 1) * qpt];
+    Real cv = c * in.ph;
+    if (mode == JM_FULL) {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) cv += a[(off + m) * qpt] * em[m];
+    } else if (mode == JM_TRANSPOSE) {
+#pragma unroll
+      for (int m = 0; m < NM; ++m) tau[m] += a[(off + m) * qpt] * in.ph;
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+      if (i == j) out.cu[i][i] = tau[m];
+      else out.cu[i][j] = out.cu[j][i] = tau[m] * RS2;
+    }
+    out.cv = cv;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) out.cg[j] = k * in.gph[j];
+  }
+};
+
+// -------------------------------------------------------------------------------------------
+// Pointwise residual of Eq. (residual) from the evaluated state (FP64):
+// u-test  g(phi~) sigma^+ + sigma^-,  phi-test  g'(phi) E_s^+ - (G_c/eps)(1 - phi),
+// grad-test G_c eps grad phi. Stored per point: g(phi~), G_c, lambda, mu.
+template <int DIM, int SPLIT>
+struct PWRes {
+  const double* st;  // [tile][4][qpt]
+  long long tstride, qpt;
+  int qpx, qpy, n;
+  double W[MAXN], hd, eps, kappa;
+  __device__ __forceinline__ void operator()(long long tile, long long qi, const QPIn<DIM, double>& in,
+                                             QPOut<DIM, double>& out) const {
+    const double* a = st + tile * tstride + qi;
+    const double gt = a[0], gc = a[qpt], lam = a[2 * qpt], mu = a[3 * qpt];
+    const int qx = int(qi % qpx) % n;
+    const int qy = int((qi / qpx) % qpy) % n;
+    double jxw = hd * W[qx] * W[qy];
+    if constexpr (DIM == 3) jxw *= W[int(qi / ((long long)qpx * qpy)) % n];
+    double e[DIM][DIM];
+    double tr = 0.0;
+    for (int i = 0; i < DIM; ++i) {
+      for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (in.gu[i][j] + in.gu[j][i]);
+      tr += e[i][i];
+    }
+    double sp[DIM][DIM], Esp;
+    if constexpr (SPLIT == 0) {
+      double ee = 0.0;
+      for (int i = 0; i < DIM; ++i)
+        for (int j = 0; j < DIM; ++j) {
+          sp[i][j] = 2.0 * mu * e[i][j] + (i == j ? lam * tr : 0.0);
+          ee += e[i][j] * e[i][j];
+        }
+      Esp = 0.5 * lam * tr * tr + mu * ee;
+    } else {
+      double l[DIM], V[DIM][DIM];
+      eig_sym<DIM>(e, l, V);
+      double trs = tr;
+      snap_zero<DIM>(l, trs);
+      const double trp = pos(trs);
+      double sl2 = 0.0;
+      for (int t = 0; t < DIM; ++t) sl2 += pos(l[t]) * pos(l[t]);
+      Esp = 0.5 * lam * trp * trp + mu * sl2;
+      for (int i = 0; i < DIM; ++i)
+        for (int j = 0; j < DIM; ++j) {
+          double epij = 0.0;
+          for (int t = 0; t < DIM; ++t) epij += pos(l[t]) * V[i][t] * V[j][t];
+          sp[i][j] = 2.0 * mu * epij + (i == j ? lam * trp : 0.0);
+        }
+    }
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        const double sig = 2.0 * mu * e[i][j] + (i == j ? lam * tr : 0.0);
+        out.cu[i][j] = jxw * (gt * sp[i][j] + (sig - sp[i][j]));
+      }
+    out.cv = jxw * (deg_dg(in.ph, kappa) * Esp - gc / eps * (1.0 - in.ph));
+    for (int j = 0; j < DIM; ++j) out.cg[j] = jxw * gc * eps * in.gph[j];
+  }
+};
+
+// -------------------------------------------------------------------------------------------
+struct OpArgs {
+  int inmask, outmask;
+};
+
+__device__ __forceinline__ unsigned char dirichlet_bits(int dim) { return (unsigned char)((1u << dim) - 1u); }
+
+// Store of one node value of the output patch (see the file comment for the seam rule).
+template <typename Real>
+__device__ __forceinline__ void store_node(Real* __restrict__ dst, const Real* __restrict__ src,
+                                           const unsigned char* __restrict__ flags, long long node,
+                                           long long gi, int f, int dim, Real v, bool low_seam,
+                                           bool high_seam, int outmask) {
+  bool masked = false;
+  if (outmask != OUT_RAW) {
+    const unsigned char fl = flags[node];
+    const unsigned char m = outmask == OUT_IDENTITY ? fl : (unsigned char)(fl & dirichlet_bits(dim));
+    masked = (m >> f) & 1u;
+  }
+  if (masked) {
+    if (!low_seam) dst[gi] = outmask == OUT_IDENTITY ? src[gi] : Real(0);
+  } else if (low_seam || high_seam) {
+    atomicAdd(dst + gi, v);
+  } else {
+    dst[gi] = v;
+  }
+}
+
+template <typename Real>
+__device__ __forceinline__ Real load_node(const Real* __restrict__ src, const unsigned char* __restrict__ flags,
+                                          long long node, long long gi, int f, int dim, int inmask) {
+  Real v = src[gi];
+  if (inmask != IN_RAW) {
+    const unsigned char fl = flags[node];
+    const unsigned char m = inmask == IN_ALL ? fl : (unsigned char)(fl & dirichlet_bits(dim));
+    if ((m >> f) & 1u) v = Real(0);
+  }
+  return v;
+}
+
+// Range of cells (within a tile of T cells) containing local node index r (0..T*P).
+template <int P>
+__device__ __forceinline__ void cells_of_node(int r, int T, int& lo, int& hi) {
+  lo = r == 0 ? 0 : (r - 1) / P;
+  hi = r / P;
+  if (hi > T - 1) hi = T - 1;
+}
+
+// ===========================================================================================
+// 2D operator kernel.
+template <int P, typename Real, class PW>
+__global__ void __launch_bounds__(256)
+k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char* __restrict__ flags,
+       Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
+  constexpr int TX = TileCfg<2, P>::TX, TY = TileCfg<2, P>::TY;
+  constexpr int n = P + 1, NF = 3;
+  constexpr int NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* X = reinterpret_cast<Real*>(smem_raw);  // [NF][NPY][NPX], later the output patch
+  Real* XB = X + NF * NPY * NPX;                 // [NF][NPY][QPX]
+  Real* XD = XB + NF * NPY * QPX;
+  Real* UB = XD + NF * NPY * QPX;                // [NF][TY][n][QPX]
+  Real* UD = UB + NF * TY * n * QPX;
+
+  const long long tile = blockIdx.x;
+  const int tx = int(tile % g.ntile[0]), ty = int(tile / g.ntile[0]);
+  const int x0 = tx * TX * P, y0 = ty * TY * P;
+  const int cx0 = tx * TX, cy0 = ty * TY;
+
+  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
+    const int gx = x0 + s, gy = y0 + r;
+    Real v = 0;
+    if (gx < g.n1 && gy < g.n1) {
+      const long long node = gx + (long long)g.n1 * gy;
+      v = load_node(src, flags, node, f * g.nn + node, f, 2, oa.inmask);
+    }
+    X[i] = v;
+  }
+  __syncthreads();
+  // x-pass: values (XB) and x-derivatives (XD) at the Gauss columns of every node row
+  for (int i = threadIdx.x; i < NF * NPY * QPX; i += blockDim.x) {
+    const int c = i % QPX, rf = i / QPX;
+    const int cx = c / n, qi = c % n;
+    const Real* xr = X + rf * NPX + cx * P;
+    Real b = 0, d = 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      b += tb.S[qi][k] * xr[k];
+      d += tb.D[qi][k] * xr[k];
+    }
+    XB[i] = b;
+    XD[i] = d;
+  }
+  __syncthreads();
+  // y-pass, pointwise, transposed y-pass: one thread per (cell row, Gauss column)
+  for (int i = threadIdx.x; i < TY * QPX; i += blockDim.x) {
+    const int c = i % QPX, cy = i / QPX;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        UB[((f * TY + cy) * n + l) * QPX + c] = 0;
+        UD[((f * TY + cy) * n + l) * QPX + c] = 0;
+      }
+    const bool inside = (cx0 + c / n < g.N) && (cy0 + cy < g.N);
+    if (!inside) continue;
+    for (int qj = 0; qj < n; ++qj) {
+      QPIn<2, Real> in;
+      Real vb[NF], vdx[NF], vdy[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Real b = 0, dx = 0, dy = 0;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          const int idx = (f * NPY + cy * P + l) * QPX + c;
+          b += tb.S[qj][l] * XB[idx];
+          dx += tb.S[qj][l] * XD[idx];
+          dy += tb.D[qj][l] * XB[idx];
+        }
+        vb[f] = b;
+        vdx[f] = dx;
+        vdy[f] = dy;
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        in.gu[k][0] = vdx[k];
+        in.gu[k][1] = vdy[k];
+      }
+      in.ph = vb[2];
+      in.gph[0] = vdx[2];
+      in.gph[1] = vdy[2];
+      QPOut<2, Real> o;
+      pw(tile, (long long)(cy * n + qj) * QPX + c, in, o);
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        const Real s = tb.S[qj][l], d = tb.D[qj][l];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          UB[((k * TY + cy) * n + l) * QPX + c] += d * o.cu[k][1];
+          UD[((k * TY + cy) * n + l) * QPX + c] += s * o.cu[k][0];
+        }
+        UB[((2 * TY + cy) * n + l) * QPX + c] += s * o.cv + d * o.cg[1];
+        UD[((2 * TY + cy) * n + l) * QPX + c] += s * o.cg[0];
+      }
+    }
+  }
+  __syncthreads();
+  // transposed x-pass into the node patch (sums over the cells sharing a node)
+  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
+    int ylo, yhi, xlo, xhi;
+    cells_of_node<P>(r, TY, ylo, yhi);
+    cells_of_node<P>(s, TX, xlo, xhi);
+    Real acc = 0;
+    for (int cy = ylo; cy <= yhi; ++cy) {
+      const int l = r - cy * P;
+      for (int cx = xlo; cx <= xhi; ++cx) {
+        const int k = s - cx * P;
+        const Real* ub = UB + ((f * TY + cy) * n + l) * QPX + cx * n;
+        const Real* ud = UD + ((f * TY + cy) * n + l) * QPX + cx * n;
+#pragma unroll
+        for (int qi = 0; qi < n; ++qi) acc += tb.S[qi][k] * ub[qi] + tb.D[qi][k] * ud[qi];
+      }
+    }
+    X[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
+    const int gx = x0 + s, gy = y0 + r;
+    if (gx >= g.n1 || gy >= g.n1) continue;
+    const long long node = gx + (long long)g.n1 * gy;
+    const bool low = (s == 0 && tx > 0) || (r == 0 && ty > 0);
+    const bool high = (s == NPX - 1 && tx < g.ntile[0] - 1) || (r == NPY - 1 && ty < g.ntile[1] - 1);
+    store_node(dst, src, flags, node, f * g.nn + node, f, 2, X[i], low, high, oa.outmask);
+  }
+}
+
+template <int P, typename Real>
+constexpr size_t op2d_smem() {
+  constexpr int TX = TileCfg<2, P>::TX, TY = TileCfg<2, P>::TY;
+  constexpr int n = P + 1, NF = 3, NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n;
+  return sizeof(Real) * (size_t)(NF * NPY * NPX + 2 * NF * NPY * QPX + 2 * NF * TY * n * QPX);
+}
+
+// ===========================================================================================
+// 3D operator kernel.
+template <int P, typename Real, class PW>
+__global__ void __launch_bounds__(256)
+k_op3d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char* __restrict__ flags,
+       Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
+  constexpr int TX = TileCfg<3, P>::TX, TY = TileCfg<3, P>::TY, TZ = TileCfg<3, P>::TZ;
+  constexpr int n = P + 1, NF = 4;
+  constexpr int NPX = TX * P + 1, NPY = TY * P + 1, NPZ = TZ * P + 1;
+  constexpr int QPX = TX * n, QPY = TY * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* X = reinterpret_cast<Real*>(smem_raw);          // [NF][NPZ][NPY][NPX]; later W* and output
+  Real* XB = X + NF * NPZ * NPY * NPX;                   // [NF][NPZ][NPY][QPX]
+  Real* XD = XB + NF * NPZ * NPY * QPX;
+  Real* YB = XD + NF * NPZ * NPY * QPX;                  // [NF][NPZ][QPY][QPX]
+  Real* YX = YB + NF * NPZ * QPY * QPX;
+  Real* YY = YX + NF * NPZ * QPY * QPX;
+  Real* ZB = YY + NF * NPZ * QPY * QPX;                  // [NF][TZ][n][QPY][QPX]
+  Real* ZX = ZB + NF * TZ * n * QPY * QPX;
+  Real* ZY = ZX + NF * TZ * n * QPY * QPX;
+
+  const long long tile = blockIdx.x;
+  const int tx = int(tile % g.ntile[0]);
+  const int ty = int((tile / g.ntile[0]) % g.ntile[1]);
+  const int tz = int(tile / ((long long)g.ntile[0] * g.ntile[1]));
+  const int x0 = tx * TX * P, y0 = ty * TY * P, z0 = tz * TZ * P;
+  const int cx0 = tx * TX, cy0 = ty * TY, cz0 = tz * TZ;
+  const long long n1 = g.n1, n1sq = n1 * n1;
+
+  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, r = (i / NPX) % NPY, t = (i / (NPX * NPY)) % NPZ, f = i / (NPX * NPY * NPZ);
+    const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
+    Real v = 0;
+    if (gx < g.n1 && gy < g.n1 && gz < g.n1) {
+      const long long node = gx + n1 * gy + n1sq * gz;
+      v = load_node(src, flags, node, f * g.nn + node, f, 3, oa.inmask);
+    }
+    X[i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NF * NPZ * NPY * QPX; i += blockDim.x) {
+    const int c = i % QPX, row = i / QPX;
+    const int cx = c / n, qi = c % n;
+    const Real* xr = X + row * NPX + cx * P;
+    Real b = 0, d = 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      b += tb.S[qi][k] * xr[k];
+      d += tb.D[qi][k] * xr[k];
+    }
+    XB[i] = b;
+    XD[i] = d;
+  }
+  __syncthreads();
+  // y-pass: YB = S_y XB, YX = S_y XD, YY = D_y XB
+  for (int i = threadIdx.x; i < NF * NPZ * QPY * QPX; i += blockDim.x) {
+    const int c = i % QPX, qyc = (i / QPX) % QPY, ft = i / (QPX * QPY);  // ft = f*NPZ + t
+    const int cy = qyc / n, qj = qyc % n;
+    Real b = 0, dx = 0, dy = 0;
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      const int idx = (ft * NPY + cy * P + l) * QPX + c;
+      b += tb.S[qj][l] * XB[idx];
+      dx += tb.S[qj][l] * XD[idx];
+      dy += tb.D[qj][l] * XB[idx];
+    }
+    YB[i] = b;
+    YX[i] = dx;
+    YY[i] = dy;
+  }
+  __syncthreads();
+  // z-pass, pointwise, transposed z-pass: one thread per (cell layer, Gauss column)
+  constexpr int PLANE = QPY * QPX;
+  for (int i = threadIdx.x; i < TZ * PLANE; i += blockDim.x) {
+    const int c = i % QPX, qyc = (i / QPX) % QPY, cz = i / PLANE;
+    const int col = qyc * QPX + c;
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        const int o = ((f * TZ + cz) * n + l) * PLANE + col;
+        ZB[o] = 0;
+        ZX[o] = 0;
+        ZY[o] = 0;
+      }
+    const bool inside = (cx0 + c / n < g.N) && (cy0 + qyc / n < g.N) && (cz0 + cz < g.N);
+    if (!inside) continue;
+    for (int qk = 0; qk < n; ++qk) {
+      Real vb[NF], vx[NF], vy[NF], vz[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        Real b = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          const int idx = (f * NPZ + cz * P + l) * PLANE + col;
+          const Real s = tb.S[qk][l];
+          b += s * YB[idx];
+          dx += s * YX[idx];
+          dy += s * YY[idx];
+          dz += tb.D[qk][l] * YB[idx];
+        }
+        vb[f] = b;
+        vx[f] = dx;
+        vy[f] = dy;
+        vz[f] = dz;
+      }
+      QPIn<3, Real> in;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        in.gu[k][0] = vx[k];
+        in.gu[k][1] = vy[k];
+        in.gu[k][2] = vz[k];
+      }
+      in.ph = vb[3];
+      in.gph[0] = vx[3];
+      in.gph[1] = vy[3];
+      in.gph[2] = vz[3];
+      QPOut<3, Real> o;
+      pw(tile, (long long)(cz * n + qk) * PLANE + col, in, o);
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        const Real s = tb.S[qk][l], d = tb.D[qk][l];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int oi = ((k * TZ + cz) * n + l) * PLANE + col;
+          ZB[oi] += d * o.cu[k][2];
+          ZX[oi] += s * o.cu[k][0];
+          ZY[oi] += s * o.cu[k][1];
+        }
+        const int oi = ((3 * TZ + cz) * n + l) * PLANE + col;
+        ZB[oi] += s * o.cv + d * o.cg[2];
+        ZX[oi] += s * o.cg[0];
+        ZY[oi] += s * o.cg[1];
+      }
+    }
+  }
+  __syncthreads();
+  // transposed y-pass into WB, WD [NF][NPZ][NPY][QPX] (reusing XB, XD)
+  Real* WB = XB;
+  Real* WD = XD;
+  for (int i = threadIdx.x; i < NF * NPZ * NPY * QPX; i += blockDim.x) {
+    const int c = i % QPX, r = (i / QPX) % NPY, t = (i / (QPX * NPY)) % NPZ, f = i / (QPX * NPY * NPZ);
+    int zlo, zhi, ylo, yhi;
+    cells_of_node<P>(t, TZ, zlo, zhi);
+    cells_of_node<P>(r, TY, ylo, yhi);
+    Real wb = 0, wd = 0;
+    for (int cz = zlo; cz <= zhi; ++cz) {
+      const int lz = t - cz * P;
+      for (int cy = ylo; cy <= yhi; ++cy) {
+        const int ly = r - cy * P;
+        const int base = ((f * TZ + cz) * n + lz) * PLANE + (cy * n) * QPX + c;
+#pragma unroll
+        for (int qj = 0; qj < n; ++qj) {
+          const int o = base + qj * QPX;
+          wb += tb.S[qj][ly] * ZB[o] + tb.D[qj][ly] * ZY[o];
+          wd += tb.S[qj][ly] * ZX[o];
+        }
+      }
+    }
+    WB[i] = wb;
+    WD[i] = wd;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, row = i / NPX;
+    int xlo, xhi;
+    cells_of_node<P>(s, TX, xlo, xhi);
+    Real acc = 0;
+    for (int cx = xlo; cx <= xhi; ++cx) {
+      const int k = s - cx * P;
+      const Real* wb = WB + row * QPX + cx * n;
+      const Real* wd = WD + row * QPX + cx * n;
+#pragma unroll
+      for (int qi = 0; qi < n; ++qi) acc += tb.S[qi][k] * wb[qi] + tb.D[qi][k] * wd[qi];
+    }
+    X[i] = acc;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
+    const int s = i % NPX, r = (i / NPX) % NPY, t = (i / (NPX * NPY)) % NPZ, f = i / (NPX * NPY * NPZ);
+    const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
+    if (gx >= g.n1 || gy >= g.n1 || gz >= g.n1) continue;
+    const long long node = gx + n1 * gy + n1sq * gz;
+    const bool low = (s == 0 && tx > 0) || (r == 0 && ty > 0) || (t == 0 && tz > 0);
+    const bool high = (s == NPX - 1 && tx < g.ntile[0] - 1) || (r == NPY - 1 && ty < g.ntile[1] - 1) ||
+                      (t == NPZ - 1 && tz < g.ntile[2] - 1);
+    store_node(dst, src, flags, node, f * g.nn + node, f, 3, X[i], low, high, oa.outmask);
+  }
+}
+
+template <int P, typename Real>
+constexpr size_t op3d_smem() {
+  constexpr int TX = TileCfg<3, P>::TX, TY = TileCfg<3, P>::TY, TZ = TileCfg<3, P>::TZ;
+  constexpr int n = P + 1, NF = 4, NPX = TX * P + 1, NPY = TY * P + 1, NPZ = TZ * P + 1;
+  constexpr int QPX = TX * n, QPY = TY * n;
+  return sizeof(Real) * (size_t)(NF * NPZ * NPY * NPX + 2 * NF * NPZ * NPY * QPX + 3 * NF * NPZ * QPY * QPX +
+                                 3 * NF * TZ * n * QPY * QPX);
+}
+
+}  // namespace pff

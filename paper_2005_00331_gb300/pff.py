@@ -1,0 +1,317 @@
+"""ctypes binding of libpff (argument marshalling only; every computation runs in the CUDA library).
+
+Vectors are torch tensors on the CUDA device, contiguous, float64 (or float32 where a precision
+argument says 32), in the component-blocked DoF layout [u_1 | ... | u_d | phi] of include/pff.h.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+PFF_SPLIT_NONE, PFF_SPLIT_MIEHE = 0, 1
+PFF_MODE_FULL, PFF_MODE_BLOCKDIAG, PFF_MODE_TRANSPOSE = 0, 1, 2
+PFF_MASK_RAW, PFF_MASK_ADJOINT = 4, 8
+PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT = 0x10, 0x20, 0x40
+PFF_PROF_OFF, PFF_PROF_JAC64_L0, PFF_PROF_JAC32_L0, PFF_PROF_JAC64, PFF_PROF_JAC32, PFF_PROF_RESIDUAL = range(6)
+
+_ERRORS = {-1: "invalid argument", -2: "out of device memory", -3: "CUDA error", -4: "non-finite value",
+           -5: "linear solver did not converge", -6: "Krylov breakdown", -7: "no state set"}
+
+
+class PFFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("n_cells_1d", ctypes.c_int),
+                ("coarse_min", ctypes.c_int), ("split", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("mu", ctypes.c_double), ("gc", ctypes.c_double),
+                ("eps", ctypes.c_double), ("kappa", ctypes.c_double), ("as_c", ctypes.c_double),
+                ("mg_precision", ctypes.c_int), ("cheb_degree", ctypes.c_int),
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int),
+                ("eig_seed", ctypes.c_ulonglong), ("gmres_restart", ctypes.c_int),
+                ("gmres_max_iters", ctypes.c_int), ("lin_rtol", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("res_norm", ctypes.c_double), ("gmres_rel", ctypes.c_double), ("gmres_iters", ctypes.c_int),
+                ("n_active", ctypes.c_int), ("n_changed", ctypes.c_int), ("status", ctypes.c_int),
+                ("t_residual_ms", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("t_solve_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+_P, _I, _D, _LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+_SIGS = {
+    "pff_default_params": (None, [ctypes.POINTER(Params)]),
+    "pff_setup_mesh": (_I, [ctypes.POINTER(_P), ctypes.POINTER(Params), _P]),
+    "pff_destroy": (None, [_P]),
+    "pff_sizes": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
+    "pff_level_sizes": (_I, [_P, _I, ctypes.POINTER(_LL), ctypes.POINTER(_I)]),
+    "pff_node_flags": (_I, [_P, _I, _P]),
+    "pff_set_state": (_I, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "pff_get_state": (_I, [_P, _P]),
+    "pff_get_active": (_I, [_P, _P]),
+    "pff_apply_jacobian": (_I, [_P, _I, _P, _P, _I, _I]),
+    "pff_residual": (_I, [_P, _P]),
+    "pff_diagonal": (_I, [_P, _I, _P, _I]),
+    "pff_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
+    "pff_level_state": (_I, [_P, _I, _P]),
+    "pff_prolongate": (_I, [_P, _I, _P, _P, _I]),
+    "pff_restrict": (_I, [_P, _I, _P, _P, _I]),
+    "pff_smooth": (_I, [_P, _I, _P, _P, _I]),
+    "pff_coarse_solve": (_I, [_P, _P, _P]),
+    "pff_vcycle": (_I, [_P, _P, _P]),
+    "pff_solve_linear": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "pff_solve_newton_step": (_I, [_P, _P, ctypes.POINTER(Report)]),
+    "pff_param_grad": (_I, [_P, _P, _P, _P, _P]),
+    "pff_strerror": (ctypes.c_char_p, [_I]),
+    "pff_profile": (_I, [_P, _I]),
+    "pff_profile_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+}
+
+
+def library_path():
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libpff.so")
+
+
+def load_library(build_if_missing=True):
+    """Loads libpff.so (building it in-tree if it is missing); raises if that fails."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libpff.so is not built (%s); run paper_2005_00331_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status, what):
+    if status != 0:
+        msg = load_library().pff_strerror(status).decode()
+        raise PFFError(status, "%s failed: %s (%d)" % (what, msg, status))
+
+
+def _ptr(t, dtype=torch.float64, numel=None):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype):
+        raise ValueError("expected a contiguous CUDA tensor of %s, got %s %s" % (dtype, t.dtype, t.device))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d entries, got %d" % (numel, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_params(**kw):
+    p = Params()
+    load_library().pff_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k == "lambda" else k, v)
+    return p
+
+
+class Context:
+    """Owns one pff_ctx: the mesh hierarchy of one problem and its Newton state."""
+
+    def __init__(self, params, stream=None):
+        lib = load_library()
+        self._lib = lib
+        self.params = params
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.pff_setup_mesh(ctypes.byref(h), ctypes.byref(params), ctypes.c_void_p(self.stream.cuda_stream)),
+               "pff_setup_mesh")
+        self._h = h
+        nd, nn, nl = _LL(), _LL(), _I()
+        _check(lib.pff_sizes(h, ctypes.byref(nd), ctypes.byref(nn), ctypes.byref(nl)), "pff_sizes")
+        self.n_dofs, self.n_nodes, self.n_levels = nd.value, nn.value, nl.value
+        self.dim = params.dim
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pff_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def level_sizes(self, level):
+        nn, N = _LL(), _I()
+        _check(self._lib.pff_level_sizes(self._h, level, ctypes.byref(nn), ctypes.byref(N)), "pff_level_sizes")
+        return nn.value, N.value
+
+    def _dev(self):
+        return torch.device("cuda", torch.cuda.current_device())
+
+    def node_flags(self, level=0):
+        nn, _ = self.level_sizes(level)
+        out = torch.empty(nn, dtype=torch.uint8, device=self._dev())
+        _check(self._lib.pff_node_flags(self._h, level, _ptr(out, torch.uint8)), "pff_node_flags")
+        return out
+
+    def set_state(self, U, phi_old, phi_tilde=None, active=None, gc_field=None, lambda_field=None, mu_field=None):
+        nn = self.n_nodes
+        _check(self._lib.pff_set_state(self._h, _ptr(U, numel=self.n_dofs), _ptr(phi_old, numel=nn),
+                                       _ptr(phi_tilde, numel=nn), _ptr(active, torch.uint8, nn),
+                                       _ptr(gc_field, numel=nn), _ptr(lambda_field, numel=nn),
+                                       _ptr(mu_field, numel=nn)), "pff_set_state")
+
+    def get_state(self):
+        out = torch.empty(self.n_dofs, dtype=torch.float64, device=self._dev())
+        _check(self._lib.pff_get_state(self._h, _ptr(out)), "pff_get_state")
+        return out
+
+    def get_active(self):
+        out = torch.empty(self.n_nodes, dtype=torch.uint8, device=self._dev())
+        _check(self._lib.pff_get_active(self._h, _ptr(out, torch.uint8)), "pff_get_active")
+        return out
+
+    def _level_nd(self, level):
+        return (self.dim + 1) * self.level_sizes(level)[0]
+
+    def apply_jacobian(self, x, y=None, level=0, mode=PFF_MODE_FULL, precision=None):
+        prec = precision or (32 if x.dtype == torch.float32 else 64)
+        dt = torch.float32 if prec == 32 else torch.float64
+        nd = self._level_nd(level)
+        if y is None:
+            y = torch.empty(nd, dtype=dt, device=x.device)
+        _check(self._lib.pff_apply_jacobian(self._h, level, _ptr(x, dt, nd), _ptr(y, dt, nd), prec, mode),
+               "pff_apply_jacobian")
+        return y
+
+    def residual(self, r=None):
+        if r is None:
+            r = torch.empty(self.n_dofs, dtype=torch.float64, device=self._dev())
+        _check(self._lib.pff_residual(self._h, _ptr(r, numel=self.n_dofs)), "pff_residual")
+        return r
+
+    def diagonal(self, level=0, precision=64):
+        dt = torch.float32 if precision == 32 else torch.float64
+        out = torch.empty(self._level_nd(level), dtype=dt, device=self._dev())
+        _check(self._lib.pff_diagonal(self._h, level, _ptr(out, dt), precision), "pff_diagonal")
+        return out
+
+    def lambda_max(self, level=0):
+        arr = (_D * 2)()
+        _check(self._lib.pff_lambda_max(self._h, level, arr), "pff_lambda_max")
+        return [arr[0], arr[1]]
+
+    def level_state(self, level):
+        out = torch.empty(self._level_nd(level), dtype=torch.float64, device=self._dev())
+        _check(self._lib.pff_level_state(self._h, level, _ptr(out)), "pff_level_state")
+        return out
+
+    def prolongate(self, level, xc, precision=64):
+        dt = torch.float32 if precision == 32 else torch.float64
+        y = torch.empty(self._level_nd(level), dtype=dt, device=xc.device)
+        _check(self._lib.pff_prolongate(self._h, level, _ptr(xc, dt, self._level_nd(level + 1)), _ptr(y, dt),
+                                        precision), "pff_prolongate")
+        return y
+
+    def restrict(self, level, xf, precision=64):
+        dt = torch.float32 if precision == 32 else torch.float64
+        y = torch.empty(self._level_nd(level + 1), dtype=dt, device=xf.device)
+        _check(self._lib.pff_restrict(self._h, level, _ptr(xf, dt, self._level_nd(level)), _ptr(y, dt), precision),
+               "pff_restrict")
+        return y
+
+    def smooth(self, level, f, precision=64):
+        dt = torch.float32 if precision == 32 else torch.float64
+        x = torch.empty(self._level_nd(level), dtype=dt, device=f.device)
+        _check(self._lib.pff_smooth(self._h, level, _ptr(f, dt, self._level_nd(level)), _ptr(x, dt), precision),
+               "pff_smooth")
+        return x
+
+    def coarse_solve(self, r):
+        z = torch.empty_like(r)
+        _check(self._lib.pff_coarse_solve(self._h, _ptr(r, numel=self._level_nd(self.n_levels - 1)), _ptr(z)),
+               "pff_coarse_solve")
+        return z
+
+    def vcycle(self, r, z=None):
+        z = torch.empty_like(r) if z is None else z
+        _check(self._lib.pff_vcycle(self._h, _ptr(r, numel=self.n_dofs), _ptr(z, numel=self.n_dofs)), "pff_vcycle")
+        return z
+
+    def solve_linear(self, b, x=None, check=True):
+        x = torch.empty_like(b) if x is None else x
+        its, rel = _I(), _D()
+        st = self._lib.pff_solve_linear(self._h, _ptr(b, numel=self.n_dofs), _ptr(x, numel=self.n_dofs),
+                                        ctypes.byref(its), ctypes.byref(rel))
+        if check:
+            _check(st, "pff_solve_linear")
+        return x, its.value, rel.value
+
+    def solve_newton_step(self, U_out=None, check=True):
+        rep = Report()
+        st = self._lib.pff_solve_newton_step(self._h, _ptr(U_out, numel=self.n_dofs), ctypes.byref(rep))
+        if check:
+            _check(st, "pff_solve_newton_step")
+        return rep.as_dict()
+
+    def profile(self, family):
+        """Starts timing one kernel family (PFF_PROF_*); 0 switches it off."""
+        _check(self._lib.pff_profile(self._h, family), "pff_profile")
+
+    def profile_result(self):
+        n, ms = _I(), _D()
+        _check(self._lib.pff_profile_result(self._h, ctypes.byref(n), ctypes.byref(ms)), "pff_profile_result")
+        return n.value, ms.value
+
+    def param_grad(self, v):
+        outs = [torch.empty(self.n_nodes, dtype=torch.float64, device=v.device) for _ in range(3)]
+        _check(self._lib.pff_param_grad(self._h, _ptr(v, numel=self.n_dofs), *[_ptr(o) for o in outs]),
+               "pff_param_grad")
+        return outs
+
+
+def setup_mesh(dim=2, degree=1, n_cells_1d=32, stream=None, **kw):
+    """Creates a Context (pff_setup_mesh) with the library defaults overridden by ``kw``."""
+    p = default_params(dim=dim, degree=degree, n_cells_1d=n_cells_1d, **kw)
+    return Context(p, stream)
+
+
+class ResidualFunction(torch.autograd.Function):
+    """R(U; G_c, lambda, mu) of Eq. (residual) with Dirichlet rows 0, differentiable in U and in the
+    nodal material fields. Backward: dR/dU^T v is the transpose Jacobian apply with the Dirichlet rows
+    of v removed (PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT); dR/dfield^T v comes from pff_param_grad.
+    phi_old and phi~ are constants (G is the derivative with phi~ frozen)."""
+
+    @staticmethod
+    def forward(fctx, ctx, U, phi_old, phi_tilde, gc_field, lambda_field, mu_field):
+        active = torch.zeros(ctx.n_nodes, dtype=torch.uint8, device=U.device)
+        ctx.set_state(U.detach().contiguous(), phi_old, phi_tilde, active, gc_field.detach().contiguous(),
+                      lambda_field.detach().contiguous(), mu_field.detach().contiguous())
+        fctx.ctx = ctx
+        fctx.save_for_backward(U, phi_old, phi_tilde, gc_field, lambda_field, mu_field, active)
+        return ctx.residual()
+
+    @staticmethod
+    def backward(fctx, v):
+        U, phi_old, phi_tilde, gc, lam, mu, active = fctx.saved_tensors
+        ctx = fctx.ctx
+        ctx.set_state(U.detach().contiguous(), phi_old, phi_tilde, active, gc.detach().contiguous(),
+                      lam.detach().contiguous(), mu.detach().contiguous())
+        v = v.contiguous()
+        gU = ctx.apply_jacobian(v, mode=PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT)
+        g_gc, g_lam, g_mu = ctx.param_grad(v)
+        return None, gU, None, None, g_gc, g_lam, g_mu

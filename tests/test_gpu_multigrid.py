@@ -1,0 +1,183 @@
+"""GPU parity of the multigrid pieces (Sec. 3.3) and of the Newton step (Alg. 1) against the oracle.
+
+Level data, transfers and the diagonal are FP64 computations compared at 1e-12. Pieces that
+depend on the CG-Lanczos eigenvalue estimate (smoother, V-cycle) are compared at 1e-9: the
+estimate itself is a 15-step Krylov process whose rounding differs between the two summation
+orders. Solves are compared through their FP64 residuals (linear tolerance 1e-6 of Sec. 6.2)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fe, solvers as S
+from problems import Problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(a), np.linalg.norm(b), 1e-300)
+
+
+def cuda(a, dtype=np.float64):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+MG_CASES = [(2, 1, 16, 0), (2, 2, 8, 1), (2, 3, 8, 1), (2, 4, 4, 0), (3, 1, 8, 1), (3, 2, 4, 0)]
+
+
+def oracle_levels(pr, cheb_degree=5):
+    return S.build_levels(pr.dim, pr.p, pr.N, pr.prm, pr.U, pr.phi_tilde, pr.active, cheb_degree=cheb_degree,
+                          eig_iters=15, eig_seed=0, coarse_min=3, **pr.fields)
+
+
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_levels_diagonal_transfers(dim, p, N, split):
+    pr = Problem(dim, p, N, split=split, seed=3, active_frac=0.25)
+    lv = oracle_levels(pr)
+    ctx = pr.context()
+    assert ctx.n_levels == len(lv)
+    for l, L in enumerate(lv):
+        # state carried to the level, active bits, masked diagonal
+        assert rel(ctx.level_state(l).cpu().numpy(), L.U) <= 1e-13
+        fl = ctx.node_flags(l).cpu().numpy()
+        np.testing.assert_array_equal(((fl >> dim) & 1).astype(bool), L.active)
+        assert rel(ctx.diagonal(l).cpu().numpy(), L.diag) <= 1e-12
+        if l + 1 < len(lv):
+            Lc = lv[l + 1]
+            nnc, nnf = Lc.mesh.n_nodes, L.mesh.n_nodes
+            xc = np.random.default_rng(l).normal(size=Lc.mesh.n_dofs)
+            ref = np.concatenate([Lc.P @ xc[c * nnc:(c + 1) * nnc] for c in range(dim + 1)])
+            ref[L.mask] = 0.0
+            assert rel(ctx.prolongate(l, cuda(xc)).cpu().numpy(), ref) <= 1e-13
+            xf = np.random.default_rng(l + 50).normal(size=L.mesh.n_dofs)
+            xfm = np.where(L.mask, 0.0, xf)
+            ref = np.concatenate([Lc.P.T @ xfm[c * nnf:(c + 1) * nnf] for c in range(dim + 1)])
+            ref[Lc.mask] = 0.0
+            assert rel(ctx.restrict(l, cuda(xf)).cpu().numpy(), ref) <= 1e-13
+            # FP32 transfers
+            assert rel(ctx.restrict(l, cuda(xf, np.float32), precision=32).cpu().numpy(), ref) <= 1e-6
+
+
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_level_operators(dim, p, N, split):
+    pr = Problem(dim, p, N, split=split, seed=4, active_frac=0.2)
+    lv = oracle_levels(pr)
+    ctx = pr.context()
+    for l in range(1, len(lv)):
+        x = np.random.default_rng(l).normal(size=lv[l].mesh.n_dofs)
+        y = ctx.apply_jacobian(cuda(x), level=l).cpu().numpy()
+        assert rel(y, lv[l].G @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_eigen_smoother_coarse_vcycle_fp64(dim, p, N, split):
+    pr = Problem(dim, p, N, split=split, seed=5, active_frac=0.2)
+    lv = oracle_levels(pr, cheb_degree=5)
+    ctx = pr.context(mg_precision=64)
+    for l in range(len(lv) - 1):
+        lam = ctx.lambda_max(l)
+        assert abs(lam[0] - lv[l].lam_max[0]) <= 1e-9 * lv[l].lam_max[0]
+        assert abs(lam[1] - lv[l].lam_max[1]) <= 1e-9 * lv[l].lam_max[1]
+        f = np.where(lv[l].mask, 0.0, np.random.default_rng(l).normal(size=lv[l].mesh.n_dofs))
+        assert rel(ctx.smooth(l, cuda(f)).cpu().numpy(), S.smooth(lv[l], f)) <= 1e-9
+    Lc = lv[-1]
+    r = np.where(Lc.mask, 0.0, np.random.default_rng(9).normal(size=Lc.mesh.n_dofs))
+    assert rel(ctx.coarse_solve(cuda(r)).cpu().numpy(), spla.spsolve(Lc.G.tocsc(), r)) <= 1e-10
+    r = np.where(lv[0].mask, 0.0, np.random.default_rng(10).normal(size=pr.mesh.n_dofs))
+    z = ctx.vcycle(cuda(r)).cpu().numpy()
+    assert rel(z, S.vcycle(lv, r)) <= 1e-9
+
+
+@pytest.mark.parametrize("dim,p,N,split", [(2, 2, 8, 1), (3, 1, 8, 0)])
+def test_vcycle_fp32(dim, p, N, split):
+    """Mixed precision: FP32 levels, FP64 coarse solve; agrees with the FP64 cycle to FP32 accuracy."""
+    pr = Problem(dim, p, N, split=split, seed=6, active_frac=0.2)
+    lv = oracle_levels(pr)
+    ctx = pr.context(mg_precision=32)
+    r = np.where(lv[0].mask, 0.0, np.random.default_rng(11).normal(size=pr.mesh.n_dofs))
+    z = ctx.vcycle(cuda(r)).cpu().numpy()
+    assert rel(z, S.vcycle(lv, r)) <= 1e-3
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("dim,p,N,split", [(2, 2, 16, 1), (3, 2, 4, 1)])
+def test_fgmres_solve(prec, dim, p, N, split):
+    pr = Problem(dim, p, N, split=split, seed=7, active_frac=0.1)
+    ctx = pr.context(mg_precision=prec)
+    Gm = fe.masked(pr.G(), pr.mask)
+    b = np.where(pr.mask, 0.0, np.random.default_rng(12).normal(size=pr.mesh.n_dofs))
+    x, its, relres = ctx.solve_linear(cuda(b))
+    x = x.cpu().numpy()
+    assert np.linalg.norm(Gm @ x - b) <= 1.01e-6 * np.linalg.norm(b)
+    assert its < 60
+    xd = spla.spsolve(Gm.tocsc(), b)
+    assert rel(x, xd) <= 1e-3
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_newton_step_c1(split):
+    """The tension test of the paper at 32 x 32 Q1 (3267 DoFs): one primal-dual active-set step with
+    GMG-preconditioned FGMRES against the oracle's step with a direct solve."""
+    from oracle import mesh as M
+    m = M.Mesh(2, 1, 32)
+    prm = fe.Params(121.15, 80.77, 2.7e-3, 2.0 / 32, 1e-10, split)
+    U = m.dirichlet_values(1e-3)
+    phi = np.ones(m.n_nodes)
+    phi[m.slit_nodes()] = 0.0
+    U[2 * m.n_nodes:] = phi
+    from paper_2005_00331_gb300 import setup_mesh
+    for prec in (64, 32):
+        ctx = setup_mesh(dim=2, degree=1, n_cells_1d=32, split=split, eps=2.0 / 32, mg_precision=prec)
+        ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
+        Uo, act, rn, _ = S.pdas_step(m, prm, U, phi, phi)
+        rep = ctx.solve_newton_step()
+        np.testing.assert_array_equal(ctx.get_active().cpu().numpy().astype(bool), act)
+        assert abs(rep["res_norm"] - rn) <= 1e-12 * rn
+        Ug = ctx.get_state().cpu().numpy()
+        assert np.linalg.norm(Ug - Uo) <= 1e-4 * np.linalg.norm(Uo - U)
+        assert rep["gmres_rel"] <= 1e-6
+
+
+def test_pdas_loop_reaches_newton_tolerance():
+    """Alg. 1 repeated on the GPU until the active set is unchanged and ||R~|| <= 1e-8 ||R~_0||; the final
+    residual is re-checked by the oracle in FP64."""
+    from oracle import mesh as M
+    from paper_2005_00331_gb300 import setup_mesh
+    m = M.Mesh(2, 1, 16)
+    prm = fe.Params(121.15, 80.77, 2.7e-3, 2.0 / 16, 1e-10, 1)
+    U = m.dirichlet_values(1e-3)
+    phi = np.ones(m.n_nodes)
+    phi[m.slit_nodes()] = 0.0
+    U[2 * m.n_nodes:] = phi
+    ctx = setup_mesh(dim=2, degree=1, n_cells_1d=16, split=1, eps=2.0 / 16, mg_precision=32, lin_rtol=1e-10)
+    ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
+    norms, changed = [], []
+    for k in range(15):
+        rep = ctx.solve_newton_step()
+        norms.append(rep["res_norm"])
+        changed.append(rep["n_changed"])
+        if k > 0 and rep["n_changed"] == 0 and rep["res_norm"] <= 1e-8 * norms[0]:
+            break
+    assert norms[-1] <= 1e-8 * norms[0] and changed[-1] == 0
+    Ug = ctx.get_state().cpu().numpy()
+    R = fe.residual(m, prm, Ug, phi)
+    act = ctx.get_active().cpu().numpy().astype(bool)
+    mask = S.newton_mask(m, act)
+    assert np.linalg.norm(np.where(mask, 0, R)) <= 1e-7 * norms[0]
+
+
+@pytest.mark.parametrize("dim,p,N,split", [(2, 2, 6, 1), (3, 1, 4, 0), (2, 3, 4, 0)])
+def test_param_grad_and_adjoint(dim, p, N, split):
+    pr = Problem(dim, p, N, split=split, seed=8, fields=True)
+    ctx = pr.context()
+    v = np.random.default_rng(13).normal(size=pr.mesh.n_dofs)
+    vm = np.where(pr.mesh.dirichlet_mask(), 0.0, v)
+    g = [t.cpu().numpy() for t in ctx.param_grad(cuda(v))]
+    ref = fe.param_grad(pr.mesh, pr.prm, pr.U, pr.phi_tilde, vm, **pr.fields)
+    for a, b in zip(g, ref):
+        assert rel(a, b) <= 1e-12
+    from paper_2005_00331_gb300 import PFF_MASK_ADJOINT, PFF_MODE_TRANSPOSE
+    gU = ctx.apply_jacobian(cuda(v), mode=PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT).cpu().numpy()
+    assert rel(gU, pr.G().T @ vm) <= 1e-12

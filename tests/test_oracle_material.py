@@ -111,3 +111,20 @@ def test_degradation():
     h = 1e-6
     np.testing.assert_allclose(mat.dg(phi, k), (mat.g(phi + h, k) - mat.g(phi - h, k)) / (2 * h), atol=1e-9)
     assert mat.g(0.0, k) == k and abs(mat.g(1.0, k) - 1.0) < 1e-16
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_noise_eigenvalues_are_zero(d):
+    """An eigenvalue at rounding-noise level (relative 1e-17) of either sign gives the tangent of an
+    exact zero eigenvalue (H(0) = 1), and the trace switch likewise."""
+    base = np.zeros((1, d, d))
+    base[0, d - 1, d - 1] = 1e-3
+    Tz = mat.tangent4(base, LAM, MU, 0.3, mat.SPLIT_MIEHE)
+    for s in (1.0, -1.0):
+        e = base.copy()
+        e[0, 0, 0] = s * 1e-20
+        np.testing.assert_allclose(mat.tangent4(e, LAM, MU, 0.3, mat.SPLIT_MIEHE), Tz, rtol=1e-12, atol=1e-9)
+    # without the snap the negative noise eigenvalue would switch H: check the switch is real
+    e = base.copy()
+    e[0, 0, 0] = -1e-6
+    assert np.abs(mat.tangent4(e, LAM, MU, 0.3, mat.SPLIT_MIEHE) - Tz).max() > 1.0
