@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the phase-field fracture hot path on one GB300 (or N replicas).
+
+Default workload: the 2D notched specimen with Q2 elements on 256 x 256 cells (789,507 DoFs),
+seeded state u ~ N(0, (1e-3)^2), phi ~ U(0.9, 1) with phi = 0 on the slit, phi_old slightly above
+phi (about half of the phase-field DoFs end up in the active set). One step is one pass of the
+whole hot path: set_state (per-point tangent data), residual, active set (Alg. 1), multigrid
+setup (state transfer, diagonals, eigenvalue estimates, dense coarse inverse), flexible GMRES
+with the monolithic GMG preconditioner to 1e-6, and the Newton update. The multigrid runs in
+FP32 (mixed precision) unless --mg-precision 64.
+
+value = DoFs processed per second of full Newton steps (n_dofs * steps / time, summed over
+ranks). Extra keys: the Jacobian-apply sweep (p = 1..4, FP64 and FP32), the Newton step with the
+FP64 multigrid, the roofline of the dominant kernel, the end-to-end figure through host buffers,
+SM clocks during the timed region and the CPU oracle baseline.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+METRIC = "Jacobian-apply DoF/s (% HBM roofline) and s per Newton step, FP64 vs mixed GMG"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--degree", type=int, default=2)
+    ap.add_argument("--cells", type=int, default=256)
+    ap.add_argument("--split", type=int, default=1)
+    ap.add_argument("--mg-precision", type=int, default=32)
+    ap.add_argument("--cheb-degree", type=int, default=5)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    n1 = a.degree * a.cells + 1
+    nd = (a.dim + 1) * n1 ** a.dim
+    return "%dD Q%d %s notched specimen, %d DoFs, split %s, PDAS Newton step with %s GMG" % (
+        a.dim, a.degree, "x".join([str(a.cells)] * a.dim), nd, "miehe" if a.split else "none",
+        "FP32 (mixed)" if a.mg_precision == 32 else "FP64")
+
+
+# ---- synthetic state (inputs module + the library's own node flags) -------------------------
+def make_state(ctx, a, seed=0):
+    import torch
+
+    from paper_2005_00331_gb300 import PFF_FLAG_SLIT, PFF_FLAG_TOP, inputs
+    nn, dim = ctx.n_nodes, a.dim
+    fl = ctx.node_flags().cpu().numpy()
+    U = np.zeros(ctx.n_dofs)
+    dmask = np.concatenate([((fl >> c) & 1).astype(bool) for c in range(dim)])
+    U[:dim * nn] = np.where(dmask, 0.0, inputs.displacement_noise(nn, dim, seed, std=1e-3))
+    U[(dim - 1) * nn:dim * nn][(fl & PFF_FLAG_TOP) != 0] = 1e-3
+    phi = inputs.uniform_phase(nn, seed)
+    phi[(fl & PFF_FLAG_SLIT) != 0] = 0.0
+    U[dim * nn:] = phi
+    phi_old = inputs.phi_old_above(phi, seed)
+    return U, phi_old
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return p.get("hbm_gbs"), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+def qp_values(dim, split):
+    nm = 3 if dim == 2 else 6
+    return (2 + nm + 2) if split == 0 else (nm * (nm + 1) // 2 + nm + 2)
+
+
+def apply_bytes_per_dof(dim, p, split, real_bytes):
+    """Algorithmic bytes per DoF of one Jacobian apply with stored per-point data: read x, write y,
+    read the per-point data ((p+1)^dim points of qp_values each per cell) and one flag byte per
+    node; (d+1) p^d DoFs per cell asymptotically."""
+    dofs_per_cell = (dim + 1) * p ** dim
+    per_cell = qp_values(dim, split) * (p + 1) ** dim * real_bytes
+    return 2 * real_bytes + per_cell / dofs_per_cell + 1.0 / (dim + 1)
+
+
+def apply_flops_per_dof(dim, p, split):
+    """Floating-point operations per DoF of one Jacobian apply as the kernels k_op2d / k_op3d do it
+    (two per fused multiply-add; amortised over large tiles, seams neglected). n = p + 1 points per
+    direction; per cell: x-pass, y-pass (3D), fused last-direction pass with the pointwise tangent
+    and its transpose, then the transposed passes back to the nodes."""
+    n = p + 1
+    if dim == 2:
+        pw = 20 if split else 12
+        fma = 6 * n * n * p + 9 * n ** 3 + 7 * n ** 3 + 6 * n * p * p + pw * n * n
+        return 2.0 * fma / (3 * p * p)
+    pw = 56 if split else 22
+    fma = (8 * n * n * p * p + 12 * p * n ** 3 + 16 * n ** 4 + 13 * n ** 4 + 12 * n * n * p * p + 8 * n * p ** 3
+           + pw * n ** 3)
+    return 2.0 * fma / (4 * p ** 3)
+
+
+# ---- native arm ------------------------------------------------------------------------------
+def run_native(a, rank, world):
+    import torch
+
+    from paper_2005_00331_gb300 import PFF_PROF_JAC32_L0, PFF_PROF_JAC64_L0, PFF_PROF_OFF, launch_count, setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    eps = 2.0 / a.cells
+    ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=eps,
+                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree)
+    U_h, phi_old_h = make_state(ctx, a, seed=rank)
+    U = torch.from_numpy(U_h).to(dev)
+    phi_old = torch.from_numpy(phi_old_h).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    nd = ctx.n_dofs
+
+    def step():
+        ctx.set_state(U, phi_old, phi_old, None)
+        return ctx.solve_newton_step(check=False)
+
+    for _ in range(a.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+    prof_family = PFF_PROF_JAC32_L0 if a.mg_precision == 32 else PFF_PROF_JAC64_L0
+    ctx.profile(prof_family)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    reps = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n_launch0 = launch_count()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        for i in range(a.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            reps.append(step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+    n_launch = launch_count() - n_launch0
+    if world > 1:
+        torch.distributed.barrier()
+    launches, kern_ms = ctx.profile_result()
+    ctx.profile(PFF_PROF_OFF)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    ms = sum(step_ms) / len(step_ms)
+    out = {"step_ms": ms, "wall_ms": (t1 - t0) * 1e3 / a.steps, "reports": reps, "clocks": clk.summary(),
+           "kern_launches": launches, "kern_ms": kern_ms, "n_dofs": nd, "launches": n_launch}
+
+    # end to end through the C-ABI with host buffers: H2D of the state, step, D2H of the result
+    U_pin = torch.from_numpy(U_h).pin_memory()
+    po_pin = torch.from_numpy(phi_old_h).pin_memory()
+    U_back = torch.empty(nd, dtype=torch.float64).pin_memory()
+    U_d = torch.empty(nd, dtype=torch.float64, device=dev)
+    po_d = torch.empty_like(phi_old)
+    e2e = []
+    for i in range(0 if a.no_e2e else max(2, min(a.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        U_d.copy_(U_pin, non_blocking=True)
+        po_d.copy_(po_pin, non_blocking=True)
+        ctx.set_state(U_d, po_d, po_d, None)
+        ctx.solve_newton_step(U_out=U_d, check=False)
+        U_back.copy_(U_d, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t)
+    out["e2e_s"] = statistics.median(e2e) if e2e else float("nan")
+    out["h2d"] = 8 * (nd + ctx.n_nodes)
+    out["d2h"] = 8 * nd
+
+    if not a.no_sweep and rank == 0:
+        out["sweep"] = apply_sweep(a, dev, flush)
+        # the same Newton step with the FP64 multigrid
+        ctx64 = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=eps,
+                           mg_precision=64, cheb_degree=a.cheb_degree)
+        ctx64.set_state(U, phi_old, phi_old, None)
+        ctx64.solve_newton_step(check=False)
+        t64 = []
+        rep64 = None
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx64.set_state(U, phi_old, phi_old, None)
+            rep64 = ctx64.solve_newton_step(check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64.append(e0.elapsed_time(e1))
+        # agreement of the two Newton updates
+        Um = ctx.get_state()
+        ctx.set_state(U, phi_old, phi_old, None)
+        ctx.solve_newton_step(check=False)
+        Um = ctx.get_state()
+        U64 = ctx64.get_state()
+        out["fp64_mg"] = {"step_ms": min(t64), "gmres_iters": rep64["gmres_iters"], "status": rep64["status"],
+                          "rel_diff_vs_mixed": float((Um - U64).norm() / (U64 - U).norm())}
+        ctx64.close()
+    ctx.close()
+    return out
+
+
+def apply_sweep(a, dev, flush, reps=20):
+    """Jacobian apply at p = 1..4 on the 2D 256^2 mesh, FP64 and FP32, L2 flushed before each."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    res = {}
+    stream = torch.cuda.current_stream()
+    for p in (1, 2, 3, 4):
+        b = argparse.Namespace(**vars(a))
+        b.degree = p
+        ctx = setup_mesh(dim=a.dim, degree=p, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                         mg_precision=32)
+        U_h, po_h = make_state(ctx, b, seed=0)
+        U = torch.from_numpy(U_h).to(dev)
+        po = torch.from_numpy(po_h).to(dev)
+        nn = ctx.n_nodes
+        act = (po - U[a.dim * nn:] < 1e-8).to(torch.uint8)  # the configured rule: phi_old - phi < 1e-8
+        ctx.set_state(U, po, po, act.contiguous())
+        for prec, dt in ((64, torch.float64), (32, torch.float32)):
+            x = torch.randn(ctx.n_dofs, dtype=torch.float64, device=dev).to(dt)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                ctx.apply_jacobian(x, y)
+            times = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.apply_jacobian(x, y)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            med = statistics.median(times)
+            nbytes = apply_bytes_per_dof(a.dim, p, a.split, 8 if prec == 64 else 4) * ctx.n_dofs
+            flops = apply_flops_per_dof(a.dim, p, a.split) * ctx.n_dofs
+            res["p%d_fp%d" % (p, prec)] = {
+                "dofs": ctx.n_dofs, "median_ms": med, "best_ms": min(times),
+                "dofs_per_s": ctx.n_dofs / (med * 1e-3), "GB_per_s": nbytes / (med * 1e-3) / 1e9,
+                "TFLOP_per_s": flops / (med * 1e-3) / 1e12}
+        ctx.close()
+    return res
+
+
+# ---- CPU oracle baseline ----------------------------------------------------------------------
+CPU_SAMPLE_CELLS = 32
+
+
+def cpu_oracle_sample(a, seconds_cap=30.0):
+    """Times the oracle's PDAS Newton step (FGMRES + V-cycle, sparse direct coarse solve) on the
+    same specimen family with CPU_SAMPLE_CELLS cells per direction, in one single-threaded process."""
+    code = r'''
+import json, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import fe, mesh as M, solvers as S
+from paper_2005_00331_gb300 import inputs
+dim, p, N, split = %d, %d, %d, %d
+m = M.Mesh(dim, p, N)
+prm = fe.Params(eps=2.0 / N, split=split)
+nn = m.n_nodes
+U = m.dirichlet_values(1e-3)
+U[:dim * nn] += np.where(m.dirichlet_mask()[:dim * nn], 0.0, inputs.displacement_noise(nn, dim, 0))
+phi = inputs.uniform_phase(nn, 0)
+phi[m.slit_nodes()] = 0.0
+U[dim * nn:] = phi
+po = inputs.phi_old_above(phi, 0)
+t = time.perf_counter()
+S.pdas_step(m, prm, U, po, po, solve="gmg", levels_kw=dict(cheb_degree=%d))
+dt = time.perf_counter() - t
+print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt}))
+''' % (ROOT, a.dim, a.degree, CPU_SAMPLE_CELLS, a.split, a.cheb_degree)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["n_dofs"] / d["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": "one oracle PDAS Newton step (FGMRES + GMG) on the %dD Q%d notched specimen with %d^%d "
+                      "cells (%d DoFs), %.1f s" % (a.dim, a.degree, CPU_SAMPLE_CELLS, a.dim, d["n_dofs"],
+                                                   d["seconds"])}
+
+
+# ---- main --------------------------------------------------------------------------------------
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    config = {"workload": workload_name(a), "dim": a.dim, "degree": a.degree, "cells_per_dir": a.cells,
+              "split": "miehe" if a.split else "none", "mg_precision": a.mg_precision,
+              "cheb_degree": a.cheb_degree, "linear_rtol": 1e-6, "parallelism": "replicas" if world > 1 else "1 GPU",
+              "l2": "256 MB buffer written before every timed step (flushes the 135 MB L2)"}
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        t = time.perf_counter()
+        vals = []
+        for _ in range(a.steps):
+            c = cpu_oracle_sample(a)
+            if "error" in c:
+                print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + c["error"][-200:]}))
+                return
+            vals.append(c)
+        v = statistics.median([c["value"] for c in vals])
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF/s", "n_gpus": a.gpus,
+                "steps": a.steps, "warmup": 0, "ms_per_step": (time.perf_counter() - t) * 1e3 / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": vals[0]["sample"]},
+                "e2e": {"value": v, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    r = run_native(a, rank, world)
+    ms = r["step_ms"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = r["n_dofs"] * world / (ms * 1e-3)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    hbm, hbm_kind = peaks()
+    real_bytes = 4 if a.mg_precision == 32 else 8
+    per_launch = r["kern_ms"] / max(1, r["kern_launches"])
+    bpd = apply_bytes_per_dof(a.dim, a.degree, a.split, real_bytes)
+    achieved = bpd * r["n_dofs"] / (per_launch * 1e-3) / 1e9 if r["kern_launches"] else None
+    rep = r["reports"][-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 outer / f32 multigrid" if a.mg_precision == 32 else "f64", "data": "synthetic",
+        "config": config,
+        "newton": {"gmres_iters": rep["gmres_iters"], "gmres_rel": rep["gmres_rel"], "status": rep["status"],
+                   "n_active": rep["n_active"], "res_norm": rep["res_norm"],
+                   "t_residual_ms": rep["t_residual_ms"], "t_setup_ms": rep["t_setup_ms"],
+                   "t_solve_ms": rep["t_solve_ms"], "wall_ms_per_step": r["wall_ms"]},
+        "roofline": {"kernel": "k_op%dd Jacobian apply, FP%d, finest level, inside the timed steps" % (a.dim, real_bytes * 8),
+                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "peak_kind": hbm_kind, "launches": r["kern_launches"], "avg_launch_ms": per_launch,
+                     "bytes_per_dof": bpd},
+        "e2e": {"value": r["n_dofs"] * world / r["e2e_s"], "unit": "DoF/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+    }
+    if "sweep" in r:
+        line["jacobian_apply"] = r["sweep"]
+        line["fp64_mg_newton_step"] = r["fp64_mg"]
+        fp64 = r["sweep"].get("p%d_fp64" % a.degree)
+        if fp64:
+            line["jacobian_apply_fp64_roofline"] = {
+                "bound": "alu", "achieved": fp64["TFLOP_per_s"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fp64["TFLOP_per_s"] / FP64_PEAK_TFLOPS,
+                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"}
+    if not a.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(a)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -207,6 +207,9 @@ int pff_param_grad(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda
 int pff_profile(pff_ctx* ctx, int family);
 int pff_profile_result(pff_ctx* ctx, int* launches, double* total_ms);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all contexts). */
+long long pff_launch_count(void);
+
 /* Human-readable name of a status code. */
 const char* pff_strerror(int status);
 

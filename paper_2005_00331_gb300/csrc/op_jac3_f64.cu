@@ -21,7 +21,7 @@ static cudaError_t run_jac3(const double* x, double* y, const unsigned char* fla
   pw.tstride = (long long)qp_nv(3, SPLIT) * g.qpt;
   pw.mode = mode;
   OpArgs oa{inmask, outmask};
-  if (g.ntiles > 0) kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   pw.eps = eps;
   pw.kappa = kappa;
   OpArgs oa{IN_RAW, OUT_ZERO_DIRICHLET};
-  if (g.ntiles > 0) kern<<<(unsigned)g.ntiles, 256, smem, s>>>(U, r, flags, g, tb, pw, oa);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(U, r, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

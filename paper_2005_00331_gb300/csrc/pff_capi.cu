@@ -1034,6 +1034,8 @@ int pff_param_grad(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, 
   return PFF_OK;
 }
 
+long long pff_launch_count(void) { return launch_count(); }
+
 int pff_profile(pff_ctx* c, int family) {
   if (!c || family < PFF_PROF_OFF || family > PFF_PROF_RESIDUAL) return PFF_ERR_INVALID_ARG;
   if (family != PFF_PROF_OFF && c->ev.empty()) {

@@ -1,10 +1,17 @@
 // pff_kernels.cu -- per-point setup, diagonal, parameter gradient, coarse assembly, transfers,
 // vector, Chebyshev, CG-Lanczos and Newton-step kernels of libpff.
 #include <cstdint>
+#include <atomic>
+
 #include "pff_kernels.h"
+#include "pff_launch.h"
 #include "pff_op.cuh"
 
 namespace pff {
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -210,7 +217,7 @@ cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const do
   const unsigned gr = grid_for(tot, 128);
 #define PFF_CASE(DD, PP, SS)                                                                          \
   if (dim == DD && p == PP && split == SS) {                                                          \
-    k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, st64); \
+    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, st64); \
     return cudaGetLastError();                                                                        \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
@@ -296,7 +303,7 @@ cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const
   bool done = false;
 #define PFF_CASE(DD, PP, SS)                                                   \
   if (!done && dim == DD && p == PP && split == SS) {                         \
-    k_diagonal<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, d64);              \
+    count_launch(); k_diagonal<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, d64);              \
     done = true;                                                               \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
@@ -305,7 +312,7 @@ cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const
   PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
 #undef PFF_CASE
   if (!done) return cudaErrorInvalidValue;
-  k_diag_finish<<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d64, d32);
+  count_launch(); k_diag_finish<<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d64, d32);
   return cudaGetLastError();
 }
 
@@ -410,8 +417,8 @@ cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const 
   bool done = false;
 #define PFF_CASE(DD, PP, SS)                                                                  \
   if (!done && dim == DD && p == PP && split == SS) {                                        \
-    k_pgrad_qp<DD, PP, SS><<<gr, 128, 0, s>>>(U, v, st64, g, tb, mc, tmp);                   \
-    k_pgrad_int<DD, PP><<<gr, 128, 0, s>>>(tmp, g, tb, out_gc, out_lam, out_mu);             \
+    count_launch(); k_pgrad_qp<DD, PP, SS><<<gr, 128, 0, s>>>(U, v, st64, g, tb, mc, tmp);                   \
+    count_launch(); k_pgrad_int<DD, PP><<<gr, 128, 0, s>>>(tmp, g, tb, out_gc, out_lam, out_mu);             \
     done = true;                                                                              \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
@@ -510,7 +517,7 @@ cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64
   bool done = false;
 #define PFF_CASE(DD, PP, SS)                                             \
   if (!done && dim == DD && p == PP && split == SS) {                   \
-    k_coarse_asm<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, Au, Ap, B); \
+    count_launch(); k_coarse_asm<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, Au, Ap, B); \
     done = true;                                                         \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
@@ -519,7 +526,7 @@ cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64
   PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
 #undef PFF_CASE
   if (!done) return cudaErrorInvalidValue;
-  k_coarse_mask<<<grid_for(nu * nu), BLK, 0, s>>>(dim, nn, flags, Au, Ap, B);
+  count_launch(); k_coarse_mask<<<grid_for(nu * nu), BLK, 0, s>>>(dim, nn, flags, Au, Ap, B);
   return cudaGetLastError();
 }
 
@@ -544,8 +551,8 @@ __global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* 
 cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s) {
   dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
   for (int k = 0; k < n; ++k) {
-    k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, k, buf);
-    k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf);
+    count_launch(); k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, k, buf);
+    count_launch(); k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf);
   }
   return cudaGetLastError();
 }
@@ -563,7 +570,7 @@ __global__ void k_gemv(const double* __restrict__ A, int n, int m, const double*
 
 cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
                         cudaStream_t s) {
-  k_gemv<<<grid_for((long long)n * 32), BLK, 0, s>>>(A, n, m, x, y, alpha, beta);
+  count_launch(); k_gemv<<<grid_for((long long)n * 32), BLK, 0, s>>>(A, n, m, x, y, alpha, beta);
   return cudaGetLastError();
 }
 
@@ -674,7 +681,7 @@ cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsig
   const unsigned gr = grid_for(gf.nn);
 #define PFF_CASE(DD, PP)                                                                            \
   if (dim == DD && p == PP) {                                                                       \
-    k_prolong<DD, PP, Real><<<gr, BLK, 0, s>>>(xc, yf, flags_f, gc, gf, xt, accumulate ? 1 : 0); \
+    count_launch(); k_prolong<DD, PP, Real><<<gr, BLK, 0, s>>>(xc, yf, flags_f, gc, gf, xt, accumulate ? 1 : 0); \
     return cudaGetLastError();                                                                      \
   }
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
@@ -690,7 +697,7 @@ cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsi
   const unsigned gr = grid_for(gc.nn, 128);
 #define PFF_CASE(DD, PP)                                                                  \
   if (dim == DD && p == PP) {                                                             \
-    k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt);  \
+    count_launch(); k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt);  \
     return cudaGetLastError();                                                            \
   }
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
@@ -750,7 +757,7 @@ __global__ void k_state_interp(int dim, int p, const double* __restrict__ xf, do
 
 cudaError_t launch_state_interp(int dim, int p, const double* xf, double* yc, int nfields, const Geom& gf,
                                 const Geom& gc, const XferTab& xt, cudaStream_t s) {
-  k_state_interp<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, xf, yc, nfields, gf, gc, xt);
+  count_launch(); k_state_interp<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, xf, yc, nfields, gf, gc, xt);
   return cudaGetLastError();
 }
 
@@ -778,7 +785,7 @@ __global__ void k_coarse_active(int dim, int p, const unsigned char* __restrict_
 
 cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, unsigned char* flags_c,
                                  const Geom& gf, const Geom& gc, const XferTab& xt, cudaStream_t s) {
-  k_coarse_active<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, flags_f, flags_c, gf, gc, xt);
+  count_launch(); k_coarse_active<<<grid_for(gc.nn), BLK, 0, s>>>(dim, p, flags_f, flags_c, gf, gc, xt);
   return cudaGetLastError();
 }
 
@@ -801,7 +808,7 @@ cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  k_axpby<Real><<<(unsigned)g, BLK, 0, s>>>(n, a, x, b, y);
+  count_launch(); k_axpby<Real><<<(unsigned)g, BLK, 0, s>>>(n, a, x, b, y);
   return cudaGetLastError();
 }
 template cudaError_t launch_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
@@ -817,7 +824,7 @@ cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  k_cast<Ti, To><<<(unsigned)g, BLK, 0, s>>>(n, x, y);
+  count_launch(); k_cast<Ti, To><<<(unsigned)g, BLK, 0, s>>>(n, x, y);
   return cudaGetLastError();
 }
 template cudaError_t launch_cast<double, float>(long long, const double*, float*, cudaStream_t);
@@ -874,8 +881,8 @@ __global__ void k_dot2_final(int nb, const double* __restrict__ part, double* __
 template <typename Real>
 cudaError_t launch_dot2(long long n, long long nu, const Real* x, const Real* y, double* partial, double* res,
                         cudaStream_t s) {
-  k_dot2_part<Real><<<DOT_GRID, BLK, 0, s>>>(n, nu, x, y, partial);
-  k_dot2_final<<<1, BLK, 0, s>>>(DOT_GRID, partial, res);
+  count_launch(); k_dot2_part<Real><<<DOT_GRID, BLK, 0, s>>>(n, nu, x, y, partial);
+  count_launch(); k_dot2_final<<<1, BLK, 0, s>>>(DOT_GRID, partial, res);
   return cudaGetLastError();
 }
 template cudaError_t launch_dot2<double>(long long, long long, const double*, const double*, double*, double*,
@@ -913,8 +920,8 @@ cudaError_t launch_mdot(long long n, int k, const double* V, const double* w, do
                         cudaStream_t s) {
   const int nb = 152;
   dim3 grd(nb, (k + 3) / 4);
-  k_mdot_part<<<grd, BLK, 0, s>>>(n, k, V, w, partial);
-  k_mdot_final<<<k, BLK, 0, s>>>(nb, partial, h);
+  count_launch(); k_mdot_part<<<grd, BLK, 0, s>>>(n, k, V, w, partial);
+  count_launch(); k_mdot_final<<<k, BLK, 0, s>>>(nb, partial, h);
   return cudaGetLastError();
 }
 
@@ -930,13 +937,13 @@ __global__ void k_maxpy(long long n, int k, const double* __restrict__ V, const 
 cudaError_t launch_maxpy(long long n, int k, const double* V, const double* h, double* w, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 8) g = 152 * 8;
-  k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, V, h, w, -1.0);
+  count_launch(); k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, V, h, w, -1.0);
   return cudaGetLastError();
 }
 cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y, double* x, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 8) g = 152 * 8;
-  k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, Z, y, x, 1.0);
+  count_launch(); k_maxpy<<<(unsigned)g, BLK, 0, s>>>(n, k, Z, y, x, 1.0);
   return cudaGetLastError();
 }
 
@@ -949,7 +956,7 @@ __global__ void k_normalize(long long n, const double* __restrict__ x, const dou
 cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, nrm2, y);
+  count_launch(); k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, nrm2, y);
   return cudaGetLastError();
 }
 
@@ -1013,7 +1020,7 @@ cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, cons
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  k_cheb<Real><<<(unsigned)g, BLK, 0, s>>>(step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1, rho_k);
+  count_launch(); k_cheb<Real><<<(unsigned)g, BLK, 0, s>>>(step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1, rho_k);
   return cudaGetLastError();
 }
 template cudaError_t launch_cheb<double>(int, long long, long long, const double*, const double*, const double*,
@@ -1049,7 +1056,7 @@ cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, c
   (void)dim;
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_cg_init<<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
+  count_launch(); k_cg_init<<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
   return cudaGetLastError();
 }
 
@@ -1067,7 +1074,7 @@ cudaError_t launch_cg_update(long long n, long long nu, const double* Ap, const 
                              double* r, double* z, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_cg_update<<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
+  count_launch(); k_cg_update<<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
   return cudaGetLastError();
 }
 __global__ void k_cg_pupdate(long long n, long long nu, const double* __restrict__ z, const double* __restrict__ scal,
@@ -1080,7 +1087,7 @@ cudaError_t launch_cg_pupdate(long long n, long long nu, const double* z, const 
                               cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_cg_pupdate<<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
+  count_launch(); k_cg_pupdate<<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
   return cudaGetLastError();
 }
 
@@ -1110,7 +1117,7 @@ __global__ void k_cg_scalars(int phase, int it, int iters, double* scal, double*
 }
 cudaError_t launch_cg_scalars(int phase, int it, int iters, double* scal, double* alpha_hist, double* beta_hist,
                               cudaStream_t s) {
-  k_cg_scalars<<<1, 32, 0, s>>>(phase, it, iters, scal, alpha_hist, beta_hist);
+  count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(phase, it, iters, scal, alpha_hist, beta_hist);
   return cudaGetLastError();
 }
 
@@ -1175,7 +1182,7 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
                                cudaStream_t s) {
-  k_tridiag_eig<<<1, 32, 0, s>>>(iters, alpha_hist, beta_hist, lam);
+  count_launch(); k_tridiag_eig<<<1, 32, 0, s>>>(iters, alpha_hist, beta_hist, lam);
   return cudaGetLastError();
 }
 
@@ -1191,7 +1198,7 @@ cudaError_t launch_inv_diag(long long n, const double* d, double* di64, float* d
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  k_inv_diag<<<(unsigned)g, BLK, 0, s>>>(n, d, di64, di32);
+  count_launch(); k_inv_diag<<<(unsigned)g, BLK, 0, s>>>(n, d, di64, di32);
   return cudaGetLastError();
 }
 
@@ -1222,7 +1229,7 @@ cudaError_t launch_active_set(int dim, long long nn, const double* R, const doub
                               double c, double* U, unsigned char* flags, int* cnt, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  k_active_set<<<grid_for(nn), BLK, 0, s>>>(dim, nn, R, mass, phi_old, c, U, flags, cnt);
+  count_launch(); k_active_set<<<grid_for(nn), BLK, 0, s>>>(dim, nn, R, mass, phi_old, c, U, flags, cnt);
   return cudaGetLastError();
 }
 
@@ -1238,7 +1245,7 @@ cudaError_t launch_newton_rhs(int dim, long long nn, const double* R, const unsi
                               cudaStream_t s) {
   long long g = ((dim + 1) * nn + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_newton_rhs<<<(unsigned)g, BLK, 0, s>>>(dim, nn, R, flags, rhs);
+  count_launch(); k_newton_rhs<<<(unsigned)g, BLK, 0, s>>>(dim, nn, R, flags, rhs);
   return cudaGetLastError();
 }
 
@@ -1254,7 +1261,7 @@ cudaError_t launch_masked_copy(int dim, long long nn, double scale, const double
                                unsigned bits, double* out, cudaStream_t s) {
   long long g = ((dim + 1) * nn + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  k_masked_copy<<<(unsigned)g, BLK, 0, s>>>(dim, nn, scale, x, flags, bits, out);
+  count_launch(); k_masked_copy<<<(unsigned)g, BLK, 0, s>>>(dim, nn, scale, x, flags, bits, out);
   return cudaGetLastError();
 }
 
@@ -1266,7 +1273,7 @@ __global__ void k_set_active(int dim, long long nn, const unsigned char* __restr
 }
 cudaError_t launch_set_active(int dim, long long nn, const unsigned char* active, unsigned char* flags,
                               cudaStream_t s) {
-  k_set_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, active, flags);
+  count_launch(); k_set_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, active, flags);
   return cudaGetLastError();
 }
 __global__ void k_get_active(int dim, long long nn, const unsigned char* __restrict__ fl, unsigned char* __restrict__ a) {
@@ -1276,7 +1283,7 @@ __global__ void k_get_active(int dim, long long nn, const unsigned char* __restr
 }
 cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags, unsigned char* active,
                               cudaStream_t s) {
-  k_get_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, flags, active);
+  count_launch(); k_get_active<<<grid_for(nn), BLK, 0, s>>>(dim, nn, flags, active);
   return cudaGetLastError();
 }
 
@@ -1292,7 +1299,7 @@ __global__ void k_lumped_mass(int dim, long long nn, int n1, const double* __res
   m[i] = v;
 }
 cudaError_t launch_lumped_mass(int dim, long long nn, int n1, const double* w1, double* mass, cudaStream_t s) {
-  k_lumped_mass<<<grid_for(nn), BLK, 0, s>>>(dim, nn, n1, w1, mass);
+  count_launch(); k_lumped_mass<<<grid_for(nn), BLK, 0, s>>>(dim, nn, n1, w1, mass);
   return cudaGetLastError();
 }
 

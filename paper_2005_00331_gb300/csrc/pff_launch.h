@@ -5,6 +5,10 @@
 
 namespace pff {
 
+// Number of kernels launched by this library since it was loaded (all contexts).
+void count_launch();
+long long launch_count();
+
 // y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be
 // zeroed by the caller (seam nodes are accumulated atomically). mode: JM_*; masks: In/OutMask.
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,

@@ -75,6 +75,7 @@ _SIGS = {
     "pff_param_grad": (_I, [_P, _P, _P, _P, _P]),
     "pff_strerror": (ctypes.c_char_p, [_I]),
     "pff_profile": (_I, [_P, _I]),
+    "pff_launch_count": (_LL, []),
     "pff_profile_result": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
 }
 
@@ -116,6 +117,11 @@ def _ptr(t, dtype=torch.float64, numel=None):
     if numel is not None and t.numel() != numel:
         raise ValueError("expected %d entries, got %d" % (numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def launch_count():
+    """Kernels launched by libpff so far in this process."""
+    return int(load_library().pff_launch_count())
 
 
 def default_params(**kw):
