@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
+    ap.add_argument("--mode", choices=["newton", "apply"], default="newton",
+                    help="apply: time only the finest-level Jacobian apply (--precision) on the workload")
+    ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
     return ap.parse_args()
 
 
@@ -315,6 +318,49 @@ def apply_sweep(a, dev, flush, reps=20):
     return res
 
 
+def run_apply_only(a):
+    """K finest-level Jacobian applies (full mode, masked) after W warm-up applies, each timed with
+    CUDA events after an L2 flush."""
+    import torch
+
+    from paper_2005_00331_gb300 import launch_count, setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                     mg_precision=32)
+    U_h, po_h = make_state(ctx, a, seed=0)
+    U = torch.from_numpy(U_h).to(dev)
+    po = torch.from_numpy(po_h).to(dev)
+    nn = ctx.n_nodes
+    act = (po - U[a.dim * nn:] < 1e-8).to(torch.uint8).contiguous()
+    ctx.set_state(U, po, po, act)
+    dt = torch.float64 if a.precision == 64 else torch.float32
+    x = torch.randn(ctx.n_dofs, dtype=torch.float64, device=dev).to(dt)
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(a.warmup):
+        ctx.apply_jacobian(x, y)
+    torch.cuda.synchronize()
+    n0 = launch_count()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.apply_jacobian(x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    med = statistics.median(times)
+    nd = ctx.n_dofs
+    real = 8 if a.precision == 64 else 4
+    return {"mode": "apply", "dofs": nd, "precision": a.precision, "median_ms": med, "best_ms": min(times),
+            "dofs_per_s": nd / (med * 1e-3),
+            "GB_per_s": apply_bytes_per_dof(a.dim, a.degree, a.split, real) * nd / (med * 1e-3) / 1e9,
+            "TFLOP_per_s": apply_flops_per_dof(a.dim, a.degree, a.split) * nd / (med * 1e-3) / 1e12,
+            "launches": launch_count() - n0}
+
+
 # ---- CPU oracle baseline ----------------------------------------------------------------------
 CPU_SAMPLE_CELLS = 32
 
@@ -387,6 +433,10 @@ def main():
         return
 
     import torch
+    if a.mode == "apply":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_apply_only(a)))
+        return
     if world > 1:
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))

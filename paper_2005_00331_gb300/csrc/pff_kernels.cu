@@ -530,29 +530,35 @@ cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64
   return cudaGetLastError();
 }
 
-// In-place Gauss-Jordan inversion, one elimination step per pair of launches.
+// In-place Gauss-Jordan inversion. Step k reads pivot row and column k from buf[k & 1] and, while
+// updating, stores the updated row and column k + 1 into buf[(k + 1) & 1] for the next step.
 __global__ void k_gj_save(double* __restrict__ A, int n, int k, double* __restrict__ buf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   buf[i] = A[(long long)i * n + k];
   buf[n + i] = A[(long long)k * n + i];
 }
-__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ buf) {
+__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ cur,
+                            double* __restrict__ nxt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
-  const double piv = buf[n + k];
+  const double piv = cur[n + k];
   double* aij = A + (long long)i * n + j;
-  if (i == k) *aij = (j == k) ? 1.0 / piv : buf[n + j] / piv;
-  else if (j == k) *aij = -buf[i] / piv;
-  else *aij -= buf[i] * buf[n + j] / piv;
+  double v;
+  if (i == k) v = (j == k) ? 1.0 / piv : cur[n + j] / piv;
+  else if (j == k) v = -cur[i] / piv;
+  else v = *aij - cur[i] * cur[n + j] / piv;
+  *aij = v;
+  if (j == k + 1) nxt[i] = v;
+  if (i == k + 1) nxt[n + j] = v;
 }
 
 cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s) {
   dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  count_launch(); k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, 0, buf);
   for (int k = 0; k < n; ++k) {
-    count_launch(); k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, k, buf);
-    count_launch(); k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf);
+    count_launch(); k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf + (k & 1) * 2 * n, buf + ((k + 1) & 1) * 2 * n);
   }
   return cudaGetLastError();
 }
@@ -1133,25 +1139,37 @@ __device__ int sturm_count(int k, const double* a, const double* b2, double x) {
   }
   return cnt;
 }
+// One warp per block b: the extreme eigenvalues of the Lanczos tridiagonal of the first k valid CG
+// steps, by multisection (each lane evaluates a Sturm count; the bracket shrinks 33-fold a round).
 __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const double* __restrict__ bh,
                               double* __restrict__ lam) {
-  const int b = threadIdx.x;
+  const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (b >= 2) return;
-  double a[64], b2[64];
-  int k = 0;
-  while (k < iters && k < 64 && ah[b * iters + k] > 0.0) ++k;
-  if (k == 0) {
-    lam[b] = 1.0;
-    lam[2 + b] = 1.0;
-    return;
-  }
-  for (int j = 0; j < k; ++j) {
-    const double al = ah[b * iters + j];
-    a[j] = 1.0 / al + (j > 0 ? bh[b * iters + j - 1] / ah[b * iters + j - 1] : 0.0);
-    if (j + 1 < k) {
-      const double off = sqrt(bh[b * iters + j]) / al;
-      b2[j] = off * off;
+  __shared__ double sa[2][64], sb2[2][64];
+  __shared__ int sk[2];
+  if (lane == 0) {
+    int k = 0;
+    while (k < iters && k < 64 && ah[b * iters + k] > 0.0) ++k;
+    for (int j = 0; j < k; ++j) {
+      const double al = ah[b * iters + j];
+      sa[b][j] = 1.0 / al + (j > 0 ? bh[b * iters + j - 1] / ah[b * iters + j - 1] : 0.0);
+      if (j + 1 < k) {
+        const double off = sqrt(bh[b * iters + j]) / al;
+        sb2[b][j] = off * off;
+      }
     }
+    sk[b] = k;
+  }
+  __syncwarp();
+  const int k = sk[b];
+  const double* a = sa[b];
+  const double* b2 = sb2[b];
+  if (k == 0) {
+    if (lane == 0) {
+      lam[b] = 1.0;
+      lam[2 + b] = 1.0;
+    }
+    return;
   }
   double lo = 1e300, hi = -1e300;
   for (int j = 0; j < k; ++j) {
@@ -1161,24 +1179,21 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
     lo = fmin(lo, a[j] - r);
     hi = fmax(hi, a[j] + r);
   }
-  // largest eigenvalue: count(x) < k  <=>  x <= lambda_max
-  double l = lo, h = hi;
-  for (int it = 0; it < 200; ++it) {
-    const double m = 0.5 * (l + h);
-    if (m <= l || m >= h) break;
-    if (sturm_count(k, a, b2, m) >= k) h = m;
-    else l = m;
+  // which = 0: largest eigenvalue (first x with count(x) >= k); which = 1: smallest (count >= 1)
+  for (int which = 0; which < 2; ++which) {
+    const int target = which == 0 ? k : 1;
+    double l = lo, h = hi;
+    for (int round = 0; round < 16 && h - l > 1e-15 * fmax(fabs(l), fabs(h)); ++round) {
+      const double x = l + (h - l) * (lane + 1) / 33.0;
+      const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(k, a, b2, x) >= target);
+      const int j = ge ? __ffs(ge) - 1 : 32;  // first lane whose point is at or above the eigenvalue
+      const double nl = j == 0 ? l : l + (h - l) * j / 33.0;
+      const double nh = j == 32 ? h : l + (h - l) * (j + 1) / 33.0;
+      l = nl;
+      h = nh;
+    }
+    if (lane == 0) lam[(which == 0 ? 0 : 2) + b] = which == 0 ? h : l;
   }
-  lam[b] = h;
-  l = lo;
-  h = hi;
-  for (int it = 0; it < 200; ++it) {
-    const double m = 0.5 * (l + h);
-    if (m <= l || m >= h) break;
-    if (sturm_count(k, a, b2, m) >= 1) h = m;
-    else l = m;
-  }
-  lam[2 + b] = l;
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
                                cudaStream_t s) {

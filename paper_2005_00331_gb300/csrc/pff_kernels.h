@@ -24,7 +24,7 @@ cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const 
 cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64, const unsigned char* flags,
                                    const Geom& g, const Tab<double>& tb, double* Au, double* Ap, double* B,
                                    cudaStream_t s);
-// In-place Gauss-Jordan inverse of an n x n matrix (no pivoting; SPD input); buf: 2n doubles.
+// In-place Gauss-Jordan inverse of an n x n matrix (no pivoting; SPD input); buf: 4n doubles.
 cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s);
 // y = A x (dense, row major, n rows, m cols); y = beta * y + alpha * A x.
 cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
