@@ -1197,7 +1197,7 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
                                cudaStream_t s) {
-  count_launch(); k_tridiag_eig<<<1, 32, 0, s>>>(iters, alpha_hist, beta_hist, lam);
+  count_launch(); k_tridiag_eig<<<1, 64, 0, s>>>(iters, alpha_hist, beta_hist, lam);
   return cudaGetLastError();
 }
 
