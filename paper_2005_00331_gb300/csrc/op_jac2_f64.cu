@@ -21,7 +21,8 @@ static cudaError_t run_jac2(const double* x, double* y, const unsigned char* fla
   pw.tstride = (long long)qp_nv(2, SPLIT) * g.qpt;
   pw.mode = mode;
   OpArgs oa{inmask, outmask};
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa); }
+  const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

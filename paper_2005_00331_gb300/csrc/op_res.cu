@@ -31,7 +31,9 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   pw.eps = eps;
   pw.kappa = kappa;
   OpArgs oa{IN_RAW, OUT_ZERO_DIRICHLET};
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(U, r, flags, g, tb, pw, oa); }
+  dim3 blk(256);
+  if constexpr (DIM == 2) blk = dim3(Tile2<P>::QPX, Tile2<P>::TY);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(U, r, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

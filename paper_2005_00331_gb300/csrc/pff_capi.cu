@@ -134,10 +134,19 @@ struct pff_ctx {
   std::vector<void*> allocs;
   // V-cycle replayed as a CUDA graph (captured once on a private stream; buffers never move)
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t vgraph[2] = {nullptr, nullptr};  // [0] FP64 multigrid, [1] FP32
+  // graphs: [0] FP64 / [1] FP32 V-cycle; setup without / with nodal fields; each in a plain variant
+  // and one variant per timed kernel family (event-record nodes around the timed launches)
+  cudaGraphExec_t vgraph[2][6] = {};
   bool vwarm[2] = {false, false};
-  cudaGraphExec_t sgraph[2] = {nullptr, nullptr};  // multigrid setup, without / with nodal fields
+  cudaGraphExec_t sgraph[2][6] = {};
   bool swarm[2] = {false, false};
+  // event slots recorded by each profiled graph, and the replays whose events await collection
+  std::vector<cudaEvent_t> gev;
+  std::vector<std::pair<int, int>> vrange[2][6], srange[2][6];
+  std::vector<std::pair<int, int>> pending;
+  double prof_ms = 0.0;
+  long long prof_n = 0;
+  bool capturing = false;
   bool use_graph = true;
   // kernel-family timing (pff_profile)
   int prof = 0;
@@ -305,9 +314,33 @@ int ensure_work(pff_ctx* c, int l) {
 
 constexpr int PROF_MAX_LAUNCHES = 16384;
 
-bool prof_on(pff_ctx* c, int family) { return c->prof == family && c->nev + 2 <= (int)c->ev.size(); }
+bool prof_on(pff_ctx* c, int family) {
+  return c->prof == family && (c->capturing || c->nev + 2 <= (int)c->ev.size());
+}
+// Records one timing event: from the per-call pool when running eagerly, from a fresh persistent
+// event when the call is being captured into a graph (the event becomes an event-record node).
 int prof_mark(pff_ctx* c) {
+  if (c->capturing) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->gev.push_back(e);
+    CK(cudaEventRecord(e, c->s));
+    return PFF_OK;
+  }
   CK(cudaEventRecord(c->ev[c->nev++], c->s));
+  return PFF_OK;
+}
+// After the stream has synchronised: adds the timings of graph replays launched since the last call.
+int prof_collect(pff_ctx* c) {
+  for (auto& r : c->pending) {
+    for (int i = r.first; i + 1 < r.second; i += 2) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->gev[i], c->gev[i + 1]));
+      c->prof_ms += ms;
+      ++c->prof_n;
+    }
+  }
+  c->pending.clear();
   return PFF_OK;
 }
 
@@ -416,11 +449,15 @@ int mg_build(pff_ctx* c) {
 
 // Captures fn into a CUDA graph on the private stream and instantiates it into *exec.
 template <class F>
-int capture_graph(pff_ctx* c, cudaGraphExec_t* exec, F fn) {
+int capture_graph(pff_ctx* c, cudaGraphExec_t* exec, std::pair<int, int>* range, F fn) {
   cudaStream_t user = c->s;
   c->s = c->cap;
+  const int ev0 = (int)c->gev.size();
   cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
+  c->capturing = true;
   int st = e == cudaSuccess ? fn() : PFF_ERR_CUDA;
+  c->capturing = false;
+  *range = {ev0, (int)c->gev.size()};
   cudaGraph_t gr = nullptr;
   if (e == cudaSuccess) {
     const cudaError_t e2 = cudaStreamEndCapture(c->s, &gr);
@@ -443,18 +480,23 @@ int mg_setup(pff_ctx* c) {
   if (!c->has_state) return PFF_ERR_NO_STATE;
   if (c->mg_ready) return PFF_OK;
   CR(ensure_qp(c));
-  const int key = c->has_fields ? 1 : 0;
-  if (!c->use_graph || c->prof != PFF_PROF_OFF || !c->swarm[key]) {
+  const int key = c->has_fields ? 1 : 0, pv = c->prof;
+  if (!c->use_graph || !c->swarm[key]) {
     CR(mg_build(c));
     c->swarm[key] = true;
   } else {
-    if (!c->sgraph[key] && capture_graph(c, &c->sgraph[key], [&] { return mg_build(c); }) != PFF_OK) {
+    std::pair<int, int> rg;
+    if (!c->sgraph[key][pv] && capture_graph(c, &c->sgraph[key][pv], &rg, [&] { return mg_build(c); }) != PFF_OK) {
       c->use_graph = false;
       CR(mg_build(c));
       c->mg_ready = true;
       return PFF_OK;
     }
-    CK(cudaGraphLaunch(c->sgraph[key], c->s));
+    if (!c->sgraph[key][pv]) return PFF_ERR_CUDA;
+    if (c->srange[key][pv].empty() && pv != PFF_PROF_OFF) c->srange[key][pv].push_back(rg);
+    CK(cudaGraphLaunch(c->sgraph[key][pv], c->s));
+    if (pv != PFF_PROF_OFF)
+      for (auto& r : c->srange[key][pv]) c->pending.push_back(r);
   }
   c->mg_ready = true;
   return PFF_OK;
@@ -537,18 +579,22 @@ int vcycle_level(pff_ctx* c, int l, const Real* r, Real* e) {
 template <typename Real>
 int vcycle_exec(pff_ctx* c) {
   Real** w = work_of<Real>(c->lv[0]);
-  const int gi = sizeof(Real) == 8 ? 0 : 1;
-  if (!c->use_graph || c->prof != PFF_PROF_OFF || !c->vwarm[gi]) {
+  const int gi = sizeof(Real) == 8 ? 0 : 1, pv = c->prof;
+  if (!c->use_graph || !c->vwarm[gi]) {
     CR(vcycle_level<Real>(c, 0, w[0], w[1]));
     c->vwarm[gi] = true;
     return PFF_OK;
   }
-  if (!c->vgraph[gi] &&
-      capture_graph(c, &c->vgraph[gi], [&] { return vcycle_level<Real>(c, 0, w[0], w[1]); }) != PFF_OK) {
+  std::pair<int, int> rg;
+  if (!c->vgraph[gi][pv] &&
+      capture_graph(c, &c->vgraph[gi][pv], &rg, [&] { return vcycle_level<Real>(c, 0, w[0], w[1]); }) != PFF_OK) {
     c->use_graph = false;
     return vcycle_level<Real>(c, 0, w[0], w[1]);
   }
-  CK(cudaGraphLaunch(c->vgraph[gi], c->s));
+  if (c->vrange[gi][pv].empty() && pv != PFF_PROF_OFF) c->vrange[gi][pv].push_back(rg);
+  CK(cudaGraphLaunch(c->vgraph[gi][pv], c->s));
+  if (pv != PFF_PROF_OFF)
+    for (auto& r : c->vrange[gi][pv]) c->pending.push_back(r);
   return PFF_OK;
 }
 
@@ -575,6 +621,7 @@ int norm2_host(pff_ctx* c, const double* x, long long n, double* out) {
   CK(launch_dot2<double>(n, n, x, x, c->partial, c->dres, c->s));
   CK(cudaMemcpyAsync(c->pinned, c->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
+  CR(prof_collect(c));
   *out = c->pinned[0] + c->pinned[1];
   return PFF_OK;
 }
@@ -633,6 +680,7 @@ int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_o
       CK(launch_dot2<double>(n, n, wv, wv, c->partial, c->hdev + 2 * (m + 1), c->s));
       CK(cudaMemcpyAsync(c->pinned, c->hdev, sizeof(double) * (2 * (m + 1) + 2), cudaMemcpyDeviceToHost, c->s));
       CK(cudaStreamSynchronize(c->s));
+      CR(prof_collect(c));
       const double* hh = c->pinned;
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
       const double nw2 = hh[2 * (m + 1)] + hh[2 * (m + 1) + 1];
@@ -749,10 +797,13 @@ void pff_destroy(pff_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->s);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
-  for (cudaGraphExec_t g : c->vgraph)
-    if (g) cudaGraphExecDestroy(g);
-  for (cudaGraphExec_t g : c->sgraph)
-    if (g) cudaGraphExecDestroy(g);
+  for (auto& row : c->vgraph)
+    for (cudaGraphExec_t g : row)
+      if (g) cudaGraphExecDestroy(g);
+  for (auto& row : c->sgraph)
+    for (cudaGraphExec_t g : row)
+      if (g) cudaGraphExecDestroy(g);
+  for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (void* q : c->allocs) cudaFree(q);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -1080,6 +1131,7 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   const auto t1 = clk::now();
   CR(mg_setup(c));
   CK(cudaStreamSynchronize(c->s));
+  CR(prof_collect(c));
   const auto t2 = clk::now();
   r.status = fgmres(c, c->rhs, c->dU, &r.gmres_iters, &r.gmres_rel);
   if (r.status == PFF_OK || r.status == PFF_ERR_NOT_CONVERGED) {
@@ -1123,21 +1175,26 @@ int pff_profile(pff_ctx* c, int family) {
     c->ev.resize(2 * PROF_MAX_LAUNCHES);
     for (auto& e : c->ev) CK(cudaEventCreate(&e));
   }
+  CK(cudaStreamSynchronize(c->s));
+  c->pending.clear();
   c->prof = family;
   c->nev = 0;
+  c->prof_ms = 0.0;
+  c->prof_n = 0;
   return PFF_OK;
 }
 
 int pff_profile_result(pff_ctx* c, int* launches, double* total_ms) {
   if (!c) return PFF_ERR_INVALID_ARG;
   CK(cudaStreamSynchronize(c->s));
-  double tot = 0.0;
+  CR(prof_collect(c));
+  double tot = c->prof_ms;
   for (int i = 0; i + 1 < c->nev; i += 2) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
     tot += ms;
   }
-  if (launches) *launches = c->nev / 2;
+  if (launches) *launches = (int)(c->nev / 2 + c->prof_n);
   if (total_ms) *total_ms = tot;
   return PFF_OK;
 }

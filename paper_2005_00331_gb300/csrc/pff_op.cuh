@@ -203,141 +203,199 @@ __device__ __forceinline__ void cells_of_node(int r, int T, int& lo, int& hi) {
 }
 
 // ===========================================================================================
-// 2D operator kernel.
+// 2D operator kernel. Thread (tx, ty) of a (TX (p+1)) x TY block owns Gauss column tx of cell row
+// ty: it contracts the node rows of its cell in x, then in y, applies the pointwise functor at its
+// p+1 points and contracts back in y, all in registers; a second pass sums the transposed x
+// contractions of the cells sharing each node of the patch.
+template <int P>
+struct Tile2 {
+  static constexpr int TX = 8, TY = (P == 1 ? 16 : 8);
+  static constexpr int n = P + 1, NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n, QPY = TY * n;
+  static constexpr int NT = QPX * TY;
+};
+
 template <int P, typename Real, class PW>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(Tile2<P>::NT)
 k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char* __restrict__ flags,
        Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
-  constexpr int TX = TileCfg<2, P>::TX, TY = TileCfg<2, P>::TY;
-  constexpr int n = P + 1, NF = 3;
-  constexpr int NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n;
+  using T = Tile2<P>;
+  constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
+  constexpr int NPX = T::NPX, NPY = T::NPY, QPX = T::QPX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* X = reinterpret_cast<Real*>(smem_raw);  // [NF][NPY][NPX], later the output patch
-  Real* XB = X + NF * NPY * NPX;                 // [NF][NPY][QPX]
-  Real* XD = XB + NF * NPY * QPX;
-  Real* UB = XD + NF * NPY * QPX;                // [NF][TY][n][QPX]
+  Real* X = reinterpret_cast<Real*>(smem_raw);  // [NF][NPY][NPX], then the output patch
+  Real* UB = X + NF * NPY * NPX;                 // [NF][TY][n][QPX]
   Real* UD = UB + NF * TY * n * QPX;
+  Real* sS = UD + NF * TY * n * QPX;             // [n][n]
+  Real* sD = sS + n * n;
 
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * QPX + tx;
   const long long tile = blockIdx.x;
-  const int tx = int(tile % g.ntile[0]), ty = int(tile / g.ntile[0]);
-  const int x0 = tx * TX * P, y0 = ty * TY * P;
-  const int cx0 = tx * TX, cy0 = ty * TY;
-
-  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
-    const int gx = x0 + s, gy = y0 + r;
-    Real v = 0;
-    if (gx < g.n1 && gy < g.n1) {
-      const long long node = gx + (long long)g.n1 * gy;
-      v = load_node(src, flags, node, f * g.nn + node, f, 2, oa.inmask);
-    }
-    X[i] = v;
+  const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
+  const int x0 = tix * TX * P, y0 = tiy * TY * P;
+  if (tid < n * n) {
+    sS[tid] = tb.S[tid / n][tid % n];
+    sD[tid] = tb.D[tid / n][tid % n];
   }
-  __syncthreads();
-  // x-pass: values (XB) and x-derivatives (XD) at the Gauss columns of every node row
-  for (int i = threadIdx.x; i < NF * NPY * QPX; i += blockDim.x) {
-    const int c = i % QPX, rf = i / QPX;
-    const int cx = c / n, qi = c % n;
-    const Real* xr = X + rf * NPX + cx * P;
-    Real b = 0, d = 0;
+  // node patch of every field (masked on input)
+  for (int r = ty; r < NPY; r += TY) {
+    const int gy = y0 + r;
+    for (int s = tx; s < NPX; s += QPX) {
+      const int gx = x0 + s;
+      Real v[NF] = {Real(0), Real(0), Real(0)};
+      if (gx < g.n1 && gy < g.n1) {
+        const long long node = gx + (long long)g.n1 * gy;
+        unsigned char m = 0;
+        if (oa.inmask != IN_RAW) {
+          m = flags[node];
+          if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
+        }
 #pragma unroll
-    for (int k = 0; k < n; ++k) {
-      b += tb.S[qi][k] * xr[k];
-      d += tb.D[qi][k] * xr[k];
+        for (int f = 0; f < NF; ++f) v[f] = ((m >> f) & 1u) ? Real(0) : src[f * g.nn + node];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) X[(f * NPY + r) * NPX + s] = v[f];
     }
-    XB[i] = b;
-    XD[i] = d;
   }
+  const int cx = tx / n, qi = tx % n;
+  const bool inside = (tix * TX + cx < g.N) && (tiy * TY + ty < g.N);
+  Real Sq[n], Dq[n];
   __syncthreads();
-  // y-pass, pointwise, transposed y-pass: one thread per (cell row, Gauss column)
-  for (int i = threadIdx.x; i < TY * QPX; i += blockDim.x) {
-    const int c = i % QPX, cy = i / QPX;
 #pragma unroll
-    for (int f = 0; f < NF; ++f)
+  for (int k = 0; k < n; ++k) {
+    Sq[k] = sS[qi * n + k];
+    Dq[k] = sD[qi * n + k];
+  }
+  // x-contraction of the n node rows of this cell at Gauss column qi
+  Real xb[NF][n], xd[NF][n];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      const Real* row = X + (f * NPY + ty * P + l) * NPX + cx * P;
+      Real b = 0, d = 0;
+#pragma unroll
+      for (int k = 0; k < n; ++k) {
+        b += Sq[k] * row[k];
+        d += Dq[k] * row[k];
+      }
+      xb[f][l] = b;
+      xd[f][l] = d;
+    }
+  Real ub[NF][n], ud[NF][n];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      ub[f][l] = 0;
+      ud[f][l] = 0;
+    }
+  if (inside) {
+#pragma unroll
+    for (int qj = 0; qj < n; ++qj) {
+      Real sj[n], dj[n];
 #pragma unroll
       for (int l = 0; l < n; ++l) {
-        UB[((f * TY + cy) * n + l) * QPX + c] = 0;
-        UD[((f * TY + cy) * n + l) * QPX + c] = 0;
+        sj[l] = sS[qj * n + l];
+        dj[l] = sD[qj * n + l];
       }
-    const bool inside = (cx0 + c / n < g.N) && (cy0 + cy < g.N);
-    if (!inside) continue;
-    for (int qj = 0; qj < n; ++qj) {
       QPIn<2, Real> in;
-      Real vb[NF], vdx[NF], vdy[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        Real b = 0, dx = 0, dy = 0;
-#pragma unroll
-        for (int l = 0; l < n; ++l) {
-          const int idx = (f * NPY + cy * P + l) * QPX + c;
-          b += tb.S[qj][l] * XB[idx];
-          dx += tb.S[qj][l] * XD[idx];
-          dy += tb.D[qj][l] * XB[idx];
-        }
-        vb[f] = b;
-        vdx[f] = dx;
-        vdy[f] = dy;
-      }
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        in.gu[k][0] = vdx[k];
-        in.gu[k][1] = vdy[k];
+        Real gx = 0, gy = 0;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          gx += sj[l] * xd[k][l];
+          gy += dj[l] * xb[k][l];
+        }
+        in.gu[k][0] = gx;
+        in.gu[k][1] = gy;
       }
-      in.ph = vb[2];
-      in.gph[0] = vdx[2];
-      in.gph[1] = vdy[2];
+      {
+        Real v = 0, gx = 0, gy = 0;
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          v += sj[l] * xb[2][l];
+          gx += sj[l] * xd[2][l];
+          gy += dj[l] * xb[2][l];
+        }
+        in.ph = v;
+        in.gph[0] = gx;
+        in.gph[1] = gy;
+      }
       QPOut<2, Real> o;
-      pw(tile, (long long)(cy * n + qj) * QPX + c, in, o);
+      pw(tile, (long long)(ty * n + qj) * QPX + tx, in, o);
 #pragma unroll
       for (int l = 0; l < n; ++l) {
-        const Real s = tb.S[qj][l], d = tb.D[qj][l];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          UB[((k * TY + cy) * n + l) * QPX + c] += d * o.cu[k][1];
-          UD[((k * TY + cy) * n + l) * QPX + c] += s * o.cu[k][0];
+          ub[k][l] += dj[l] * o.cu[k][1];
+          ud[k][l] += sj[l] * o.cu[k][0];
         }
-        UB[((2 * TY + cy) * n + l) * QPX + c] += s * o.cv + d * o.cg[1];
-        UD[((2 * TY + cy) * n + l) * QPX + c] += s * o.cg[0];
+        ub[2][l] += sj[l] * o.cv + dj[l] * o.cg[1];
+        ud[2][l] += sj[l] * o.cg[0];
       }
     }
   }
-  __syncthreads();
-  // transposed x-pass into the node patch (sums over the cells sharing a node)
-  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
-    int ylo, yhi, xlo, xhi;
-    cells_of_node<P>(r, TY, ylo, yhi);
-    cells_of_node<P>(s, TX, xlo, xhi);
-    Real acc = 0;
-    for (int cy = ylo; cy <= yhi; ++cy) {
-      const int l = r - cy * P;
-      for (int cx = xlo; cx <= xhi; ++cx) {
-        const int k = s - cx * P;
-        const Real* ub = UB + ((f * TY + cy) * n + l) * QPX + cx * n;
-        const Real* ud = UD + ((f * TY + cy) * n + l) * QPX + cx * n;
 #pragma unroll
-        for (int qi = 0; qi < n; ++qi) acc += tb.S[qi][k] * ub[qi] + tb.D[qi][k] * ud[qi];
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int l = 0; l < n; ++l) {
+      UB[((f * TY + ty) * n + l) * QPX + tx] = ub[f][l];
+      UD[((f * TY + ty) * n + l) * QPX + tx] = ud[f][l];
+    }
+  __syncthreads();
+  // transposed x-contraction: each node of the patch sums the cells that share it, then stores
+  for (int r = ty; r < NPY; r += TY) {
+    const int gy = y0 + r;
+    const int ylo = r == 0 ? 0 : (r - 1) / P, yhi = r / P < TY - 1 ? r / P : TY - 1;
+    for (int s = tx; s < NPX; s += QPX) {
+      const int gx = x0 + s;
+      if (gx >= g.n1 || gy >= g.n1) continue;
+      const int xlo = s == 0 ? 0 : (s - 1) / P, xhi = s / P < TX - 1 ? s / P : TX - 1;
+      Real acc[NF] = {Real(0), Real(0), Real(0)};
+      for (int cy = ylo; cy <= yhi; ++cy) {
+        const int l = r - cy * P;
+        for (int cxx = xlo; cxx <= xhi; ++cxx) {
+          const int k = s - cxx * P;
+#pragma unroll
+          for (int q = 0; q < n; ++q) {
+            const Real sk = sS[q * n + k], dk = sD[q * n + k];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const int o = ((f * TY + cy) * n + l) * QPX + cxx * n + q;
+              acc[f] += sk * UB[o] + dk * UD[o];
+            }
+          }
+        }
+      }
+      const long long node = gx + (long long)g.n1 * gy;
+      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0);
+      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1);
+      unsigned char m = 0;
+      if (oa.outmask != OUT_RAW) {
+        m = flags[node];
+        if (oa.outmask == OUT_ZERO_DIRICHLET) m &= dirichlet_bits(2);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const long long gi = f * g.nn + node;
+        if ((m >> f) & 1u) {
+          if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Real(0);
+        } else if (low || high) {
+          atomicAdd(dst + gi, acc[f]);
+        } else {
+          dst[gi] = acc[f];
+        }
       }
     }
-    X[i] = acc;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NF * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
-    const int gx = x0 + s, gy = y0 + r;
-    if (gx >= g.n1 || gy >= g.n1) continue;
-    const long long node = gx + (long long)g.n1 * gy;
-    const bool low = (s == 0 && tx > 0) || (r == 0 && ty > 0);
-    const bool high = (s == NPX - 1 && tx < g.ntile[0] - 1) || (r == NPY - 1 && ty < g.ntile[1] - 1);
-    store_node(dst, src, flags, node, f * g.nn + node, f, 2, X[i], low, high, oa.outmask);
   }
 }
 
 template <int P, typename Real>
 constexpr size_t op2d_smem() {
-  constexpr int TX = TileCfg<2, P>::TX, TY = TileCfg<2, P>::TY;
-  constexpr int n = P + 1, NF = 3, NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n;
-  return sizeof(Real) * (size_t)(NF * NPY * NPX + 2 * NF * NPY * QPX + 2 * NF * TY * n * QPX);
+  using T = Tile2<P>;
+  return sizeof(Real) * (size_t)(3 * T::NPY * T::NPX + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
 }
 
 // ===========================================================================================
