@@ -141,7 +141,8 @@ struct pff_ctx {
   cudaGraphExec_t sgraph[2][6] = {};
   bool swarm[2] = {false, false};
   // event slots recorded by each profiled graph, and the replays whose events await collection
-  std::vector<cudaEvent_t> gev;
+  std::vector<cudaEvent_t> gev;  // created by pff_profile; graphs take slots in capture order
+  int gnext = 0;
   std::vector<std::pair<int, int>> vrange[2][6], srange[2][6];
   std::vector<std::pair<int, int>> pending;
   double prof_ms = 0.0;
@@ -175,6 +176,7 @@ int dalloc(pff_ctx* c, T** p, long long n) {
     cudaError_t e_ = (__VA_ARGS__);             \
     if (e_ != cudaSuccess) {                    \
       g_last_cuda = cudaGetErrorString(e_);     \
+      cudaGetLastError();                       \
       return PFF_ERR_CUDA;                      \
     }                                           \
   } while (0)
@@ -321,10 +323,8 @@ bool prof_on(pff_ctx* c, int family) {
 // event when the call is being captured into a graph (the event becomes an event-record node).
 int prof_mark(pff_ctx* c) {
   if (c->capturing) {
-    cudaEvent_t e;
-    CK(cudaEventCreate(&e));
-    c->gev.push_back(e);
-    CK(cudaEventRecord(e, c->s));
+    if (c->gnext >= (int)c->gev.size()) return PFF_OK;  // pool exhausted: this launch is not timed
+    CK(cudaEventRecordWithFlags(c->gev[c->gnext++], c->s, cudaEventRecordExternal));
     return PFF_OK;
   }
   CK(cudaEventRecord(c->ev[c->nev++], c->s));
@@ -452,12 +452,12 @@ template <class F>
 int capture_graph(pff_ctx* c, cudaGraphExec_t* exec, std::pair<int, int>* range, F fn) {
   cudaStream_t user = c->s;
   c->s = c->cap;
-  const int ev0 = (int)c->gev.size();
+  const int ev0 = c->gnext;
   cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
   c->capturing = true;
   int st = e == cudaSuccess ? fn() : PFF_ERR_CUDA;
   c->capturing = false;
-  *range = {ev0, (int)c->gev.size()};
+  *range = {ev0, c->gnext - ((c->gnext - ev0) & 1)};
   cudaGraph_t gr = nullptr;
   if (e == cudaSuccess) {
     const cudaError_t e2 = cudaStreamEndCapture(c->s, &gr);
@@ -1174,6 +1174,8 @@ int pff_profile(pff_ctx* c, int family) {
   if (family != PFF_PROF_OFF && c->ev.empty()) {
     c->ev.resize(2 * PROF_MAX_LAUNCHES);
     for (auto& e : c->ev) CK(cudaEventCreate(&e));
+    c->gev.resize(2 * PROF_MAX_LAUNCHES);
+    for (auto& e : c->gev) CK(cudaEventCreate(&e));
   }
   CK(cudaStreamSynchronize(c->s));
   c->pending.clear();
