@@ -39,6 +39,7 @@ extern "C" {
 #define PFF_ERR_NOT_CONVERGED (-5) /* FGMRES reached its iteration cap */
 #define PFF_ERR_BREAKDOWN (-6)     /* Krylov breakdown (zero norm before convergence) */
 #define PFF_ERR_NO_STATE (-7)      /* pff_set_state has not been called */
+#define PFF_ERR_TOO_LARGE (-8)     /* problem exceeds the fixed scratch of pff_param_grad_noalloc */
 
 /* Splits of the elastic energy (Sec. 2.1): none = isotropic model, miehe = spectral split. */
 #define PFF_SPLIT_NONE 0
@@ -190,6 +191,23 @@ int pff_solve_newton_step(pff_ctx* ctx, double* U_out, pff_report* rep);
  * on Dirichlet DoFs are ignored (those rows of the residual are zero). Any output may be NULL;
  * outputs are overwritten. */
 int pff_param_grad(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda, double* g_mu);
+
+/* Allocation-free variant of pff_param_grad (the paper has no counterpart: this exists for callers
+ * of this library that must not allocate device memory, e.g. code running while a CUDA graph is
+ * being captured, where cudaMalloc is illegal, or a host that owns all device memory through its
+ * own pool). pff_param_grad allocates its per-point scratch (3 x cells x points-per-cell doubles)
+ * on first use; this entry point uses a fixed array in device global memory instead, of
+ * PFF_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), which every GPU that loads the library holds until
+ * the process exits. Problems that need more (3 * N^dim * (p+1)^dim doubles) are rejected with
+ * PFF_ERR_TOO_LARGE before any work is queued. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. No call allocates (no cudaMalloc, cudaFree or allocating library routine).
+ * All calls share the array: calls whose work overlaps on the GPU (other streams, other contexts)
+ * race on it, so serialise them. Every scratch entry read is written earlier in the same call, so
+ * the contents left by a previous call do not matter. Same arguments, results and requirements as
+ * pff_param_grad otherwise (the state must have been set; outputs are overwritten). */
+#define PFF_NOALLOC_SCRATCH_DOUBLES (2LL * 1024 * 1024)
+int pff_param_grad_noalloc(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda, double* g_mu);
 
 /* Device timing of one kernel family with CUDA events recorded on the context's stream around
  * each launch of that family (for throughput and roofline figures; off by default):

@@ -5,6 +5,7 @@
 // rotations). Every vector operation of the hot path runs in the kernels of this library.
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -789,6 +790,7 @@ const char* pff_strerror(int st) {
     case PFF_ERR_NOT_CONVERGED: return "linear solver did not converge";
     case PFF_ERR_BREAKDOWN: return "Krylov breakdown";
     case PFF_ERR_NO_STATE: return "no state set";
+    case PFF_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }
@@ -1202,3 +1204,46 @@ int pff_profile_result(pff_ctx* c, int* launches, double* total_ms) {
 }
 
 }  // extern "C"
+
+// ---- allocation-free parameter gradient ---------------------------------------------------------
+// Per-point scratch of pff_param_grad_noalloc: a file-scope array in device global memory. In host
+// code g_noalloc_scratch only names the symbol; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[PFF_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device (looked up once per device).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PFF_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return PFF_OK;
+}
+}  // namespace
+
+extern "C" int pff_param_grad_noalloc(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
+  if (!c || !v) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  LevelData& L = c->lv[0];
+  const long long ncell = c->dim == 2 ? (long long)L.N * L.N : (long long)L.N * L.N * L.N;
+  const int nq = c->dim == 2 ? (c->p + 1) * (c->p + 1) : (c->p + 1) * (c->p + 1) * (c->p + 1);
+  if (3 * ncell * nq > PFF_NOALLOC_SCRATCH_DOUBLES) return PFF_ERR_TOO_LARGE;
+  double* tmp = nullptr;
+  CR(noalloc_scratch(&tmp));
+  CR(ensure_qp(c));
+  MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+  double* vm = c->scratch;  // allocated with the context
+  CK(launch_masked_copy(c->dim, L.nn, 1.0, v, L.flags, (1u << c->dim) - 1u, vm, c->s));
+  CK(launch_param_grad(c->dim, c->p, c->prm.split, L.U, vm, L.st64, L.g, L.t64, mc, tmp, g_gc, g_lambda, g_mu, c->s));
+  return PFF_OK;
+}

@@ -16,8 +16,7 @@ PFF_MASK_RAW, PFF_MASK_ADJOINT = 4, 8
 PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT = 0x10, 0x20, 0x40
 PFF_PROF_OFF, PFF_PROF_JAC64_L0, PFF_PROF_JAC32_L0, PFF_PROF_JAC64, PFF_PROF_JAC32, PFF_PROF_RESIDUAL = range(6)
 
-_ERRORS = {-1: "invalid argument", -2: "out of device memory", -3: "CUDA error", -4: "non-finite value",
-           -5: "linear solver did not converge", -6: "Krylov breakdown", -7: "no state set"}
+PFF_ERR_TOO_LARGE = -8
 
 
 class PFFError(RuntimeError):
@@ -73,6 +72,7 @@ _SIGS = {
     "pff_solve_linear": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pff_solve_newton_step": (_I, [_P, _P, ctypes.POINTER(Report)]),
     "pff_param_grad": (_I, [_P, _P, _P, _P, _P]),
+    "pff_param_grad_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "pff_strerror": (ctypes.c_char_p, [_I]),
     "pff_profile": (_I, [_P, _I]),
     "pff_launch_count": (_LL, []),
@@ -273,6 +273,14 @@ class Context:
         if check:
             _check(st, "pff_solve_newton_step")
         return rep.as_dict()
+
+    def param_grad_noalloc(self, g_gc, g_lambda, g_mu, v):
+        """pff_param_grad_noalloc: like param_grad, but the library allocates nothing; the caller passes
+        the three output tensors (one value per node each)."""
+        _check(self._lib.pff_param_grad_noalloc(self._h, _ptr(v, numel=self.n_dofs), _ptr(g_gc, numel=self.n_nodes),
+                                                _ptr(g_lambda, numel=self.n_nodes), _ptr(g_mu, numel=self.n_nodes)),
+               "pff_param_grad_noalloc")
+        return g_gc, g_lambda, g_mu
 
     def profile(self, family):
         """Starts timing one kernel family (PFF_PROF_*); 0 switches it off."""
