@@ -83,6 +83,8 @@ typedef struct {
   int gmres_restart;  /* FGMRES restart length (default 50) */
   int gmres_max_iters;/* FGMRES iteration cap per linear solve (default 500) */
   double lin_rtol;    /* FGMRES relative tolerance (paper: 1e-6) */
+  int fp64_mode;      /* FP64 Jacobian applies: 0 native FP64 arithmetic; 1 double-word (float-float)
+                         arithmetic on the FP32 pipe, about 48 significant bits (2D only; 3D uses 0) */
 } pff_params;
 
 typedef struct {
@@ -97,7 +99,8 @@ typedef struct {
 
 /* Defaults: the paper's tension test (lambda 121.15, mu 80.77, G_c 2.7e-3, kappa 1e-10), split none,
  * dim 2, p 1, N 32, eps 2/N, c 1, FP32 multigrid, Chebyshev degree 5 on [0.24, 1.2] lambda_max,
- * 15 eigen iterations, restart 50, relative tolerance 1e-6 (Sec. 5.1, Sec. 6.2). Never fails. */
+ * 15 eigen iterations, restart 50, relative tolerance 1e-6 (Sec. 5.1, Sec. 6.2), native FP64 applies.
+ * Never fails. */
 void pff_default_params(pff_params* p);
 
 /* Builds the mesh hierarchy and allocates per-level storage (Sec. 3.3 nested meshes).

@@ -9,7 +9,7 @@ static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags
                              const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
   constexpr size_t smem = op2d_smem<P, float>();
   static bool attr = false;
-  auto kern = k_op2d<P, float, PWJac<2, float, SPLIT>>;
+  auto kern = k_op2d<P, float, float, PWJac<2, float, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

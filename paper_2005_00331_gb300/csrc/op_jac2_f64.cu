@@ -9,7 +9,7 @@ static cudaError_t run_jac2(const double* x, double* y, const unsigned char* fla
                              const double* qp, int mode, int inmask, int outmask, cudaStream_t s) {
   constexpr size_t smem = op2d_smem<P, double>();
   static bool attr = false;
-  auto kern = k_op2d<P, double, PWJac<2, double, SPLIT>>;
+  auto kern = k_op2d<P, double, double, PWJac<2, double, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

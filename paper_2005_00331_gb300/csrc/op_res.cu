@@ -12,7 +12,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   else smem = op3d_smem<P, double>();
   static bool attr = false;
   void (*kern)(const double*, double*, const unsigned char*, Geom, Tab<double>, PWRes<DIM, SPLIT>, OpArgs);
-  if constexpr (DIM == 2) kern = k_op2d<P, double, PWRes<2, SPLIT>>;
+  if constexpr (DIM == 2) kern = k_op2d<P, double, double, PWRes<2, SPLIT>>;
   else kern = k_op3d<P, double, PWRes<3, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -99,6 +99,8 @@ struct LevelData {
   double* fields = nullptr; // 3 nodal fields (G_c, lambda, mu) when given
   double* qp64 = nullptr;
   float* qp32 = nullptr;
+  df64* qpdf = nullptr;     // per-point data as double-word pairs (float-float FP64 applies)
+  Tab<df64> tdf{};
   double* st64 = nullptr;
   double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
   double* di64 = nullptr;   // its inverse (Jacobi scaling)
@@ -226,6 +228,15 @@ void make_tabs(LevelData& L, int dim, int p) {
   }
   L.t64.hd = std::pow(L.h, dim);
   L.t32.hd = (float)L.t64.hd;
+  auto split = [](double v) { return df64((float)v, (float)(v - (double)(float)v)); };
+  for (int q = 0; q < MAXN; ++q) {
+    for (int k = 0; k < MAXN; ++k) {
+      L.tdf.S[q][k] = split(L.t64.S[q][k]);
+      L.tdf.D[q][k] = split(L.t64.D[q][k]);
+    }
+    L.tdf.W[q] = split(L.t64.W[q]);
+  }
+  L.tdf.hd = split(L.t64.hd);
 }
 
 void make_xfer(XferTab& xt, int p) {
@@ -360,8 +371,12 @@ int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask,
   CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
   const bool timed = prof_jac<Real>(c, l);
   if (timed) CR(prof_mark(c));
-  CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
-                outmask, c->s));
+  if (sizeof(Real) == 8 && c->prm.fp64_mode == 1 && c->dim == 2)
+    CK(launch_jac_df(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
+                     L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s));
+  else
+    CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
+                  outmask, c->s));
   if (timed) CR(prof_mark(c));
   return PFF_OK;
 }
@@ -372,7 +387,7 @@ int qp_setup_level(pff_ctx* c, int l) {
   const double* F = L.fields;
   CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
                      c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
-                     L.qp64, L.qp32, L.st64, c->s));
+                     L.qp64, L.qp32, L.qpdf, L.st64, c->s));
   return PFF_OK;
 }
 
@@ -396,32 +411,35 @@ int residual_into(pff_ctx* c, double* r) {
   return PFF_OK;
 }
 
-// lambda_max of D^{-1} G_uu and D^{-1} G_phiphi on level l by CG-Lanczos (FP64).
+// lambda_max of D^{-1} G_uu and D^{-1} G_phiphi on level l by CG-Lanczos, in the precision of the
+// multigrid that uses it (the estimate only places the smoothing interval); scalars in FP64.
+template <typename Real>
 int eig_estimate(pff_ctx* c, int l) {
   LevelData& L = c->lv[l];
   const long long n = L.nd, nu = c->dim * L.nn;
-  double *r = c->scratch, *z = r + c->lv[0].nd, *pv = z + c->lv[0].nd, *Ap = pv + c->lv[0].nd;
+  CR(ensure_work<Real>(c, l));
+  Real** w = work_of<Real>(L);
+  Real *r = w[0], *z = w[1], *pv = w[2], *Ap = w[3];
   double* scal = c->dres + 8;  // 12 doubles
   const int it_max = c->prm.eig_iters;
   double* ah = c->hist;
   double* bh = c->hist + 2 * it_max;
   CK(cudaMemsetAsync(scal, 0, 12 * sizeof(double), c->s));
   CK(cudaMemsetAsync(c->hist, 0, 4 * it_max * sizeof(double), c->s));
-  CK(launch_cg_init(n, nu, c->prm.eig_seed, L.flags, c->dim, L.nn, L.di64, r, z, pv, c->s));
-  CK(launch_dot2(n, nu, r, z, c->partial, scal + 0, c->s));
+  CK(launch_cg_init<Real>(n, nu, c->prm.eig_seed, L.flags, c->dim, L.nn, dinv_of<Real>(L), r, z, pv, c->s));
+  CK(launch_dot2<Real>(n, nu, r, z, c->partial, scal + 0, c->s));
   for (int it = 0; it < it_max; ++it) {
-    CR(apply_level<double>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
-    CK(launch_dot2(n, nu, pv, Ap, c->partial, scal + 2, c->s));
+    CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
+    CK(launch_dot2<Real>(n, nu, pv, Ap, c->partial, scal + 2, c->s));
     CK(launch_cg_scalars(0, it, it_max, scal, ah, bh, c->s));
-    CK(launch_cg_update(n, nu, Ap, L.di64, scal, r, z, c->s));
-    CK(launch_dot2(n, nu, r, z, c->partial, scal + 8, c->s));
+    CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, c->s));
+    CK(launch_dot2<Real>(n, nu, r, z, c->partial, scal + 8, c->s));
     CK(launch_cg_scalars(1, it, it_max, scal, ah, bh, c->s));
-    CK(launch_cg_pupdate(n, nu, z, scal, pv, c->s));
+    CK(launch_cg_pupdate<Real>(n, nu, z, scal, pv, c->s));
   }
   CK(launch_tridiag_eig(it_max, ah, bh, L.lam, c->s));
   return PFF_OK;
 }
-
 
 // Every launch of the multigrid setup of one Newton state (no host synchronisation inside).
 int mg_build(pff_ctx* c) {
@@ -437,7 +455,10 @@ int mg_build(pff_ctx* c) {
     LevelData& L = c->lv[l];
     CK(launch_diagonal(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, nullptr, c->s));
     CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
-    if (l < c->nlev - 1) CR(eig_estimate(c, l));
+    if (l < c->nlev - 1) {
+      if (c->prm.mg_precision == 32) CR(eig_estimate<float>(c, l));
+      else CR(eig_estimate<double>(c, l));
+    }
   }
   // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
   LevelData& C = c->lv[c->nlev - 1];
@@ -778,6 +799,7 @@ void pff_default_params(pff_params* p) {
   p->gmres_restart = 50;
   p->gmres_max_iters = 500;
   p->lin_rtol = 1e-6;
+  p->fp64_mode = 0;
 }
 
 const char* pff_strerror(int st) {
@@ -839,6 +861,8 @@ static int setup_impl(pff_ctx* c) {
     const long long nqp = L.g.ntiles * L.g.qpt;
     CR(dalloc(c, &L.qp64, nv * nqp));
     CR(dalloc(c, &L.qp32, nv * nqp));
+    CR(dalloc(c, &L.qpdf, nv * nqp));
+    CK(cudaMemsetAsync(L.qpdf, 0, sizeof(df64) * nv * nqp, c->s));
     CK(cudaMemsetAsync(L.qp64, 0, sizeof(double) * nv * nqp, c->s));
     CK(cudaMemsetAsync(L.qp32, 0, sizeof(float) * nv * nqp, c->s));
     if (l == 0) {
@@ -904,7 +928,7 @@ int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream) {
       p->coarse_min < 1 || (p->split != PFF_SPLIT_NONE && p->split != PFF_SPLIT_MIEHE) ||
       !valid_prec(p->mg_precision) || p->cheb_degree < 1 || !(p->cheb_hi > p->cheb_lo) || !(p->cheb_lo > 0) ||
       p->eig_iters < 1 || p->eig_iters > 64 || p->gmres_restart < 1 || p->gmres_max_iters < 1 ||
-      !(p->lin_rtol > 0) || !(p->eps > 0))
+      !(p->lin_rtol > 0) || !(p->eps > 0) || (p->fp64_mode != 0 && p->fp64_mode != 1))
     return PFF_ERR_INVALID_ARG;
   pff_ctx* c = new (std::nothrow) pff_ctx();
   if (!c) return PFF_ERR_OOM;

@@ -115,7 +115,8 @@ template <int DIM, int P, int SPLIT>
 __global__ void k_qp_setup(const double* __restrict__ U, const double* __restrict__ phit,
                            const double* __restrict__ gcf, const double* __restrict__ lamf,
                            const double* __restrict__ muf, Geom g, Tab<double> tb, MatConst mc,
-                           double* __restrict__ qp64, float* __restrict__ qp32, double* __restrict__ st64) {
+                           double* __restrict__ qp64, float* __restrict__ qp32, df64* __restrict__ qpdf,
+                           double* __restrict__ st64) {
   constexpr int NQ = ipow<DIM>(P + 1);
   constexpr int NM = Mandel<DIM>::NM;
   constexpr int NV = qp_nv(DIM, SPLIT);
@@ -199,6 +200,7 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
   for (int v = 0; v < NV; ++v) {
     qp64[base + v * g.qpt] = vals[v];
     if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
+    if (qpdf) qpdf[base + v * g.qpt] = df_from(vals[v]);
   }
   if (st64) {
     const long long sb = cq.tile * ST_NV * g.qpt + cq.qidx;
@@ -211,13 +213,13 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
 
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
                             const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
-                            const MatConst& mc, double* qp64, float* qp32, double* st64, cudaStream_t s) {
+                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s) {
   const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
   const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
   const unsigned gr = grid_for(tot, 128);
 #define PFF_CASE(DD, PP, SS)                                                                          \
   if (dim == DD && p == PP && split == SS) {                                                          \
-    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, st64); \
+    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, qpdf, st64); \
     return cudaGetLastError();                                                                        \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
@@ -1043,59 +1045,73 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+template <typename Real>
 __global__ void k_cg_init(long long n, unsigned long long seed, const unsigned char* __restrict__ flags, long long nn,
-                          const double* __restrict__ dinv, double* __restrict__ r, double* __restrict__ z,
-                          double* __restrict__ pv) {
+                          const Real* __restrict__ dinv, Real* __restrict__ r, Real* __restrict__ z,
+                          Real* __restrict__ pv) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int f = int(e / nn);
     const bool masked = (flags[e % nn] >> f) & 1u;
     const double v = masked ? 0.0 : (double)(splitmix64(seed, (uint64_t)e) >> 11) * 0x1.0p-53 - 0.5;
-    r[e] = v;
-    const double zz = dinv[e] * v;
+    r[e] = Real(v);
+    const Real zz = dinv[e] * Real(v);
     z[e] = zz;
     pv[e] = zz;
   }
 }
+template <typename Real>
 cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags, int dim,
-                           long long nn, const double* dinv, double* r, double* z, double* pv, cudaStream_t s) {
+                           long long nn, const Real* dinv, Real* r, Real* z, Real* pv, cudaStream_t s) {
   (void)nu;
   (void)dim;
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_cg_init<<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
+  count_launch(); k_cg_init<Real><<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
   return cudaGetLastError();
 }
 
-__global__ void k_cg_update(long long n, long long nu, const double* __restrict__ Ap, const double* __restrict__ dinv,
-                            const double* __restrict__ scal, double* __restrict__ r, double* __restrict__ z) {
-  const double a0 = scal[4], a1 = scal[5];
+template <typename Real>
+__global__ void k_cg_update(long long n, long long nu, const Real* __restrict__ Ap, const Real* __restrict__ dinv,
+                            const double* __restrict__ scal, Real* __restrict__ r, Real* __restrict__ z) {
+  const Real a0 = Real(scal[4]), a1 = Real(scal[5]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const double al = e < nu ? a0 : a1;
-    const double rr = r[e] - al * Ap[e];
+    const Real al = e < nu ? a0 : a1;
+    const Real rr = r[e] - al * Ap[e];
     r[e] = rr;
     z[e] = dinv[e] * rr;
   }
 }
-cudaError_t launch_cg_update(long long n, long long nu, const double* Ap, const double* dinv, const double* scal,
-                             double* r, double* z, cudaStream_t s) {
+template <typename Real>
+cudaError_t launch_cg_update(long long n, long long nu, const Real* Ap, const Real* dinv, const double* scal, Real* r,
+                             Real* z, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_cg_update<<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
+  count_launch(); k_cg_update<Real><<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
   return cudaGetLastError();
 }
-__global__ void k_cg_pupdate(long long n, long long nu, const double* __restrict__ z, const double* __restrict__ scal,
-                             double* __restrict__ pv) {
-  const double b0 = scal[6], b1 = scal[7];
+template <typename Real>
+__global__ void k_cg_pupdate(long long n, long long nu, const Real* __restrict__ z, const double* __restrict__ scal,
+                             Real* __restrict__ pv) {
+  const Real b0 = Real(scal[6]), b1 = Real(scal[7]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     pv[e] = z[e] + (e < nu ? b0 : b1) * pv[e];
 }
-cudaError_t launch_cg_pupdate(long long n, long long nu, const double* z, const double* scal, double* pv,
-                              cudaStream_t s) {
+template <typename Real>
+cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const double* scal, Real* pv, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_cg_pupdate<<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
+  count_launch(); k_cg_pupdate<Real><<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
   return cudaGetLastError();
 }
+#define PFF_INST_CG(R)                                                                                          \
+  template cudaError_t launch_cg_init<R>(long long, long long, unsigned long long, const unsigned char*, int,   \
+                                         long long, const R*, R*, R*, R*, cudaStream_t);                       \
+  template cudaError_t launch_cg_update<R>(long long, long long, const R*, const R*, const double*, R*, R*,     \
+                                           cudaStream_t);                                                      \
+  template cudaError_t launch_cg_pupdate<R>(long long, long long, const R*, const double*, R*, cudaStream_t);
+PFF_INST_CG(double)
+PFF_INST_CG(float)
+#undef PFF_INST_CG
 
 // scal: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1]
 __global__ void k_cg_scalars(int phase, int it, int iters, double* scal, double* ah, double* bh) {

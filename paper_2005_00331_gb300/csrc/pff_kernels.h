@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "pff_common.cuh"
+#include "pff_df64.cuh"
 
 namespace pff {
 
@@ -12,7 +13,7 @@ struct MatConst {
 // Per-point data of the Jacobian (FP64 and optionally an FP32 copy) and of the residual.
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
                             const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
-                            const MatConst& mc, double* qp64, float* qp32, double* st64, cudaStream_t s);
+                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s);
 // diag(G_uu, G_phiphi) of a level into d64 (zeroed here), masked rows set to 1; FP32 copy if d32.
 cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const unsigned char* flags,
                             const Geom& g, const Tab<double>& tb, double* d64, float* d32, cudaStream_t s);
@@ -76,13 +77,15 @@ template <typename Real>
 cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, const Real* Ax, const Real* dinv,
                         Real* d, Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
                         cudaStream_t s);
-// CG-Lanczos on the two diagonal blocks (FP64 vectors).
+// CG-Lanczos on the two diagonal blocks (vectors in the multigrid precision, scalars in FP64).
+template <typename Real>
 cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags,
-                           int dim, long long nn, const double* dinv, double* r, double* z, double* pv,
-                           cudaStream_t s);
-cudaError_t launch_cg_update(long long n, long long nu, const double* Ap, const double* dinv, const double* scal,
-                             double* r, double* z, cudaStream_t s);
-cudaError_t launch_cg_pupdate(long long n, long long nu, const double* z, const double* scal, double* pv,
+                           int dim, long long nn, const Real* dinv, Real* r, Real* z, Real* pv, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_cg_update(long long n, long long nu, const Real* Ap, const Real* dinv, const double* scal,
+                             Real* r, Real* z, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const double* scal, Real* pv,
                               cudaStream_t s);
 // scalar bookkeeping (single thread): phase 0 after <p,Ap>: alpha = rz/pAp; phase 1 after <r,z>_new:
 // beta = rz_new/rz, rz = rz_new. scal layout: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include "pff_common.cuh"
+#include "pff_df64.cuh"
 
 namespace pff {
 
@@ -28,6 +29,10 @@ cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y,
                           cudaStream_t s);
 cudaError_t launch_jac_d3(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                           const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s);
+// The same Jacobian in double-word arithmetic (FP64 vectors, per-point data as df64 pairs); 2D.
+cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                          const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
                           cudaStream_t s);
 // r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu.
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,

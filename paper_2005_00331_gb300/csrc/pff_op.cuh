@@ -11,6 +11,7 @@
 // active set) are written once, by the tile that owns the node.
 #pragma once
 #include "pff_common.cuh"
+#include "pff_df64.cuh"
 
 namespace pff {
 
@@ -42,7 +43,8 @@ struct PWJac {
   __device__ __forceinline__ void operator()(long long tile, long long qi, const QPIn<DIM, Real>& in,
                                              QPOut<DIM, Real>& out) const {
     constexpr int NM = Mandel<DIM>::NM;
-    constexpr Real RS2 = Real(0.70710678118654752440);
+    constexpr Real RS2 = rconst<Real>(0.70710678118654752440);
+    constexpr Real TWO = rconst<Real>(2.0);
     const Real* a = qp + tile * tstride + qi;
     Real em[NM];
 #pragma unroll
@@ -53,23 +55,24 @@ struct PWJac {
     Real tau[NM];
     int off;
     if constexpr (SPLIT == 0) {
-      const Real gl = a[0], gm2 = Real(2) * a[qpt];
-      Real tr = 0;
+      const Real gl = a[0], gm2 = TWO * a[qpt];
+      Real tr = em[0];
 #pragma unroll
-      for (int t = 0; t < DIM; ++t) tr += em[t];
+      for (int t = 1; t < DIM; ++t) tr = tr + em[t];
+      const Real gltr = gl * tr;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) tau[m] = gm2 * em[m] + (m < DIM ? gl * tr : Real(0));
+      for (int m = 0; m < NM; ++m) tau[m] = (m < DIM) ? fmac(gm2, em[m], gltr) : gm2 * em[m];
       off = 2;
     } else {
 #pragma unroll
-      for (int m = 0; m < NM; ++m) tau[m] = 0;
+      for (int m = 0; m < NM; ++m) tau[m] = Real(0);
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
 #pragma unroll
         for (int j = i; j < NM; ++j) {
           const Real cij = a[sym_index(NM, i, j) * qpt];
-          tau[i] += cij * em[j];
-          if (j != i) tau[j] += cij * em[i];
+          tau[i] = fmac(cij, em[j], tau[i]);
+          if (j != i) tau[j] = fmac(cij, em[i], tau[j]);
         }
       }
       off = NM * (NM + 1) / 2;
@@ -78,10 +81,10 @@ struct PWJac {
     Real cv = c * in.ph;
     if (mode == JM_FULL) {
 #pragma unroll
-      for (int m = 0; m < NM; ++m) cv += a[(off + m) * qpt] * em[m];
+      for (int m = 0; m < NM; ++m) cv = fmac(a[(off + m) * qpt], em[m], cv);
     } else if (mode == JM_TRANSPOSE) {
 #pragma unroll
-      for (int m = 0; m < NM; ++m) tau[m] += a[(off + m) * qpt] * in.ph;
+      for (int m = 0; m < NM; ++m) tau[m] = fmac(a[(off + m) * qpt], in.ph, tau[m]);
     }
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
@@ -214,9 +217,9 @@ struct Tile2 {
   static constexpr int NT = QPX * TY;
 };
 
-template <int P, typename Real, class PW>
+template <int P, typename Real, typename Store, class PW>
 __global__ void __launch_bounds__(Tile2<P>::NT)
-k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char* __restrict__ flags,
+k_op2d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
        Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
   using T = Tile2<P>;
   constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
@@ -251,7 +254,7 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
           if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
         }
 #pragma unroll
-        for (int f = 0; f < NF; ++f) v[f] = ((m >> f) & 1u) ? Real(0) : src[f * g.nn + node];
+        for (int f = 0; f < NF; ++f) v[f] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(src[f * g.nn + node]);
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) X[(f * NPY + r) * NPX + s] = v[f];
@@ -273,11 +276,11 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
 #pragma unroll
     for (int l = 0; l < n; ++l) {
       const Real* row = X + (f * NPY + ty * P + l) * NPX + cx * P;
-      Real b = 0, d = 0;
+      Real b = Sq[0] * row[0], d = Dq[0] * row[0];
 #pragma unroll
-      for (int k = 0; k < n; ++k) {
-        b += Sq[k] * row[k];
-        d += Dq[k] * row[k];
+      for (int k = 1; k < n; ++k) {
+        b = fmac(Sq[k], row[k], b);
+        d = fmac(Dq[k], row[k], d);
       }
       xb[f][l] = b;
       xd[f][l] = d;
@@ -287,8 +290,8 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
   for (int f = 0; f < NF; ++f)
 #pragma unroll
     for (int l = 0; l < n; ++l) {
-      ub[f][l] = 0;
-      ud[f][l] = 0;
+      ub[f][l] = Real(0);
+      ud[f][l] = Real(0);
     }
   if (inside) {
 #pragma unroll
@@ -302,22 +305,22 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
       QPIn<2, Real> in;
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        Real gx = 0, gy = 0;
+        Real gx = sj[0] * xd[k][0], gy = dj[0] * xb[k][0];
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
-          gx += sj[l] * xd[k][l];
-          gy += dj[l] * xb[k][l];
+        for (int l = 1; l < n; ++l) {
+          gx = fmac(sj[l], xd[k][l], gx);
+          gy = fmac(dj[l], xb[k][l], gy);
         }
         in.gu[k][0] = gx;
         in.gu[k][1] = gy;
       }
       {
-        Real v = 0, gx = 0, gy = 0;
+        Real v = sj[0] * xb[2][0], gx = sj[0] * xd[2][0], gy = dj[0] * xb[2][0];
 #pragma unroll
-        for (int l = 0; l < n; ++l) {
-          v += sj[l] * xb[2][l];
-          gx += sj[l] * xd[2][l];
-          gy += dj[l] * xb[2][l];
+        for (int l = 1; l < n; ++l) {
+          v = fmac(sj[l], xb[2][l], v);
+          gx = fmac(sj[l], xd[2][l], gx);
+          gy = fmac(dj[l], xb[2][l], gy);
         }
         in.ph = v;
         in.gph[0] = gx;
@@ -329,11 +332,11 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
       for (int l = 0; l < n; ++l) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          ub[k][l] += dj[l] * o.cu[k][1];
-          ud[k][l] += sj[l] * o.cu[k][0];
+          ub[k][l] = fmac(dj[l], o.cu[k][1], ub[k][l]);
+          ud[k][l] = fmac(sj[l], o.cu[k][0], ud[k][l]);
         }
-        ub[2][l] += sj[l] * o.cv + dj[l] * o.cg[1];
-        ud[2][l] += sj[l] * o.cg[0];
+        ub[2][l] = fmac(sj[l], o.cv, fmac(dj[l], o.cg[1], ub[2][l]));
+        ud[2][l] = fmac(sj[l], o.cg[0], ud[2][l]);
       }
     }
   }
@@ -364,7 +367,7 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
               const int o = ((f * TY + cy) * n + l) * QPX + cxx * n + q;
-              acc[f] += sk * UB[o] + dk * UD[o];
+              acc[f] = fmac(sk, UB[o], fmac(dk, UD[o], acc[f]));
             }
           }
         }
@@ -381,11 +384,11 @@ k_op2d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char
       for (int f = 0; f < NF; ++f) {
         const long long gi = f * g.nn + node;
         if ((m >> f) & 1u) {
-          if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Real(0);
+          if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
         } else if (low || high) {
-          atomicAdd(dst + gi, acc[f]);
+          atomicAdd(dst + gi, cvt<Store>(acc[f]));
         } else {
-          dst[gi] = acc[f];
+          dst[gi] = cvt<Store>(acc[f]);
         }
       }
     }

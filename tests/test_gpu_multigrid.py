@@ -101,11 +101,11 @@ def test_vcycle_fp32(dim, p, N, split):
     assert rel(z, S.vcycle(lv, r)) <= 1e-3
 
 
-@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("prec,fp64_mode", [(64, 0), (32, 0), (32, 1)])
 @pytest.mark.parametrize("dim,p,N,split", [(2, 2, 16, 1), (3, 2, 4, 1)])
-def test_fgmres_solve(prec, dim, p, N, split):
+def test_fgmres_solve(prec, fp64_mode, dim, p, N, split):
     pr = Problem(dim, p, N, split=split, seed=7, active_frac=0.1)
-    ctx = pr.context(mg_precision=prec)
+    ctx = pr.context(mg_precision=prec, fp64_mode=fp64_mode)
     Gm = fe.masked(pr.G(), pr.mask)
     b = np.where(pr.mask, 0.0, np.random.default_rng(12).normal(size=pr.mesh.n_dofs))
     x, its, relres = ctx.solve_linear(cuda(b))

@@ -110,3 +110,23 @@ def test_zero_strain_state_miehe():
     y = ctx.apply_jacobian(cuda(x)).cpu().numpy()
     assert rel(y, fe.masked(pr.G(), pr.mask) @ x) <= FP64_TOL
     assert rel(ctx.residual().cpu().numpy(), pr.residual()) <= FP64_TOL
+
+
+@pytest.mark.parametrize("p,N", [(1, 9), (2, 9), (3, 6), (4, 5)])
+@pytest.mark.parametrize("split", [0, 1])
+def test_apply_float_float_fp64(p, N, split):
+    """fp64_mode = 1: the FP64 Jacobian in double-word arithmetic on the FP32 pipe, all modes, 2D;
+    same 1e-12 tolerance as native FP64."""
+    from paper_2005_00331_gb300 import PFF_MASK_ADJOINT, PFF_MASK_RAW, PFF_MODE_BLOCKDIAG, PFF_MODE_TRANSPOSE
+    pr = Problem(2, p, N, split=split, seed=40 + p, active_frac=0.3)
+    ctx = pr.context(fp64_mode=1)
+    x = np.random.default_rng(p + 40).normal(size=pr.mesh.n_dofs)
+    xd = cuda(x)
+    G = pr.G()
+    assert rel(ctx.apply_jacobian(xd).cpu().numpy(), fe.masked(G, pr.mask) @ x) <= FP64_TOL
+    assert rel(ctx.apply_jacobian(xd, mode=PFF_MASK_RAW).cpu().numpy(), G @ x) <= FP64_TOL
+    Gb = pr.G(fe.MODE_BLOCKDIAG)
+    assert rel(ctx.apply_jacobian(xd, mode=PFF_MODE_BLOCKDIAG).cpu().numpy(), fe.masked(Gb, pr.mask) @ x) <= FP64_TOL
+    dmask = pr.mesh.dirichlet_mask()
+    y = ctx.apply_jacobian(xd, mode=PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT).cpu().numpy()
+    assert rel(y, G.T @ np.where(dmask, 0.0, x)) <= FP64_TOL
