@@ -228,7 +228,8 @@ int pff_param_grad_noalloc(pff_ctx* ctx, const double* v, double* g_gc, double* 
 int pff_profile(pff_ctx* ctx, int family);
 int pff_profile_result(pff_ctx* ctx, int* launches, double* total_ms);
 
-/* Number of CUDA kernels this library has launched since it was loaded (all contexts). */
+/* Number of CUDA kernels this library has launched since it was loaded (all contexts), counting
+ * the kernels inside each replay of a captured graph (captured launches themselves are not counted). */
 long long pff_launch_count(void);
 
 /* Human-readable name of a status code. */

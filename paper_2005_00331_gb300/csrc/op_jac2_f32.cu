@@ -7,22 +7,27 @@ namespace pff {
 template <int P, int SPLIT>
 static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
                              const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
-  constexpr size_t smem = op2d_smem<P, float>();
-  static bool attr = false;
-  auto kern = k_op2d<P, float, float, PWJac<2, float, SPLIT>>;
-  if (!attr) {
+  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT>();
+  static int grid_per_sm = 0;
+  auto kern = k_jac2_staged<P, float, float, SPLIT>;
+  if (!grid_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&grid_per_sm, kern, Tile2<P>::NT, smem);
+    if (e != cudaSuccess) return e;
+    if (grid_per_sm < 1) grid_per_sm = 1;
   }
-  PWJac<2, float, SPLIT> pw;
-  pw.qp = qp;
-  pw.qpt = g.qpt;
-  pw.tstride = (long long)qp_nv(2, SPLIT) * g.qpt;
-  pw.mode = mode;
+  int sms = 152;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  long long grid = (long long)sms * grid_per_sm;
+  if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
+  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa); }
   return cudaGetLastError();
 }
 

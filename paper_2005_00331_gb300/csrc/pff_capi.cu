@@ -147,6 +147,7 @@ struct pff_ctx {
   std::vector<cudaEvent_t> gev;  // created by pff_profile; graphs take slots in capture order
   int gnext = 0;
   std::vector<std::pair<int, int>> vrange[2][6], srange[2][6];
+  long long vkern[2][6] = {}, skern[2][6] = {};  // kernel launches per replay of each graph
   std::vector<std::pair<int, int>> pending;
   double prof_ms = 0.0;
   long long prof_n = 0;
@@ -471,15 +472,18 @@ int mg_build(pff_ctx* c) {
 
 // Captures fn into a CUDA graph on the private stream and instantiates it into *exec.
 template <class F>
-int capture_graph(pff_ctx* c, cudaGraphExec_t* exec, std::pair<int, int>* range, F fn) {
+int capture_graph(pff_ctx* c, cudaGraphExec_t* exec, std::pair<int, int>* range, long long* kernels, F fn) {
   cudaStream_t user = c->s;
   c->s = c->cap;
   const int ev0 = c->gnext;
+  const long long k0 = launch_count();
   cudaError_t e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal);
   c->capturing = true;
   int st = e == cudaSuccess ? fn() : PFF_ERR_CUDA;
   c->capturing = false;
   *range = {ev0, c->gnext - ((c->gnext - ev0) & 1)};
+  *kernels = launch_count() - k0;
+  add_launches(-*kernels);  // captured, not launched
   cudaGraph_t gr = nullptr;
   if (e == cudaSuccess) {
     const cudaError_t e2 = cudaStreamEndCapture(c->s, &gr);
@@ -508,7 +512,8 @@ int mg_setup(pff_ctx* c) {
     c->swarm[key] = true;
   } else {
     std::pair<int, int> rg;
-    if (!c->sgraph[key][pv] && capture_graph(c, &c->sgraph[key][pv], &rg, [&] { return mg_build(c); }) != PFF_OK) {
+    if (!c->sgraph[key][pv] &&
+        capture_graph(c, &c->sgraph[key][pv], &rg, &c->skern[key][pv], [&] { return mg_build(c); }) != PFF_OK) {
       c->use_graph = false;
       CR(mg_build(c));
       c->mg_ready = true;
@@ -517,6 +522,7 @@ int mg_setup(pff_ctx* c) {
     if (!c->sgraph[key][pv]) return PFF_ERR_CUDA;
     if (c->srange[key][pv].empty() && pv != PFF_PROF_OFF) c->srange[key][pv].push_back(rg);
     CK(cudaGraphLaunch(c->sgraph[key][pv], c->s));
+    add_launches(c->skern[key][pv]);
     if (pv != PFF_PROF_OFF)
       for (auto& r : c->srange[key][pv]) c->pending.push_back(r);
   }
@@ -609,12 +615,14 @@ int vcycle_exec(pff_ctx* c) {
   }
   std::pair<int, int> rg;
   if (!c->vgraph[gi][pv] &&
-      capture_graph(c, &c->vgraph[gi][pv], &rg, [&] { return vcycle_level<Real>(c, 0, w[0], w[1]); }) != PFF_OK) {
+      capture_graph(c, &c->vgraph[gi][pv], &rg, &c->vkern[gi][pv],
+                    [&] { return vcycle_level<Real>(c, 0, w[0], w[1]); }) != PFF_OK) {
     c->use_graph = false;
     return vcycle_level<Real>(c, 0, w[0], w[1]);
   }
   if (c->vrange[gi][pv].empty() && pv != PFF_PROF_OFF) c->vrange[gi][pv].push_back(rg);
   CK(cudaGraphLaunch(c->vgraph[gi][pv], c->s));
+  add_launches(c->vkern[gi][pv]);
   if (pv != PFF_PROF_OFF)
     for (auto& r : c->vrange[gi][pv]) c->pending.push_back(r);
   return PFF_OK;

@@ -33,8 +33,8 @@ template <int DIM, int P>
 struct TileCfg;
 template <> struct TileCfg<2, 1> { static constexpr int TX = 8, TY = 16, TZ = 1; };
 template <> struct TileCfg<2, 2> { static constexpr int TX = 8, TY = 8, TZ = 1; };
-template <> struct TileCfg<2, 3> { static constexpr int TX = 8, TY = 8, TZ = 1; };
-template <> struct TileCfg<2, 4> { static constexpr int TX = 8, TY = 8, TZ = 1; };
+template <> struct TileCfg<2, 3> { static constexpr int TX = 8, TY = 4, TZ = 1; };
+template <> struct TileCfg<2, 4> { static constexpr int TX = 8, TY = 4, TZ = 1; };
 template <> struct TileCfg<3, 1> { static constexpr int TX = 4, TY = 4, TZ = 2; };
 template <> struct TileCfg<3, 2> { static constexpr int TX = 4, TY = 2, TZ = 2; };
 template <> struct TileCfg<3, 3> { static constexpr int TX = 2, TY = 2, TZ = 2; };
@@ -42,7 +42,7 @@ template <> struct TileCfg<3, 4> { static constexpr int TX = 2, TY = 2, TZ = 1; 
 
 // Host-visible copy of the tile shapes (same numbers as TileCfg).
 inline void tile_shape(int dim, int p, int* t) {
-  static const int t2[4][3] = {{8, 16, 1}, {8, 8, 1}, {8, 8, 1}, {8, 8, 1}};
+  static const int t2[4][3] = {{8, 16, 1}, {8, 8, 1}, {8, 4, 1}, {8, 4, 1}};
   static const int t3[4][3] = {{4, 4, 2}, {4, 2, 2}, {2, 2, 2}, {2, 2, 1}};
   const int(*tt)[3] = dim == 2 ? t2 : t3;
   t[0] = tt[p - 1][0];

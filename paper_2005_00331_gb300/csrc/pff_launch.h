@@ -8,6 +8,7 @@ namespace pff {
 
 // Number of kernels launched by this library since it was loaded (all contexts).
 void count_launch();
+void add_launches(long long n);
 long long launch_count();
 
 // y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be

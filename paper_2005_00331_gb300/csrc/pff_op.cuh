@@ -212,7 +212,7 @@ __device__ __forceinline__ void cells_of_node(int r, int T, int& lo, int& hi) {
 // contractions of the cells sharing each node of the patch.
 template <int P>
 struct Tile2 {
-  static constexpr int TX = 8, TY = (P == 1 ? 16 : 8);
+  static constexpr int TX = 8, TY = (P == 1 ? 16 : (P == 2 ? 8 : 4));
   static constexpr int n = P + 1, NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n, QPY = TY * n;
   static constexpr int NT = QPX * TY;
 };
@@ -399,6 +399,263 @@ template <int P, typename Real>
 constexpr size_t op2d_smem() {
   using T = Tile2<P>;
   return sizeof(Real) * (size_t)(3 * T::NPY * T::NPX + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
+}
+
+// ===========================================================================================
+// 2D Jacobian kernel, persistent and staged: each CTA walks tiles blockIdx.x, +gridDim.x, ... and
+// copies the next tile's node patch and per-point data into shared memory with cp.async while it
+// computes the current tile (NSTAGE = 2; with NSTAGE = 1 the copy for the next tile overlaps the
+// store phase only). The arithmetic is that of k_op2d.
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, bool valid, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 4 : 0));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int P, typename Real>
+struct Stage2 {
+  static constexpr int NSTAGE = sizeof(Real) == 4 ? 2 : 1;
+};
+
+template <int P, typename Real, typename Store, int SPLIT>
+__global__ void __launch_bounds__(Tile2<P>::NT)
+k_jac2_staged(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
+              Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa) {
+  using T = Tile2<P>;
+  constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
+  constexpr int NPX = T::NPX, NPY = T::NPY, QPX = T::QPX;
+  constexpr int QPT = T::QPX * T::QPY;
+  constexpr int NV = qp_nv(2, SPLIT);
+  constexpr int NS = Stage2<P, Real>::NSTAGE;
+  constexpr int NT = T::NT;
+  constexpr int XS = NF * NPY * NPX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* QPs = reinterpret_cast<Real*>(smem_raw);                  // [NS][NV][QPT]
+  Store* Xs = reinterpret_cast<Store*>(QPs + NS * NV * QPT);      // [NS][NF][NPY][NPX] raw copies
+  Real* X = reinterpret_cast<Real*>(Xs + NS * XS);                // [NF][NPY][NPX] masked, compute type
+  Real* UB = X + XS;                                              // [NF][TY][n][QPX]
+  Real* UD = UB + NF * TY * n * QPX;
+  Real* sS = UD + NF * TY * n * QPX;
+  Real* sD = sS + n * n;
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * QPX + tx;
+  if (tid < n * n) {
+    sS[tid] = tb.S[tid / n][tid % n];
+    sD[tid] = tb.D[tid / n][tid % n];
+  }
+  const long long ntiles = g.ntiles;
+  auto prefetch = [&](long long tile, int st) {
+    const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
+    const int x0 = tix * TX * P, y0 = tiy * TY * P;
+    Store* xs = Xs + st * XS;
+    for (int i = tid; i < XS; i += NT) {
+      const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
+      const int gx = x0 + s, gy = y0 + r;
+      const bool ok = gx < g.n1 && gy < g.n1;
+      const long long gi = ok ? f * g.nn + gx + (long long)g.n1 * gy : 0;
+      cp_async_bytes(xs + i, src + gi, ok, (int)sizeof(Store));
+    }
+    const char* qsrc = reinterpret_cast<const char*>(qpg + tile * (long long)NV * QPT);
+    char* qdst = reinterpret_cast<char*>(QPs + st * NV * QPT);
+    constexpr int NCH = NV * QPT * (int)sizeof(Real) / 16;
+    for (int i = tid; i < NCH; i += NT) cp_async16(qdst + 16 * i, qsrc + 16 * i);
+  };
+
+  int it = 0;
+  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
+  cp_async_commit();
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = NS == 2 ? (it & 1) : 0;
+    if constexpr (NS == 2) {
+      const long long nxt = tile + gridDim.x;
+      if (nxt < ntiles) prefetch(nxt, st ^ 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
+    const int x0 = tix * TX * P, y0 = tiy * TY * P;
+    // masked compute-type node patch
+    const Store* xs = Xs + st * XS;
+    for (int rs = tid; rs < NPY * NPX; rs += NT) {
+      const int s = rs % NPX, r = rs / NPX;
+      const int gx = x0 + s, gy = y0 + r;
+      unsigned char m = 0;
+      if (oa.inmask != IN_RAW && gx < g.n1 && gy < g.n1) {
+        m = flags[gx + (long long)g.n1 * gy];
+        if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int i = f * NPY * NPX + rs;
+        X[i] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(xs[i]);
+      }
+    }
+    __syncthreads();
+    const int cx = tx / n, qi = tx % n;
+    const bool inside = (tix * TX + cx < g.N) && (tiy * TY + ty < g.N);
+    Real Sq[n], Dq[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      Sq[k] = sS[qi * n + k];
+      Dq[k] = sD[qi * n + k];
+    }
+    Real xb[NF][n], xd[NF][n];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        const Real* row = X + (f * NPY + ty * P + l) * NPX + cx * P;
+        Real b = Sq[0] * row[0], d = Dq[0] * row[0];
+#pragma unroll
+        for (int k = 1; k < n; ++k) {
+          b = fmac(Sq[k], row[k], b);
+          d = fmac(Dq[k], row[k], d);
+        }
+        xb[f][l] = b;
+        xd[f][l] = d;
+      }
+    Real ub[NF][n], ud[NF][n];
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        ub[f][l] = Real(0);
+        ud[f][l] = Real(0);
+      }
+    if (inside) {
+      PWJac<2, Real, SPLIT> pw;
+      pw.qp = QPs + st * NV * QPT;
+      pw.tstride = 0;
+      pw.qpt = QPT;
+      pw.mode = mode;
+#pragma unroll
+      for (int qj = 0; qj < n; ++qj) {
+        Real sj[n], dj[n];
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          sj[l] = sS[qj * n + l];
+          dj[l] = sD[qj * n + l];
+        }
+        QPIn<2, Real> in;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          Real gx = sj[0] * xd[k][0], gy = dj[0] * xb[k][0];
+#pragma unroll
+          for (int l = 1; l < n; ++l) {
+            gx = fmac(sj[l], xd[k][l], gx);
+            gy = fmac(dj[l], xb[k][l], gy);
+          }
+          in.gu[k][0] = gx;
+          in.gu[k][1] = gy;
+        }
+        {
+          Real v = sj[0] * xb[2][0], gx = sj[0] * xd[2][0], gy = dj[0] * xb[2][0];
+#pragma unroll
+          for (int l = 1; l < n; ++l) {
+            v = fmac(sj[l], xb[2][l], v);
+            gx = fmac(sj[l], xd[2][l], gx);
+            gy = fmac(dj[l], xb[2][l], gy);
+          }
+          in.ph = v;
+          in.gph[0] = gx;
+          in.gph[1] = gy;
+        }
+        QPOut<2, Real> o;
+        pw(0, (long long)(ty * n + qj) * QPX + tx, in, o);
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            ub[k][l] = fmac(dj[l], o.cu[k][1], ub[k][l]);
+            ud[k][l] = fmac(sj[l], o.cu[k][0], ud[k][l]);
+          }
+          ub[2][l] = fmac(sj[l], o.cv, fmac(dj[l], o.cg[1], ub[2][l]));
+          ud[2][l] = fmac(sj[l], o.cg[0], ud[2][l]);
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int l = 0; l < n; ++l) {
+        UB[((f * TY + ty) * n + l) * QPX + tx] = ub[f][l];
+        UD[((f * TY + ty) * n + l) * QPX + tx] = ud[f][l];
+      }
+    __syncthreads();
+    if constexpr (NS == 1) {
+      // the staging buffers are free: start the next tile's copies under the store phase
+      const long long nxt = tile + gridDim.x;
+      if (nxt < ntiles) prefetch(nxt, 0);
+      cp_async_commit();
+    }
+    for (int rs = tid; rs < NPY * NPX; rs += NT) {
+      const int s = rs % NPX, r = rs / NPX;
+      const int gx = x0 + s, gy = y0 + r;
+      if (gx >= g.n1 || gy >= g.n1) continue;
+      const int ylo = r == 0 ? 0 : (r - 1) / P, yhi = r / P < TY - 1 ? r / P : TY - 1;
+      const int xlo = s == 0 ? 0 : (s - 1) / P, xhi = s / P < TX - 1 ? s / P : TX - 1;
+      Real acc[NF] = {Real(0), Real(0), Real(0)};
+      for (int cy = ylo; cy <= yhi; ++cy) {
+        const int l = r - cy * P;
+        for (int cxx = xlo; cxx <= xhi; ++cxx) {
+          const int k = s - cxx * P;
+#pragma unroll
+          for (int q = 0; q < n; ++q) {
+            const Real sk = sS[q * n + k], dk = sD[q * n + k];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const int o = ((f * TY + cy) * n + l) * QPX + cxx * n + q;
+              acc[f] = fmac(sk, UB[o], fmac(dk, UD[o], acc[f]));
+            }
+          }
+        }
+      }
+      const long long node = gx + (long long)g.n1 * gy;
+      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0);
+      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1);
+      unsigned char m = 0;
+      if (oa.outmask != OUT_RAW) {
+        m = flags[node];
+        if (oa.outmask == OUT_ZERO_DIRICHLET) m &= dirichlet_bits(2);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const long long gi = f * g.nn + node;
+        if ((m >> f) & 1u) {
+          if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
+        } else if (low || high) {
+          atomicAdd(dst + gi, cvt<Store>(acc[f]));
+        } else {
+          dst[gi] = cvt<Store>(acc[f]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int P, typename Real, typename Store, int SPLIT>
+constexpr size_t jac2_staged_smem() {
+  using T = Tile2<P>;
+  constexpr int NS = Stage2<P, Real>::NSTAGE;
+  constexpr int XS = 3 * T::NPY * T::NPX;
+  return sizeof(Real) * (size_t)NS * qp_nv(2, SPLIT) * T::QPX * T::QPY + sizeof(Store) * (size_t)NS * XS +
+         sizeof(Real) * (size_t)(XS + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
 }
 
 // ===========================================================================================
