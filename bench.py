@@ -48,8 +48,13 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", choices=["newton", "apply"], default="newton",
-                    help="apply: time only the finest-level Jacobian apply (--precision) on the workload")
+    ap.add_argument("--mode", choices=["newton", "apply", "pdas"], default="newton",
+                    help="apply: time only the finest-level Jacobian apply (--precision) on the workload; "
+                         "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid")
+    ap.add_argument("--state", choices=["random", "tension"], default="random",
+                    help="random: seeded u, phi (the apply-sweep workload); tension: u = 0 with the top load "
+                         "lifted, phi = 1 except 0 on the slit (a load step from rest)")
+    ap.add_argument("--newton-rtol", type=float, default=1e-8)
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
     ap.add_argument("--fp64-mode", type=int, default=1,
                     help="FP64 Jacobian applies: 0 native FP64, 1 double-word arithmetic on the FP32 pipe (2D)")
@@ -72,6 +77,12 @@ def make_state(ctx, a, seed=0):
     nn, dim = ctx.n_nodes, a.dim
     fl = ctx.node_flags().cpu().numpy()
     U = np.zeros(ctx.n_dofs)
+    if getattr(a, "state", "random") == "tension":
+        U[(dim - 1) * nn:dim * nn][(fl & PFF_FLAG_TOP) != 0] = 1e-3
+        phi = np.ones(nn)
+        phi[(fl & PFF_FLAG_SLIT) != 0] = 0.0
+        U[dim * nn:] = phi
+        return U, phi.copy()
     dmask = np.concatenate([((fl >> c) & 1).astype(bool) for c in range(dim)])
     U[:dim * nn] = np.where(dmask, 0.0, inputs.displacement_noise(nn, dim, seed, std=1e-3))
     U[(dim - 1) * nn:dim * nn][(fl & PFF_FLAG_TOP) != 0] = 1e-3
@@ -369,6 +380,42 @@ def run_apply_only(a):
             "launches": launch_count() - n0}
 
 
+def run_pdas(a):
+    """Full active-set Newton solve (Alg. 1 to --newton-rtol) from the workload state, with the FP32
+    (mixed) and with the FP64 multigrid; both inside FP64 FGMRES with the FP64 residual."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"mode": "pdas", "workload": workload_name(a), "state": a.state, "newton_rtol": a.newton_rtol}
+    finals = {}
+    for prec in (32, 64):
+        ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+        U_h, po_h = make_state(ctx, a, seed=0)
+        U = torch.from_numpy(U_h).to(dev)
+        po = torch.from_numpy(po_h).to(dev)
+        # warm-up solve (graph capture, kernel attributes), then the timed solve from the same state
+        ctx.set_state(U, po, po, None)
+        ctx.solve_pdas(max_iters=30, newton_rtol=a.newton_rtol, check=False)
+        ctx.set_state(U, po, po, None)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, reps = ctx.solve_pdas(max_iters=30, newton_rtol=a.newton_rtol, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        finals[prec] = ctx.get_state()
+        out["mg_fp%d" % prec] = {
+            "status": st, "newton_steps": len(reps), "seconds": dt, "s_per_newton_step": dt / max(1, len(reps)),
+            "gmres_iters": [r["gmres_iters"] for r in reps], "res_norms": [r["res_norm"] for r in reps],
+            "n_active_final": reps[-1]["n_active"] if reps else None}
+        out["n_dofs"] = ctx.n_dofs
+        ctx.close()
+    d = (finals[32] - finals[64]).norm() / max(float(finals[64].norm()), 1e-300)
+    out["rel_diff_mixed_vs_fp64"] = float(d)
+    return out
+
+
 # ---- CPU oracle baseline ----------------------------------------------------------------------
 CPU_SAMPLE_CELLS = 32
 
@@ -444,6 +491,10 @@ def main():
     if a.mode == "apply":
         torch.cuda.set_device(local if world > 1 else 0)
         print(json.dumps(run_apply_only(a)))
+        return
+    if a.mode == "pdas":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_pdas(a)))
         return
     if world > 1:
         torch.cuda.set_device(local)

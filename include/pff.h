@@ -188,6 +188,13 @@ int pff_solve_linear(pff_ctx* ctx, const double* b, double* x, int* iters, doubl
  * non-NULL. `rep` (host, may be NULL) receives the report. Synchronous. */
 int pff_solve_newton_step(pff_ctx* ctx, double* U_out, pff_report* rep);
 
+/* Alg. 1 repeated from the current state until the active set no longer changes and
+ * ||R~_k|| <= newton_rtol * ||R~_0|| (paper: 1e-8), or max_iters steps. Reports of the steps go to
+ * `reps` (host array of max_iters entries, may be NULL); *n_steps receives the number of steps.
+ * Returns PFF_ERR_NOT_CONVERGED if the loop ended by max_iters, or the first failing step's status.
+ * The final state is the context's state (and is copied to U_out when non-NULL). Synchronous. */
+int pff_solve_pdas(pff_ctx* ctx, int max_iters, double newton_rtol, double* U_out, pff_report* reps, int* n_steps);
+
 /* Parameter gradients of the residual (not in the paper; needed for adjoints): for a test vector v
  * (DoF layout), g_gc = (dR/dG_c)^T v, g_lambda = (dR/dlambda)^T v, g_mu = (dR/dmu)^T v with the
  * material parameters as nodal fields, one value per node each, at the current state. Entries of v

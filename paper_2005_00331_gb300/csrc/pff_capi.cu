@@ -1183,6 +1183,33 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   return r.status;
 }
 
+int pff_solve_pdas(pff_ctx* c, int max_iters, double newton_rtol, double* U_out, pff_report* reps, int* n_steps) {
+  if (!c || max_iters < 1 || !(newton_rtol > 0)) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  double r0 = -1.0;
+  int st = PFF_ERR_NOT_CONVERGED, k = 0;
+  for (; k < max_iters;) {
+    pff_report r{};
+    const int s = pff_solve_newton_step(c, nullptr, &r);
+    if (reps) reps[k] = r;
+    ++k;
+    if (s != PFF_OK && s != PFF_ERR_NOT_CONVERGED) {
+      st = s;
+      break;
+    }
+    if (r0 < 0) r0 = r.res_norm;
+    // converged: active set unchanged against the previous step and the reduced residual small
+    if (k > 1 && r.n_changed == 0 && r.res_norm <= newton_rtol * r0) {
+      st = PFF_OK;
+      break;
+    }
+  }
+  if (n_steps) *n_steps = k;
+  if (U_out) CK(cudaMemcpyAsync(U_out, c->lv[0].U, sizeof(double) * c->lv[0].nd, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return st;
+}
+
 int pff_param_grad(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
   if (!c || !v) return PFF_ERR_INVALID_ARG;
   CR(ensure_qp(c));

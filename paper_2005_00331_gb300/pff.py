@@ -71,6 +71,7 @@ _SIGS = {
     "pff_vcycle": (_I, [_P, _P, _P]),
     "pff_solve_linear": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pff_solve_newton_step": (_I, [_P, _P, ctypes.POINTER(Report)]),
+    "pff_solve_pdas": (_I, [_P, _I, _D, _P, ctypes.POINTER(Report), ctypes.POINTER(_I)]),
     "pff_param_grad": (_I, [_P, _P, _P, _P, _P]),
     "pff_param_grad_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "pff_strerror": (ctypes.c_char_p, [_I]),
@@ -290,6 +291,16 @@ class Context:
         n, ms = _I(), _D()
         _check(self._lib.pff_profile_result(self._h, ctypes.byref(n), ctypes.byref(ms)), "pff_profile_result")
         return n.value, ms.value
+
+    def solve_pdas(self, max_iters=30, newton_rtol=1e-8, U_out=None, check=True):
+        """Alg. 1 repeated until the active set settles and ||R~|| <= newton_rtol ||R~_0||."""
+        reps = (Report * max_iters)()
+        n = _I()
+        st = self._lib.pff_solve_pdas(self._h, max_iters, newton_rtol, _ptr(U_out, numel=self.n_dofs), reps,
+                                      ctypes.byref(n))
+        if check:
+            _check(st, "pff_solve_pdas")
+        return st, [reps[i].as_dict() for i in range(n.value)]
 
     def param_grad(self, v):
         outs = [torch.empty(self.n_nodes, dtype=torch.float64, device=v.device) for _ in range(3)]

@@ -153,14 +153,9 @@ def test_pdas_loop_reaches_newton_tolerance():
     U[2 * m.n_nodes:] = phi
     ctx = setup_mesh(dim=2, degree=1, n_cells_1d=16, split=1, eps=2.0 / 16, mg_precision=32, lin_rtol=1e-10)
     ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
-    norms, changed = [], []
-    for k in range(15):
-        rep = ctx.solve_newton_step()
-        norms.append(rep["res_norm"])
-        changed.append(rep["n_changed"])
-        if k > 0 and rep["n_changed"] == 0 and rep["res_norm"] <= 1e-8 * norms[0]:
-            break
-    assert norms[-1] <= 1e-8 * norms[0] and changed[-1] == 0
+    st, reps = ctx.solve_pdas(max_iters=15, newton_rtol=1e-8)
+    norms = [r["res_norm"] for r in reps]
+    assert st == 0 and norms[-1] <= 1e-8 * norms[0] and reps[-1]["n_changed"] == 0
     Ug = ctx.get_state().cpu().numpy()
     R = fe.residual(m, prm, Ug, phi)
     act = ctx.get_active().cpu().numpy().astype(bool)
