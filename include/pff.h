@@ -84,7 +84,7 @@ typedef struct {
   int gmres_max_iters;/* FGMRES iteration cap per linear solve (default 500) */
   double lin_rtol;    /* FGMRES relative tolerance (paper: 1e-6) */
   int fp64_mode;      /* FP64 Jacobian applies: 0 native FP64 arithmetic; 1 double-word (float-float)
-                         arithmetic on the FP32 pipe, about 48 significant bits (2D only; 3D uses 0) */
+                         arithmetic on the FP32 pipe, about 48 significant bits */
 } pff_params;
 
 typedef struct {

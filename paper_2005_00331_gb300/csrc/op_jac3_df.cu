@@ -1,0 +1,43 @@
+// Explicit instantiations of the 3D Jacobian operator kernels in double-word (float-float)
+// arithmetic: FP64 vectors in global memory, per-point data as double-word pairs.
+#include "pff_launch.h"
+#include "pff_op.cuh"
+
+namespace pff {
+
+template <int P, int SPLIT>
+static cudaError_t run_jac3_df(const double* x, double* y, const unsigned char* flags, const Geom& g,
+                               const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
+                               cudaStream_t s) {
+  constexpr size_t smem = op3d_smem<P, df64>();
+  static bool attr = false;
+  auto kern = k_op3d<P, df64, double, PWJac<3, df64, SPLIT>>;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  PWJac<3, df64, SPLIT> pw;
+  pw.qp = qp;
+  pw.qpt = g.qpt;
+  pw.tstride = (long long)qp_nv(3, SPLIT) * g.qpt;
+  pw.mode = mode;
+  OpArgs oa{inmask, outmask};
+  const dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                          const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
+                          cudaStream_t s) {
+  if (dim != 3) return cudaErrorInvalidValue;
+#define PFF_CASE(PP, SS) \
+  if (p == PP && split == SS) return run_jac3_df<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s);
+  PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
+  PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
+#undef PFF_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pff

@@ -9,7 +9,7 @@ static cudaError_t run_jac3(const float* x, float* y, const unsigned char* flags
                              const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
   constexpr size_t smem = op3d_smem<P, float>();
   static bool attr = false;
-  auto kern = k_op3d<P, float, PWJac<3, float, SPLIT>>;
+  auto kern = k_op3d<P, float, float, PWJac<3, float, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -21,7 +21,8 @@ static cudaError_t run_jac3(const float* x, float* y, const unsigned char* flags
   pw.tstride = (long long)qp_nv(3, SPLIT) * g.qpt;
   pw.mode = mode;
   OpArgs oa{inmask, outmask};
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa); }
+  const dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

@@ -9,7 +9,7 @@ static cudaError_t run_jac3(const double* x, double* y, const unsigned char* fla
                              const double* qp, int mode, int inmask, int outmask, cudaStream_t s) {
   constexpr size_t smem = op3d_smem<P, double>();
   static bool attr = false;
-  auto kern = k_op3d<P, double, PWJac<3, double, SPLIT>>;
+  auto kern = k_op3d<P, double, double, PWJac<3, double, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -21,7 +21,8 @@ static cudaError_t run_jac3(const double* x, double* y, const unsigned char* fla
   pw.tstride = (long long)qp_nv(3, SPLIT) * g.qpt;
   pw.mode = mode;
   OpArgs oa{inmask, outmask};
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, 256, smem, s>>>(x, y, flags, g, tb, pw, oa); }
+  const dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
+  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
   return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   static bool attr = false;
   void (*kern)(const double*, double*, const unsigned char*, Geom, Tab<double>, PWRes<DIM, SPLIT>, OpArgs);
   if constexpr (DIM == 2) kern = k_op2d<P, double, double, PWRes<2, SPLIT>>;
-  else kern = k_op3d<P, double, PWRes<3, SPLIT>>;
+  else kern = k_op3d<P, double, double, PWRes<3, SPLIT>>;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -31,7 +31,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   pw.eps = eps;
   pw.kappa = kappa;
   OpArgs oa{IN_RAW, OUT_ZERO_DIRICHLET};
-  dim3 blk(256);
+  dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
   if constexpr (DIM == 2) blk = dim3(Tile2<P>::QPX, Tile2<P>::TY);
   if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(U, r, flags, g, tb, pw, oa); }
   return cudaGetLastError();

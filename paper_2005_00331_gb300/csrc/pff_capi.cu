@@ -372,9 +372,10 @@ int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask,
   CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
   const bool timed = prof_jac<Real>(c, l);
   if (timed) CR(prof_mark(c));
-  if (sizeof(Real) == 8 && c->prm.fp64_mode == 1 && c->dim == 2)
-    CK(launch_jac_df(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
-                     L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s));
+  if (sizeof(Real) == 8 && c->prm.fp64_mode == 1)
+    CK((c->dim == 2 ? launch_jac_df : launch_jac_df3)(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x),
+                                                      reinterpret_cast<double*>(y), L.flags, L.g, L.tdf, L.qpdf, mode,
+                                                      inmask, outmask, c->s));
   else
     CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
                   outmask, c->s));

@@ -35,6 +35,9 @@ cudaError_t launch_jac_d3(int dim, int p, int split, const float* x, float* y, c
 cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
                           cudaStream_t s);
+cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
+                           const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
+                           cudaStream_t s);
 // r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu.
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* st, double eps, double kappa,

@@ -659,202 +659,273 @@ constexpr size_t jac2_staged_smem() {
 }
 
 // ===========================================================================================
-// 3D operator kernel.
-template <int P, typename Real, class PW>
-__global__ void __launch_bounds__(256)
-k_op3d(const Real* __restrict__ src, Real* __restrict__ dst, const unsigned char* __restrict__ flags,
+// 3D operator kernel. Block (TX (p+1), TY (p+1), TZ): x- and y-contractions run as passes over the
+// tile's node patch in shared memory (a node row shared by two cells is contracted once); thread
+// (tx, ty, tz) then owns the Gauss pencil (tx, ty) of cell layer tz, contracts in z, applies the
+// pointwise functor at its p+1 points and accumulates the transposed z-contraction; transposed y-
+// and x-passes return to the nodes, whose seam copies are accumulated atomically.
+template <int P>
+struct Tile3 {
+  static constexpr int TX = TileCfg<3, P>::TX, TY = TileCfg<3, P>::TY, TZ = TileCfg<3, P>::TZ;
+  static constexpr int n = P + 1, NPX = TX * P + 1, NPY = TY * P + 1, NPZ = TZ * P + 1;
+  static constexpr int QPX = TX * n, QPY = TY * n, NT = QPX * QPY * TZ;
+};
+
+template <int P, typename Real, typename Store, class PW>
+__global__ void __launch_bounds__(Tile3<P>::NT)
+k_op3d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
        Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
-  constexpr int TX = TileCfg<3, P>::TX, TY = TileCfg<3, P>::TY, TZ = TileCfg<3, P>::TZ;
-  constexpr int n = P + 1, NF = 4;
-  constexpr int NPX = TX * P + 1, NPY = TY * P + 1, NPZ = TZ * P + 1;
-  constexpr int QPX = TX * n, QPY = TY * n;
+  using T = Tile3<P>;
+  constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, n = T::n, NF = 4;
+  constexpr int NPX = T::NPX, NPY = T::NPY, NPZ = T::NPZ, QPX = T::QPX, QPY = T::QPY;
+  constexpr int PLANE = QPY * QPX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* X = reinterpret_cast<Real*>(smem_raw);          // [NF][NPZ][NPY][NPX]; later W* and output
-  Real* XB = X + NF * NPZ * NPY * NPX;                   // [NF][NPZ][NPY][QPX]
-  Real* XD = XB + NF * NPZ * NPY * QPX;
-  Real* YB = XD + NF * NPZ * NPY * QPX;                  // [NF][NPZ][QPY][QPX]
-  Real* YX = YB + NF * NPZ * QPY * QPX;
-  Real* YY = YX + NF * NPZ * QPY * QPX;
-  Real* ZB = YY + NF * NPZ * QPY * QPX;                  // [NF][TZ][n][QPY][QPX]
-  Real* ZX = ZB + NF * TZ * n * QPY * QPX;
-  Real* ZY = ZX + NF * TZ * n * QPY * QPX;
+  Real* X = reinterpret_cast<Real*>(smem_raw);   // [NF][NPZ][NPY][NPX], later the output patch
+  Real* XB = X + NF * NPZ * NPY * NPX;            // [NF][NPZ][NPY][QPX], later WB
+  Real* XD = XB + NF * NPZ * NPY * QPX;           // later WD
+  Real* YB = XD + NF * NPZ * NPY * QPX;           // [NF][NPZ][QPY][QPX]
+  Real* YX = YB + NF * NPZ * PLANE;
+  Real* YY = YX + NF * NPZ * PLANE;
+  Real* ZB = YY + NF * NPZ * PLANE;               // [NF][TZ][n][QPY][QPX]
+  Real* ZX = ZB + NF * TZ * n * PLANE;
+  Real* ZY = ZX + NF * TZ * n * PLANE;
+  Real* sS = ZY + NF * TZ * n * PLANE;
+  Real* sD = sS + n * n;
 
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int tid = (tz * QPY + ty) * QPX + tx;
   const long long tile = blockIdx.x;
-  const int tx = int(tile % g.ntile[0]);
-  const int ty = int((tile / g.ntile[0]) % g.ntile[1]);
-  const int tz = int(tile / ((long long)g.ntile[0] * g.ntile[1]));
-  const int x0 = tx * TX * P, y0 = ty * TY * P, z0 = tz * TZ * P;
-  const int cx0 = tx * TX, cy0 = ty * TY, cz0 = tz * TZ;
+  const int tix = int(tile % g.ntile[0]);
+  const int tiy = int((tile / g.ntile[0]) % g.ntile[1]);
+  const int tiz = int(tile / ((long long)g.ntile[0] * g.ntile[1]));
+  const int x0 = tix * TX * P, y0 = tiy * TY * P, z0 = tiz * TZ * P;
   const long long n1 = g.n1, n1sq = n1 * n1;
-
-  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, r = (i / NPX) % NPY, t = (i / (NPX * NPY)) % NPZ, f = i / (NPX * NPY * NPZ);
-    const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
-    Real v = 0;
-    if (gx < g.n1 && gy < g.n1 && gz < g.n1) {
-      const long long node = gx + n1 * gy + n1sq * gz;
-      v = load_node(src, flags, node, f * g.nn + node, f, 3, oa.inmask);
-    }
-    X[i] = v;
+  if (tid < n * n) {
+    sS[tid] = tb.S[tid / n][tid % n];
+    sD[tid] = tb.D[tid / n][tid % n];
   }
+  for (int t = tz; t < NPZ; t += TZ)
+    for (int r = ty; r < NPY; r += QPY)
+      for (int s = tx; s < NPX; s += QPX) {
+        const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
+        Real v[NF] = {Real(0), Real(0), Real(0), Real(0)};
+        if (gx < g.n1 && gy < g.n1 && gz < g.n1) {
+          const long long node = gx + n1 * gy + n1sq * gz;
+          unsigned char m = 0;
+          if (oa.inmask != IN_RAW) {
+            m = flags[node];
+            if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(3);
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) v[f] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(src[f * g.nn + node]);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) X[((f * NPZ + t) * NPY + r) * NPX + s] = v[f];
+      }
   __syncthreads();
-  for (int i = threadIdx.x; i < NF * NPZ * NPY * QPX; i += blockDim.x) {
-    const int c = i % QPX, row = i / QPX;
-    const int cx = c / n, qi = c % n;
-    const Real* xr = X + row * NPX + cx * P;
-    Real b = 0, d = 0;
+  {  // x-pass at Gauss column tx
+    const int cx = tx / n, qi = tx % n;
+    Real Sq[n], Dq[n];
 #pragma unroll
     for (int k = 0; k < n; ++k) {
-      b += tb.S[qi][k] * xr[k];
-      d += tb.D[qi][k] * xr[k];
+      Sq[k] = sS[qi * n + k];
+      Dq[k] = sD[qi * n + k];
     }
-    XB[i] = b;
-    XD[i] = d;
+    for (int t = tz; t < NPZ; t += TZ)
+      for (int r = ty; r < NPY; r += QPY)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const Real* row = X + ((f * NPZ + t) * NPY + r) * NPX + cx * P;
+          Real b = Sq[0] * row[0], d = Dq[0] * row[0];
+#pragma unroll
+          for (int k = 1; k < n; ++k) {
+            b = fmac(Sq[k], row[k], b);
+            d = fmac(Dq[k], row[k], d);
+          }
+          const int o = ((f * NPZ + t) * NPY + r) * QPX + tx;
+          XB[o] = b;
+          XD[o] = d;
+        }
   }
   __syncthreads();
-  // y-pass: YB = S_y XB, YX = S_y XD, YY = D_y XB
-  for (int i = threadIdx.x; i < NF * NPZ * QPY * QPX; i += blockDim.x) {
-    const int c = i % QPX, qyc = (i / QPX) % QPY, ft = i / (QPX * QPY);  // ft = f*NPZ + t
-    const int cy = qyc / n, qj = qyc % n;
-    Real b = 0, dx = 0, dy = 0;
+  {  // y-pass at Gauss row ty
+    const int cy = ty / n, qj = ty % n;
+    Real Sj[n], Dj[n];
 #pragma unroll
     for (int l = 0; l < n; ++l) {
-      const int idx = (ft * NPY + cy * P + l) * QPX + c;
-      b += tb.S[qj][l] * XB[idx];
-      dx += tb.S[qj][l] * XD[idx];
-      dy += tb.D[qj][l] * XB[idx];
+      Sj[l] = sS[qj * n + l];
+      Dj[l] = sD[qj * n + l];
     }
-    YB[i] = b;
-    YX[i] = dx;
-    YY[i] = dy;
+    for (int t = tz; t < NPZ; t += TZ)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int base = ((f * NPZ + t) * NPY + cy * P) * QPX + tx;
+        Real b = Sj[0] * XB[base], dx = Sj[0] * XD[base], dy = Dj[0] * XB[base];
+#pragma unroll
+        for (int l = 1; l < n; ++l) {
+          const int o = base + l * QPX;
+          b = fmac(Sj[l], XB[o], b);
+          dx = fmac(Sj[l], XD[o], dx);
+          dy = fmac(Dj[l], XB[o], dy);
+        }
+        const int o = (f * NPZ + t) * PLANE + ty * QPX + tx;
+        YB[o] = b;
+        YX[o] = dx;
+        YY[o] = dy;
+      }
   }
   __syncthreads();
-  // z-pass, pointwise, transposed z-pass: one thread per (cell layer, Gauss column)
-  constexpr int PLANE = QPY * QPX;
-  for (int i = threadIdx.x; i < TZ * PLANE; i += blockDim.x) {
-    const int c = i % QPX, qyc = (i / QPX) % QPY, cz = i / PLANE;
-    const int col = qyc * QPX + c;
+  {  // z-pass, pointwise, transposed z-pass: pencil (tx, ty) of cell layer tz
+    const int col = ty * QPX + tx;
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int l = 0; l < n; ++l) {
-        const int o = ((f * TZ + cz) * n + l) * PLANE + col;
-        ZB[o] = 0;
-        ZX[o] = 0;
-        ZY[o] = 0;
+        const int o = ((f * TZ + tz) * n + l) * PLANE + col;
+        ZB[o] = Real(0);
+        ZX[o] = Real(0);
+        ZY[o] = Real(0);
       }
-    const bool inside = (cx0 + c / n < g.N) && (cy0 + qyc / n < g.N) && (cz0 + cz < g.N);
-    if (!inside) continue;
-    for (int qk = 0; qk < n; ++qk) {
-      Real vb[NF], vx[NF], vy[NF], vz[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        Real b = 0, dx = 0, dy = 0, dz = 0;
+    const bool inside = (tix * TX + tx / n < g.N) && (tiy * TY + ty / n < g.N) && (tiz * TZ + tz < g.N);
+    if (inside) {
+      for (int qk = 0; qk < n; ++qk) {
+        Real sk[n], dk[n];
 #pragma unroll
         for (int l = 0; l < n; ++l) {
-          const int idx = (f * NPZ + cz * P + l) * PLANE + col;
-          const Real s = tb.S[qk][l];
-          b += s * YB[idx];
-          dx += s * YX[idx];
-          dy += s * YY[idx];
-          dz += tb.D[qk][l] * YB[idx];
+          sk[l] = sS[qk * n + l];
+          dk[l] = sD[qk * n + l];
         }
-        vb[f] = b;
-        vx[f] = dx;
-        vy[f] = dy;
-        vz[f] = dz;
-      }
-      QPIn<3, Real> in;
+        QPIn<3, Real> in;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        in.gu[k][0] = vx[k];
-        in.gu[k][1] = vy[k];
-        in.gu[k][2] = vz[k];
-      }
-      in.ph = vb[3];
-      in.gph[0] = vx[3];
-      in.gph[1] = vy[3];
-      in.gph[2] = vz[3];
-      QPOut<3, Real> o;
-      pw(tile, (long long)(cz * n + qk) * PLANE + col, in, o);
+        for (int f = 0; f < NF; ++f) {
+          const int base = (f * NPZ + tz * P) * PLANE + col;
+          Real b = sk[0] * YB[base], dx = sk[0] * YX[base], dy = sk[0] * YY[base], dz = dk[0] * YB[base];
 #pragma unroll
-      for (int l = 0; l < n; ++l) {
-        const Real s = tb.S[qk][l], d = tb.D[qk][l];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int oi = ((k * TZ + cz) * n + l) * PLANE + col;
-          ZB[oi] += d * o.cu[k][2];
-          ZX[oi] += s * o.cu[k][0];
-          ZY[oi] += s * o.cu[k][1];
+          for (int l = 1; l < n; ++l) {
+            const int o = base + l * PLANE;
+            b = fmac(sk[l], YB[o], b);
+            dx = fmac(sk[l], YX[o], dx);
+            dy = fmac(sk[l], YY[o], dy);
+            dz = fmac(dk[l], YB[o], dz);
+          }
+          if (f < 3) {
+            in.gu[f][0] = dx;
+            in.gu[f][1] = dy;
+            in.gu[f][2] = dz;
+          } else {
+            in.ph = b;
+            in.gph[0] = dx;
+            in.gph[1] = dy;
+            in.gph[2] = dz;
+          }
         }
-        const int oi = ((3 * TZ + cz) * n + l) * PLANE + col;
-        ZB[oi] += s * o.cv + d * o.cg[2];
-        ZX[oi] += s * o.cg[0];
-        ZY[oi] += s * o.cg[1];
+        QPOut<3, Real> o;
+        pw(tile, (long long)(tz * n + qk) * PLANE + col, in, o);
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int oi = ((k * TZ + tz) * n + l) * PLANE + col;
+            ZB[oi] = fmac(dk[l], o.cu[k][2], ZB[oi]);
+            ZX[oi] = fmac(sk[l], o.cu[k][0], ZX[oi]);
+            ZY[oi] = fmac(sk[l], o.cu[k][1], ZY[oi]);
+          }
+          const int oi = ((3 * TZ + tz) * n + l) * PLANE + col;
+          ZB[oi] = fmac(sk[l], o.cv, fmac(dk[l], o.cg[2], ZB[oi]));
+          ZX[oi] = fmac(sk[l], o.cg[0], ZX[oi]);
+          ZY[oi] = fmac(sk[l], o.cg[1], ZY[oi]);
+        }
       }
     }
   }
   __syncthreads();
-  // transposed y-pass into WB, WD [NF][NPZ][NPY][QPX] (reusing XB, XD)
+  // transposed y-pass into WB, WD [NF][NPZ][NPY][QPX] (reusing XB, XD): node row r of plane t
   Real* WB = XB;
   Real* WD = XD;
-  for (int i = threadIdx.x; i < NF * NPZ * NPY * QPX; i += blockDim.x) {
-    const int c = i % QPX, r = (i / QPX) % NPY, t = (i / (QPX * NPY)) % NPZ, f = i / (QPX * NPY * NPZ);
-    int zlo, zhi, ylo, yhi;
-    cells_of_node<P>(t, TZ, zlo, zhi);
-    cells_of_node<P>(r, TY, ylo, yhi);
-    Real wb = 0, wd = 0;
-    for (int cz = zlo; cz <= zhi; ++cz) {
-      const int lz = t - cz * P;
-      for (int cy = ylo; cy <= yhi; ++cy) {
-        const int ly = r - cy * P;
-        const int base = ((f * TZ + cz) * n + lz) * PLANE + (cy * n) * QPX + c;
+  for (int t = tz; t < NPZ; t += TZ) {
+    const int zlo = t == 0 ? 0 : (t - 1) / P, zhi = t / P < TZ - 1 ? t / P : TZ - 1;
+    for (int r = ty; r < NPY; r += QPY) {
+      const int ylo = r == 0 ? 0 : (r - 1) / P, yhi = r / P < TY - 1 ? r / P : TY - 1;
+      Real wb[NF], wd[NF];
 #pragma unroll
-        for (int qj = 0; qj < n; ++qj) {
-          const int o = base + qj * QPX;
-          wb += tb.S[qj][ly] * ZB[o] + tb.D[qj][ly] * ZY[o];
-          wd += tb.S[qj][ly] * ZX[o];
+      for (int f = 0; f < NF; ++f) {
+        wb[f] = Real(0);
+        wd[f] = Real(0);
+      }
+      for (int cz = zlo; cz <= zhi; ++cz) {
+        const int lz = t - cz * P;
+        for (int cy = ylo; cy <= yhi; ++cy) {
+          const int ly = r - cy * P;
+#pragma unroll
+          for (int qj = 0; qj < n; ++qj) {
+            const Real s = sS[qj * n + ly], d = sD[qj * n + ly];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const int o = ((f * TZ + cz) * n + lz) * PLANE + (cy * n + qj) * QPX + tx;
+              wb[f] = fmac(s, ZB[o], fmac(d, ZY[o], wb[f]));
+              wd[f] = fmac(s, ZX[o], wd[f]);
+            }
+          }
         }
       }
-    }
-    WB[i] = wb;
-    WD[i] = wd;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, row = i / NPX;
-    int xlo, xhi;
-    cells_of_node<P>(s, TX, xlo, xhi);
-    Real acc = 0;
-    for (int cx = xlo; cx <= xhi; ++cx) {
-      const int k = s - cx * P;
-      const Real* wb = WB + row * QPX + cx * n;
-      const Real* wd = WD + row * QPX + cx * n;
 #pragma unroll
-      for (int qi = 0; qi < n; ++qi) acc += tb.S[qi][k] * wb[qi] + tb.D[qi][k] * wd[qi];
+      for (int f = 0; f < NF; ++f) {
+        const int o = ((f * NPZ + t) * NPY + r) * QPX + tx;
+        WB[o] = wb[f];
+        WD[o] = wd[f];
+      }
     }
-    X[i] = acc;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < NF * NPZ * NPY * NPX; i += blockDim.x) {
-    const int s = i % NPX, r = (i / NPX) % NPY, t = (i / (NPX * NPY)) % NPZ, f = i / (NPX * NPY * NPZ);
-    const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
-    if (gx >= g.n1 || gy >= g.n1 || gz >= g.n1) continue;
-    const long long node = gx + n1 * gy + n1sq * gz;
-    const bool low = (s == 0 && tx > 0) || (r == 0 && ty > 0) || (t == 0 && tz > 0);
-    const bool high = (s == NPX - 1 && tx < g.ntile[0] - 1) || (r == NPY - 1 && ty < g.ntile[1] - 1) ||
-                      (t == NPZ - 1 && tz < g.ntile[2] - 1);
-    store_node(dst, src, flags, node, f * g.nn + node, f, 3, X[i], low, high, oa.outmask);
-  }
+  // transposed x-pass and store
+  for (int t = tz; t < NPZ; t += TZ)
+    for (int r = ty; r < NPY; r += QPY)
+      for (int s = tx; s < NPX; s += QPX) {
+        const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
+        if (gx >= g.n1 || gy >= g.n1 || gz >= g.n1) continue;
+        const int xlo = s == 0 ? 0 : (s - 1) / P, xhi = s / P < TX - 1 ? s / P : TX - 1;
+        Real acc[NF] = {Real(0), Real(0), Real(0), Real(0)};
+        for (int cx = xlo; cx <= xhi; ++cx) {
+          const int k = s - cx * P;
+#pragma unroll
+          for (int qi = 0; qi < n; ++qi) {
+            const Real sv = sS[qi * n + k], dv = sD[qi * n + k];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+              const int o = ((f * NPZ + t) * NPY + r) * QPX + cx * n + qi;
+              acc[f] = fmac(sv, WB[o], fmac(dv, WD[o], acc[f]));
+            }
+          }
+        }
+        const long long node = gx + n1 * gy + n1sq * gz;
+        const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0) || (t == 0 && tiz > 0);
+        const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1) ||
+                          (t == NPZ - 1 && tiz < g.ntile[2] - 1);
+        unsigned char m = 0;
+        if (oa.outmask != OUT_RAW) {
+          m = flags[node];
+          if (oa.outmask == OUT_ZERO_DIRICHLET) m &= dirichlet_bits(3);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const long long gi = f * g.nn + node;
+          if ((m >> f) & 1u) {
+            if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
+          } else if (low || high) {
+            atomicAdd(dst + gi, cvt<Store>(acc[f]));
+          } else {
+            dst[gi] = cvt<Store>(acc[f]);
+          }
+        }
+      }
 }
 
 template <int P, typename Real>
 constexpr size_t op3d_smem() {
-  constexpr int TX = TileCfg<3, P>::TX, TY = TileCfg<3, P>::TY, TZ = TileCfg<3, P>::TZ;
-  constexpr int n = P + 1, NF = 4, NPX = TX * P + 1, NPY = TY * P + 1, NPZ = TZ * P + 1;
-  constexpr int QPX = TX * n, QPY = TY * n;
-  return sizeof(Real) * (size_t)(NF * NPZ * NPY * NPX + 2 * NF * NPZ * NPY * QPX + 3 * NF * NPZ * QPY * QPX +
-                                 3 * NF * TZ * n * QPY * QPX);
+  using T = Tile3<P>;
+  constexpr int NF = 4, PLANE = T::QPX * T::QPY;
+  return sizeof(Real) * (size_t)(NF * T::NPZ * T::NPY * T::NPX + 2 * NF * T::NPZ * T::NPY * T::QPX +
+                                 3 * NF * T::NPZ * PLANE + 3 * NF * T::TZ * T::n * PLANE + 2 * T::n * T::n);
 }
 
 }  // namespace pff

@@ -112,13 +112,14 @@ def test_zero_strain_state_miehe():
     assert rel(ctx.residual().cpu().numpy(), pr.residual()) <= FP64_TOL
 
 
-@pytest.mark.parametrize("p,N", [(1, 9), (2, 9), (3, 6), (4, 5)])
+@pytest.mark.parametrize("dim,p,N", [(2, 1, 9), (2, 2, 9), (2, 3, 6), (2, 4, 5), (3, 1, 5), (3, 2, 3), (3, 3, 3),
+                                     (3, 4, 2)])
 @pytest.mark.parametrize("split", [0, 1])
-def test_apply_float_float_fp64(p, N, split):
-    """fp64_mode = 1: the FP64 Jacobian in double-word arithmetic on the FP32 pipe, all modes, 2D;
+def test_apply_float_float_fp64(dim, p, N, split):
+    """fp64_mode = 1: the FP64 Jacobian in double-word arithmetic on the FP32 pipe, all modes;
     same 1e-12 tolerance as native FP64."""
     from paper_2005_00331_gb300 import PFF_MASK_ADJOINT, PFF_MASK_RAW, PFF_MODE_BLOCKDIAG, PFF_MODE_TRANSPOSE
-    pr = Problem(2, p, N, split=split, seed=40 + p, active_frac=0.3)
+    pr = Problem(dim, p, N, split=split, seed=40 + p, active_frac=0.3)
     ctx = pr.context(fp64_mode=1)
     x = np.random.default_rng(p + 40).normal(size=pr.mesh.n_dofs)
     xd = cuda(x)
