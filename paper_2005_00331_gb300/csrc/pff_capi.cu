@@ -105,7 +105,13 @@ struct LevelData {
   double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
   double* di64 = nullptr;   // its inverse (Jacobi scaling)
   float* di32 = nullptr;
-  double* lam = nullptr;    // device [lmax_u, lmax_phi, lmin_u, lmin_phi]
+  double* lam = nullptr;    // device [lmax_u, lmax_phi, lower bounds]
+  // per-level reduction scratch, so that the levels' setup branches can run concurrently
+  double* lscal = nullptr;  // 16
+  double* lhist = nullptr;  // 4 * eig_iters
+  double* lpart = nullptr;  // reduction partials
+  cudaStream_t aux = nullptr;
+  cudaEvent_t join = nullptr;
   // multigrid work vectors, per precision: r, e, t, res, dv, s
   double* w64[6] = {};
   float* w32[6] = {};
@@ -137,6 +143,7 @@ struct pff_ctx {
   std::vector<void*> allocs;
   // V-cycle replayed as a CUDA graph (captured once on a private stream; buffers never move)
   cudaStream_t cap = nullptr;
+  cudaEvent_t fork = nullptr;
   // graphs: [0] FP64 / [1] FP32 V-cycle; setup without / with nodal fields; each in a plain variant
   // and one variant per timed kernel family (event-record nodes around the timed launches)
   cudaGraphExec_t vgraph[2][6] = {};
@@ -422,20 +429,20 @@ int eig_estimate(pff_ctx* c, int l) {
   CR(ensure_work<Real>(c, l));
   Real** w = work_of<Real>(L);
   Real *r = w[0], *z = w[1], *pv = w[2], *Ap = w[3];
-  double* scal = c->dres + 8;  // 12 doubles
+  double* scal = L.lscal;  // 12 doubles
   const int it_max = c->prm.eig_iters;
-  double* ah = c->hist;
-  double* bh = c->hist + 2 * it_max;
+  double* ah = L.lhist;
+  double* bh = L.lhist + 2 * it_max;
   CK(cudaMemsetAsync(scal, 0, 12 * sizeof(double), c->s));
-  CK(cudaMemsetAsync(c->hist, 0, 4 * it_max * sizeof(double), c->s));
+  CK(cudaMemsetAsync(L.lhist, 0, 4 * it_max * sizeof(double), c->s));
   CK(launch_cg_init<Real>(n, nu, c->prm.eig_seed, L.flags, c->dim, L.nn, dinv_of<Real>(L), r, z, pv, c->s));
-  CK(launch_dot2<Real>(n, nu, r, z, c->partial, scal + 0, c->s));
+  CK(launch_dot2<Real>(n, nu, r, z, L.lpart, scal + 0, c->s));
   for (int it = 0; it < it_max; ++it) {
     CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
-    CK(launch_dot2<Real>(n, nu, pv, Ap, c->partial, scal + 2, c->s));
+    CK(launch_dot2<Real>(n, nu, pv, Ap, L.lpart, scal + 2, c->s));
     CK(launch_cg_scalars(0, it, it_max, scal, ah, bh, c->s));
     CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, c->s));
-    CK(launch_dot2<Real>(n, nu, r, z, c->partial, scal + 8, c->s));
+    CK(launch_dot2<Real>(n, nu, r, z, L.lpart, scal + 8, c->s));
     CK(launch_cg_scalars(1, it, it_max, scal, ah, bh, c->s));
     CK(launch_cg_pupdate<Real>(n, nu, z, scal, pv, c->s));
   }
@@ -443,7 +450,31 @@ int eig_estimate(pff_ctx* c, int l) {
   return PFF_OK;
 }
 
-// Every launch of the multigrid setup of one Newton state (no host synchronisation inside).
+// Setup work of one level that does not depend on other levels once its state is known: per-point
+// data (coarse levels), diagonal and its inverse, lambda_max (smoothed levels) or the dense coarse
+// inverses (coarsest level).
+int mg_level_branch(pff_ctx* c, int l) {
+  LevelData& L = c->lv[l];
+  if (l > 0) CR(qp_setup_level(c, l));
+  CK(launch_diagonal(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, nullptr, c->s));
+  CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
+  if (l < c->nlev - 1) {
+    if (c->prm.mg_precision == 32) CR(eig_estimate<float>(c, l));
+    else CR(eig_estimate<double>(c, l));
+  } else {
+    // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
+    const int nn = (int)L.nn, nu = c->dim * nn;
+    CK(launch_coarse_assemble(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, c->Au, c->Ap, c->Bc, c->s));
+    CK(launch_gj_inverse(c->Au, nu, c->gjbuf, c->s));
+    CK(launch_gj_inverse(c->Ap, nn, c->gjbuf + 4 * nu, c->s));
+  }
+  return PFF_OK;
+}
+
+// Every launch of the multigrid setup of one Newton state (no host synchronisation inside): the
+// state is carried down the levels in sequence, then every level's branch runs on its own stream
+// (forked from and joined back into the context's stream with events, which a graph capture turns
+// into parallel branches).
 int mg_build(pff_ctx* c) {
   const int nf_state = c->dim + 2;  // U (dim+1 fields) and phi~ are contiguous
   for (int l = 1; l < c->nlev; ++l) {
@@ -451,23 +482,24 @@ int mg_build(pff_ctx* c) {
     CK(launch_state_interp(c->dim, c->p, F.U, L.U, nf_state, F.g, L.g, c->xt, c->s));
     if (c->has_fields) CK(launch_state_interp(c->dim, c->p, F.fields, L.fields, 3, F.g, L.g, c->xt, c->s));
     CK(launch_coarse_active(c->dim, c->p, F.flags, L.flags, F.g, L.g, c->xt, c->s));
-    CR(qp_setup_level(c, l));
   }
-  for (int l = 0; l < c->nlev; ++l) {
+  CK(cudaEventRecord(c->fork, c->s));
+  const cudaStream_t main_s = c->s;
+  int st = PFF_OK;
+  for (int l = 0; l < c->nlev && st == PFF_OK; ++l) {
     LevelData& L = c->lv[l];
-    CK(launch_diagonal(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, nullptr, c->s));
-    CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
-    if (l < c->nlev - 1) {
-      if (c->prm.mg_precision == 32) CR(eig_estimate<float>(c, l));
-      else CR(eig_estimate<double>(c, l));
+    if (cudaStreamWaitEvent(L.aux, c->fork, 0) != cudaSuccess) {
+      st = PFF_ERR_CUDA;
+      break;
     }
+    c->s = L.aux;
+    st = mg_level_branch(c, l);
+    c->s = main_s;
+    if (st == PFF_OK && cudaEventRecord(L.join, L.aux) != cudaSuccess) st = PFF_ERR_CUDA;
   }
-  // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
-  LevelData& C = c->lv[c->nlev - 1];
-  const int nn = (int)C.nn, nu = c->dim * nn;
-  CK(launch_coarse_assemble(c->dim, c->p, c->prm.split, C.qp64, C.flags, C.g, C.t64, c->Au, c->Ap, c->Bc, c->s));
-  CK(launch_gj_inverse(c->Au, nu, c->gjbuf, c->s));
-  CK(launch_gj_inverse(c->Ap, nn, c->gjbuf, c->s));
+  c->s = main_s;
+  CR(st);
+  for (int l = 0; l < c->nlev; ++l) CK(cudaStreamWaitEvent(c->s, c->lv[l].join, 0));
   return PFF_OK;
 }
 
@@ -590,7 +622,8 @@ int vcycle_level(pff_ctx* c, int l, const Real* r, Real* e) {
   CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
   CK(cudaMemcpyAsync(res, r, sizeof(Real) * L.nd, cudaMemcpyDeviceToDevice, c->s));
   CK(launch_axpby<Real>(L.nd, -1.0, t, 1.0, res, c->s));
-  CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s));
+  // res is zero on masked fine rows (r is, and G has identity rows there with e = 0): no Z_f needed
+  CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s, false));
   CR(vcycle_level<Real>(c, l + 1, wc[0], wc[1]));
   CK(launch_prolong<Real>(c->dim, c->p, wc[1], e, L.flags, Lc.g, L.g, c->xt, true, c->s));
   CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
@@ -838,6 +871,11 @@ void pff_destroy(pff_ctx* c) {
       if (g) cudaGraphExecDestroy(g);
   for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->fork) cudaEventDestroy(c->fork);
+  for (auto& L : c->lv) {
+    if (L.aux) cudaStreamDestroy(L.aux);
+    if (L.join) cudaEventDestroy(L.join);
+  }
   for (void* q : c->allocs) cudaFree(q);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
@@ -846,6 +884,7 @@ void pff_destroy(pff_ctx* c) {
 static int setup_impl(pff_ctx* c) {
   const pff_params& P = c->prm;
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
   c->dim = P.dim;
   c->p = P.degree;
   std::vector<int> sizes{P.n_cells_1d};
@@ -882,6 +921,11 @@ static int setup_impl(pff_ctx* c) {
     CR(dalloc(c, &L.di64, L.nd));
     CR(dalloc(c, &L.di32, L.nd));
     CR(dalloc(c, &L.lam, 4));
+    CR(dalloc(c, &L.lscal, 16));
+    CR(dalloc(c, &L.lhist, 4 * P.eig_iters));
+    CR(dalloc(c, &L.lpart, 2 * 152 * 2));
+    CK(cudaStreamCreateWithFlags(&L.aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
     std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N);
     CK(cudaMemcpyAsync(L.flags, fl.data(), fl.size(), cudaMemcpyHostToDevice, c->s));
     CK(cudaStreamSynchronize(c->s));
@@ -909,7 +953,7 @@ static int setup_impl(pff_ctx* c) {
   CR(dalloc(c, &c->Au, nuc * nuc));
   CR(dalloc(c, &c->Ap, nnc * nnc));
   CR(dalloc(c, &c->Bc, nnc * nuc));
-  CR(dalloc(c, &c->gjbuf, 4 * nuc));
+  CR(dalloc(c, &c->gjbuf, 4 * nuc + 4 * nnc));
   CR(dalloc(c, &c->cr, C.nd));
   CR(dalloc(c, &c->ce, C.nd));
   CR(dalloc(c, &c->ct, C.nd));
@@ -1129,7 +1173,11 @@ int pff_coarse_solve(pff_ctx* c, const double* r, double* z) {
 int pff_vcycle(pff_ctx* c, const double* r, double* z) {
   if (!c || !r || !z || r == z) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
-  return precondition(c, r, z);
+  CR(mg_setup(c));
+  // the cycle assumes a residual that is zero on masked rows (Dirichlet DoFs, active set)
+  double* rm = c->scratch;
+  CK(launch_masked_copy(c->dim, c->lv[0].nn, 1.0, r, c->lv[0].flags, 0xffu, rm, c->s));
+  return precondition(c, rm, z);
 }
 
 int pff_solve_linear(pff_ctx* c, const double* b, double* x, int* iters, double* rel) {

@@ -635,7 +635,7 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
 
 template <int DIM, int P, typename Real>
 __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
-                           const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt) {
+                           const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine) {
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gc.nn) return;
   constexpr int MAXL = 2 * (2 * P + 1);
@@ -669,14 +669,15 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
         for (int b = 0; b < cnt[1]; ++b)
           for (int a = 0; a < cnt[0]; ++a) {
             const long long fn = fi[0][a] + (long long)gf.n1 * fi[1][b];
-            if (!((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * (double)xf[f * gf.nn + fn];
+            if (!mask_fine || !((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * (double)xf[f * gf.nn + fn];
           }
       } else {
         for (int c = 0; c < cnt[2]; ++c)
           for (int b = 0; b < cnt[1]; ++b)
             for (int a = 0; a < cnt[0]; ++a) {
               const long long fn = fi[0][a] + (long long)gf.n1 * (fi[1][b] + (long long)gf.n1 * fi[2][c]);
-              if (!((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * fw[2][c] * (double)xf[f * gf.nn + fn];
+              if (!mask_fine || !((flf[fn] >> f) & 1u))
+                v += fw[0][a] * fw[1][b] * fw[2][c] * (double)xf[f * gf.nn + fn];
             }
       }
     }
@@ -702,11 +703,11 @@ cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsig
 template <typename Real>
 cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
                             const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool mask_fine) {
   const unsigned gr = grid_for(gc.nn, 128);
 #define PFF_CASE(DD, PP)                                                                  \
   if (dim == DD && p == PP) {                                                             \
-    count_launch(); k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt);  \
+    count_launch(); k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt, mask_fine ? 1 : 0); \
     return cudaGetLastError();                                                            \
   }
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
@@ -721,10 +722,10 @@ template cudaError_t launch_prolong<float>(int, int, const float*, float*, const
                                            const Geom&, const XferTab&, bool, cudaStream_t);
 template cudaError_t launch_restrict<double>(int, int, const double*, double*, const unsigned char*,
                                              const unsigned char*, const Geom&, const Geom&, const XferTab&,
-                                             cudaStream_t);
+                                             cudaStream_t, bool);
 template cudaError_t launch_restrict<float>(int, int, const float*, float*, const unsigned char*,
                                             const unsigned char*, const Geom&, const Geom&, const XferTab&,
-                                            cudaStream_t);
+                                            cudaStream_t, bool);
 
 // Fine FE function evaluated at the coarse nodes (carries the state to coarse levels).
 __global__ void k_state_interp(int dim, int p, const double* __restrict__ xf, double* __restrict__ yc, int nfields,
@@ -1196,11 +1197,11 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
     lo = fmin(lo, a[j] - r);
     hi = fmax(hi, a[j] + r);
   }
-  // which = 0: largest eigenvalue (first x with count(x) >= k); which = 1: smallest (count >= 1)
-  for (int which = 0; which < 2; ++which) {
-    const int target = which == 0 ? k : 1;
+  // largest eigenvalue: the first point x with count(x) >= k (the smallest is not needed)
+  for (int which = 0; which < 1; ++which) {
+    const int target = k;
     double l = lo, h = hi;
-    for (int round = 0; round < 16 && h - l > 1e-15 * fmax(fabs(l), fabs(h)); ++round) {
+    for (int round = 0; round < 12 && h - l > 1e-15 * fmax(fabs(l), fabs(h)); ++round) {
       const double x = l + (h - l) * (lane + 1) / 33.0;
       const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(k, a, b2, x) >= target);
       const int j = ge ? __ffs(ge) - 1 : 32;  // first lane whose point is at or above the eigenvalue
@@ -1209,7 +1210,10 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
       l = nl;
       h = nh;
     }
-    if (lane == 0) lam[(which == 0 ? 0 : 2) + b] = which == 0 ? h : l;
+    if (lane == 0) {
+      lam[b] = h;
+      lam[2 + b] = lo;  // Gershgorin lower bound
+    }
   }
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,

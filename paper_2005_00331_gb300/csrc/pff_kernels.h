@@ -41,10 +41,12 @@ struct XferTab {
 template <typename Real>
 cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f,
                            const Geom& gc, const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s);
+// mask_fine = false skips Z_f (valid when x is already zero on masked fine rows, as the V-cycle's
+// residuals are).
 template <typename Real>
 cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
                             const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
-                            cudaStream_t s);
+                            cudaStream_t s, bool mask_fine = true);
 // Evaluates `nfields` fine nodal fields (each nn_f long, consecutive) at the coarse nodes.
 cudaError_t launch_state_interp(int dim, int p, const double* xf, double* yc, int nfields, const Geom& gf,
                                 const Geom& gc, const XferTab& xt, cudaStream_t s);
