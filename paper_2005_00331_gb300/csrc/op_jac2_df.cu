@@ -7,7 +7,8 @@ namespace pff {
 
 template <int P, int SPLIT>
 static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* flags, const Geom& g, const Tab<df64>& tb,
-                             const df64* qp, int mode, int inmask, int outmask, cudaStream_t s) {
+                             const df64* qp, int mode, int inmask, int outmask, cudaStream_t s,
+                             const ChebEpi<double>& ce) {
   constexpr size_t smem = jac2_staged_smem<P, df64, double, SPLIT>();
   static int grid_per_sm = 0;
   auto kern = k_jac2_staged<P, df64, double, SPLIT>;
@@ -28,16 +29,19 @@ static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* 
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa); }
+  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa, ce); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s) {
+                          cudaStream_t s, const ChebEpi<double>* ce) {
+  ChebEpi<double> off{};
+  off.on = 0;
+  const ChebEpi<double>& e = ce ? *ce : off;
   if (dim != 2) return cudaErrorInvalidValue;
 #define PFF_CASE(PP, SS) \
-  if (p == PP && split == SS) return run_jac2_df<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s);
+  if (p == PP && split == SS) return run_jac2_df<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e);
   PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
   PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
 #undef PFF_CASE

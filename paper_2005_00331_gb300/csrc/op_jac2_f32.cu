@@ -6,7 +6,8 @@ namespace pff {
 
 template <int P, int SPLIT>
 static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
-                             const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
+                             const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
+                             const ChebEpi<float>& ce) {
   constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT>();
   static int grid_per_sm = 0;
   auto kern = k_jac2_staged<P, float, float, SPLIT>;
@@ -27,19 +28,32 @@ static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa); }
+  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa, ce); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags, const Geom& g,
-                       const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask, cudaStream_t s) {
+                       const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
+                       const ChebEpi<float>* ce) {
+  ChebEpi<float> off{};
+  off.on = 0;
+  const ChebEpi<float>& e = ce ? *ce : off;
   if (dim != 2) return cudaErrorInvalidValue;
 #define PFF_CASE(PP, SS) \
-  if (p == PP && split == SS) return run_jac2<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s);
+  if (p == PP && split == SS) return run_jac2<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e);
   PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
   PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
 #undef PFF_CASE
   return cudaErrorInvalidValue;
+}
+
+template <>
+cudaError_t launch_cheb_seam<float>(const Geom& g, const float* y, const ChebEpi<float>& ce, cudaStream_t s) {
+  const long long n = (long long)(g.ntile[0] - 1 + g.ntile[1] - 1) * g.n1;
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_cheb_seam2<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, g.tdim[0] * g.p, g.tdim[1] * g.p, y, ce);
+  return cudaGetLastError();
 }
 
 }  // namespace pff

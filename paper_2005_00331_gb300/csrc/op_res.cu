@@ -52,14 +52,14 @@ cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, co
 
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s) {
-  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s)
+                       cudaStream_t s, const ChebEpi<double>* ce) {
+  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce)
                   : launch_jac_d3(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s);
 }
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s) {
-  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s)
+                       cudaStream_t s, const ChebEpi<float>* ce) {
+  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce)
                   : launch_jac_d3(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s);
 }
 

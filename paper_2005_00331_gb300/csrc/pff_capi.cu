@@ -372,20 +372,27 @@ bool prof_jac(pff_ctx* c, int l) {
          (l == 0 && prof_on(c, d ? PFF_PROF_JAC64_L0 : PFF_PROF_JAC32_L0));
 }
 
-// y = G x on level l (y zeroed first).
+// y = G x on level l (y zeroed first). With ce (2D), a fused Chebyshev step: see launch_jac; such
+// launches are not timed by pff_profile (they move more than the apply's bytes).
 template <typename Real>
-int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask, int outmask) {
+int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask, int outmask,
+                const ChebEpi<Real>* ce = nullptr) {
   LevelData& L = c->lv[l];
   CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
-  const bool timed = prof_jac<Real>(c, l);
+  const bool timed = !ce && prof_jac<Real>(c, l);
   if (timed) CR(prof_mark(c));
-  if (sizeof(Real) == 8 && c->prm.fp64_mode == 1)
-    CK((c->dim == 2 ? launch_jac_df : launch_jac_df3)(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x),
-                                                      reinterpret_cast<double*>(y), L.flags, L.g, L.tdf, L.qpdf, mode,
-                                                      inmask, outmask, c->s));
-  else
+  if (sizeof(Real) == 8 && c->prm.fp64_mode == 1) {
+    if (c->dim == 2)
+      CK(launch_jac_df(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
+                       L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s,
+                       reinterpret_cast<const ChebEpi<double>*>(ce)));
+    else
+      CK(launch_jac_df3(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
+                        L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s));
+  } else {
     CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
-                  outmask, c->s));
+                  outmask, c->s, ce));
+  }
   if (timed) CR(prof_mark(c));
   return PFF_OK;
 }
@@ -599,9 +606,26 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
   double rho = 1.0 / sigma;
   CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, L.lam, lo, hi, 0.0, 0.0, c->s));
   for (int k = 1; k < c->prm.cheb_degree; ++k) {
-    CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, L.lam, lo, hi, rho_new * rho, rho_new, c->s));
+    if (c->dim == 2) {
+      // the apply finishes the step on single-tile nodes; the seam nodes follow
+      ChebEpi<Real> ce;
+      ce.f = f;
+      ce.dinv = dinv_of<Real>(L);
+      ce.d = dv;
+      ce.x = x;
+      ce.lam_max = L.lam;
+      ce.lo = lo;
+      ce.hi = hi;
+      ce.c1 = rho_new * rho;
+      ce.rho_k = rho_new;
+      ce.on = 1;
+      CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce));
+      CK(launch_cheb_seam<Real>(L.g, t, ce, c->s));
+    } else {
+      CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
+      CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, L.lam, lo, hi, rho_new * rho, rho_new, c->s));
+    }
     rho = rho_new;
   }
   return PFF_OK;

@@ -61,6 +61,21 @@ struct Geom {
   long long ntiles;
 };
 
+// Chebyshev-Jacobi step fused into the block-diagonal apply (Sec. 3.3 smoother): for a node that
+// only this tile touches, y = (G x)_i is final in registers, so the update
+//   d_i <- c1 d_i + (2 rho_k / delta_b) dinv_i (f_i - y_i),   x_i <- x_i + d_i
+// is done in place and y_i is never stored; seam nodes go through y and k_cheb_seam afterwards.
+template <typename Store>
+struct ChebEpi {
+  const Store* f;
+  const Store* dinv;
+  Store* d;
+  Store* x;
+  const double* lam_max;  // [2]: u block, phi block
+  double lo, hi, c1, rho_k;
+  int on;
+};
+
 // ---------------------------------------------------------------------------------------------
 // Mandel representation: a symmetric d x d tensor as an orthonormal vector of NM components,
 // 2D (11, 22, 12), 3D (11, 22, 33, 23, 13, 12), shear components scaled by sqrt(2).

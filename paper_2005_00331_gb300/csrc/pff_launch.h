@@ -13,18 +13,23 @@ long long launch_count();
 
 // y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be
 // zeroed by the caller (seam nodes are accumulated atomically). mode: JM_*; masks: In/OutMask.
+// With ce != nullptr (2D only) the block-diagonal apply finishes a Chebyshev step on the nodes of a
+// single tile (x and d updated in place) and accumulates only seam nodes into y; launch_cheb_seam
+// then completes the step on the seam nodes.
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask,
-                       int outmask, cudaStream_t s);
+                       int outmask, cudaStream_t s, const ChebEpi<double>* ce = nullptr);
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s);
+                       cudaStream_t s, const ChebEpi<float>* ce = nullptr);
+template <typename Store>
+cudaError_t launch_cheb_seam(const Geom& g, const Store* y, const ChebEpi<Store>& ce, cudaStream_t s);
 cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s);
+                          cudaStream_t s, const ChebEpi<double>* ce);
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                           const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s);
+                          cudaStream_t s, const ChebEpi<float>* ce);
 cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
                           cudaStream_t s);
@@ -34,7 +39,7 @@ cudaError_t launch_jac_d3(int dim, int p, int split, const float* x, float* y, c
 // The same Jacobian in double-word arithmetic (FP64 vectors, per-point data as df64 pairs); 2D.
 cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s);
+                          cudaStream_t s, const ChebEpi<double>* ce = nullptr);
 cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                            const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
                            cudaStream_t s);

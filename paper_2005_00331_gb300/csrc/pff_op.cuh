@@ -430,8 +430,8 @@ struct Stage2 {
 
 template <int P, typename Real, typename Store, int SPLIT>
 __global__ void __launch_bounds__(Tile2<P>::NT)
-k_jac2_staged(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
-              Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa) {
+k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
+              Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce) {
   using T = Tile2<P>;
   constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
   constexpr int NPX = T::NPX, NPY = T::NPY, QPX = T::QPX;
@@ -454,6 +454,17 @@ k_jac2_staged(const Store* __restrict__ src, Store* __restrict__ dst, const unsi
   if (tid < n * n) {
     sS[tid] = tb.S[tid / n][tid % n];
     sD[tid] = tb.D[tid / n][tid % n];
+  }
+  // Chebyshev coefficients per block (field < 2: u block)
+  double ch_c1 = 0.0, ch_c2[2] = {0.0, 0.0};
+  if (ce.on) {
+    for (int b = 0; b < 2; ++b) {
+      const double lm = ce.lam_max[b];
+      const double a = ce.lo * lm, bb = ce.hi * lm;
+      const bool ok = lm > 0.0 && lm < 1e300;
+      ch_c2[b] = ok ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0;
+    }
+    ch_c1 = ce.c1;
   }
   const long long ntiles = g.ntiles;
   auto prefetch = [&](long long tile, int st) {
@@ -636,7 +647,15 @@ k_jac2_staged(const Store* __restrict__ src, Store* __restrict__ dst, const unsi
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const long long gi = f * g.nn + node;
-        if ((m >> f) & 1u) {
+        const bool masked = (m >> f) & 1u;
+        if (ce.on && !low && !high) {
+          // node of this tile only: finish the smoothing step here
+          const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
+          const double c2 = ch_c2[f < 2 ? 0 : 1];
+          const Store dn = Store(ch_c1 * (double)ce.d[gi] + c2 * (double)ce.dinv[gi] * ((double)ce.f[gi] - (double)y));
+          ce.d[gi] = dn;
+          ce.x[gi] = ce.x[gi] + dn;
+        } else if (masked) {
           if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
         } else if (low || high) {
           atomicAdd(dst + gi, cvt<Store>(acc[f]));
@@ -647,6 +666,37 @@ k_jac2_staged(const Store* __restrict__ src, Store* __restrict__ dst, const unsi
     }
   }
   cp_async_wait<0>();
+}
+
+// The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete.
+template <typename Store>
+__global__ void k_cheb_seam2(Geom g, int tpx, int tpy, const Store* __restrict__ y, ChebEpi<Store> ce) {
+  const long long nv = (long long)(g.ntile[0] - 1) * g.n1, nh = (long long)(g.ntile[1] - 1) * g.n1;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nv + nh) return;
+  int gx, gy;
+  if (t < nv) {
+    gx = int(t / g.n1 + 1) * tpx;
+    gy = int(t % g.n1);
+  } else {
+    const long long u = t - nv;
+    gy = int(u / g.n1 + 1) * tpy;
+    gx = int(u % g.n1);
+    if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
+  }
+  const long long node = gx + (long long)g.n1 * gy;
+  double c2[2];
+  for (int b = 0; b < 2; ++b) {
+    const double lm = ce.lam_max[b];
+    const double a = ce.lo * lm, bb = ce.hi * lm;
+    c2[b] = (lm > 0.0 && lm < 1e300) ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0;
+  }
+  for (int f = 0; f < 3; ++f) {
+    const long long gi = f * g.nn + node;
+    const Store dn = Store(ce.c1 * (double)ce.d[gi] + c2[f < 2 ? 0 : 1] * (double)ce.dinv[gi] * ((double)ce.f[gi] - (double)y[gi]));
+    ce.d[gi] = dn;
+    ce.x[gi] = ce.x[gi] + dn;
+  }
 }
 
 template <int P, typename Real, typename Store, int SPLIT>
