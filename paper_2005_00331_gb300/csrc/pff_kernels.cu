@@ -602,34 +602,34 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
   }
   const unsigned char fl = flf[nd];
   for (int f = 0; f <= DIM; ++f) {
-    double v = 0.0;
+    Real v = Real(0);
     if (!((fl >> f) & 1u)) {
       if constexpr (DIM == 2) {
         for (int ky = 0; ky <= P; ++ky) {
-          const double wy = xt.E[o[1]][ky];
-          if (wy == 0.0) continue;
+          const Real wy = Real(xt.E[o[1]][ky]);
+          if (wy == Real(0)) continue;
           const Real* row = xc + f * gc.nn + (long long)(C[1] * P + ky) * gc.n1 + C[0] * P;
-          double sx = 0.0;
-          for (int kx = 0; kx <= P; ++kx) sx += xt.E[o[0]][kx] * (double)row[kx];
+          Real sx = Real(0);
+          for (int kx = 0; kx <= P; ++kx) sx += Real(xt.E[o[0]][kx]) * row[kx];
           v += wy * sx;
         }
       } else {
         for (int kz = 0; kz <= P; ++kz) {
-          const double wz = xt.E[o[2]][kz];
-          if (wz == 0.0) continue;
+          const Real wz = Real(xt.E[o[2]][kz]);
+          if (wz == Real(0)) continue;
           for (int ky = 0; ky <= P; ++ky) {
-            const double wy = xt.E[o[1]][ky];
-            if (wy == 0.0) continue;
+            const Real wy = Real(xt.E[o[1]][ky]);
+            if (wy == Real(0)) continue;
             const Real* row = xc + f * gc.nn + ((long long)(C[2] * P + kz) * gc.n1 + (C[1] * P + ky)) * gc.n1 + C[0] * P;
-            double sx = 0.0;
-            for (int kx = 0; kx <= P; ++kx) sx += xt.E[o[0]][kx] * (double)row[kx];
+            Real sx = Real(0);
+            for (int kx = 0; kx <= P; ++kx) sx += Real(xt.E[o[0]][kx]) * row[kx];
             v += wz * wy * sx;
           }
         }
       }
     }
     Real* y = yf + f * gf.nn + nd;
-    *y = accumulate ? Real((double)*y + v) : Real(v);
+    *y = accumulate ? *y + v : v;
   }
 }
 
@@ -640,7 +640,7 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
   if (nd >= gc.nn) return;
   constexpr int MAXL = 2 * (2 * P + 1);
   int fi[3][MAXL];
-  double fw[3][MAXL];
+  Real fw[3][MAXL];
   int cnt[3] = {0, 0, 0};
   long long rem = nd;
   for (int t = 0; t < DIM; ++t) {
@@ -656,20 +656,20 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
         const double w = xt.E[o][k];
         if (w == 0.0) continue;
         fi[t][cnt[t]] = 2 * P * c + o;
-        fw[t][cnt[t]] = w;
+        fw[t][cnt[t]] = Real(w);
         ++cnt[t];
       }
     }
   }
   const unsigned char fc = flc[nd];
   for (int f = 0; f <= DIM; ++f) {
-    double v = 0.0;
+    Real v = Real(0);
     if (!((fc >> f) & 1u)) {
       if constexpr (DIM == 2) {
         for (int b = 0; b < cnt[1]; ++b)
           for (int a = 0; a < cnt[0]; ++a) {
             const long long fn = fi[0][a] + (long long)gf.n1 * fi[1][b];
-            if (!mask_fine || !((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * (double)xf[f * gf.nn + fn];
+            if (!mask_fine || !((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * xf[f * gf.nn + fn];
           }
       } else {
         for (int c = 0; c < cnt[2]; ++c)
@@ -677,11 +677,11 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
             for (int a = 0; a < cnt[0]; ++a) {
               const long long fn = fi[0][a] + (long long)gf.n1 * (fi[1][b] + (long long)gf.n1 * fi[2][c]);
               if (!mask_fine || !((flf[fn] >> f) & 1u))
-                v += fw[0][a] * fw[1][b] * fw[2][c] * (double)xf[f * gf.nn + fn];
+                v += fw[0][a] * fw[1][b] * fw[2][c] * xf[f * gf.nn + fn];
             }
       }
     }
-    yc[f * gc.nn + nd] = Real(v);
+    yc[f * gc.nn + nd] = v;
   }
 }
 

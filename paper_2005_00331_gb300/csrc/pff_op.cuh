@@ -455,16 +455,16 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
     sS[tid] = tb.S[tid / n][tid % n];
     sD[tid] = tb.D[tid / n][tid % n];
   }
-  // Chebyshev coefficients per block (field < 2: u block)
-  double ch_c1 = 0.0, ch_c2[2] = {0.0, 0.0};
+  // Chebyshev coefficients per block (field < 2: u block), in the storage precision
+  Store ch_c1 = Store(0), ch_c2[2] = {Store(0), Store(0)};
   if (ce.on) {
     for (int b = 0; b < 2; ++b) {
       const double lm = ce.lam_max[b];
       const double a = ce.lo * lm, bb = ce.hi * lm;
       const bool ok = lm > 0.0 && lm < 1e300;
-      ch_c2[b] = ok ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0;
+      ch_c2[b] = Store(ok ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0);
     }
-    ch_c1 = ce.c1;
+    ch_c1 = Store(ce.c1);
   }
   const long long ntiles = g.ntiles;
   auto prefetch = [&](long long tile, int st) {
@@ -651,8 +651,7 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         if (ce.on && !low && !high) {
           // node of this tile only: finish the smoothing step here
           const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
-          const double c2 = ch_c2[f < 2 ? 0 : 1];
-          const Store dn = Store(ch_c1 * (double)ce.d[gi] + c2 * (double)ce.dinv[gi] * ((double)ce.f[gi] - (double)y));
+          const Store dn = ch_c1 * ce.d[gi] + ch_c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y));
           ce.d[gi] = dn;
           ce.x[gi] = ce.x[gi] + dn;
         } else if (masked) {
@@ -685,15 +684,16 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, const Store* __restrict__
     if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
   }
   const long long node = gx + (long long)g.n1 * gy;
-  double c2[2];
+  Store c2[2];
   for (int b = 0; b < 2; ++b) {
     const double lm = ce.lam_max[b];
     const double a = ce.lo * lm, bb = ce.hi * lm;
-    c2[b] = (lm > 0.0 && lm < 1e300) ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0;
+    c2[b] = Store((lm > 0.0 && lm < 1e300) ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0);
   }
+  const Store c1 = Store(ce.c1);
   for (int f = 0; f < 3; ++f) {
     const long long gi = f * g.nn + node;
-    const Store dn = Store(ce.c1 * (double)ce.d[gi] + c2[f < 2 ? 0 : 1] * (double)ce.dinv[gi] * ((double)ce.f[gi] - (double)y[gi]));
+    const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y[gi]));
     ce.d[gi] = dn;
     ce.x[gi] = ce.x[gi] + dn;
   }
