@@ -48,13 +48,15 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", choices=["newton", "apply", "pdas"], default="newton",
+    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps"], default="newton",
                     help="apply: time only the finest-level Jacobian apply (--precision) on the workload; "
                          "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid")
     ap.add_argument("--state", choices=["random", "tension"], default="random",
                     help="random: seeded u, phi (the apply-sweep workload); tension: u = 0 with the top load "
                          "lifted, phi = 1 except 0 on the slit (a load step from rest)")
     ap.add_argument("--newton-rtol", type=float, default=1e-8)
+    ap.add_argument("--load-steps", type=int, default=10, help="--mode loadsteps: number of load steps")
+    ap.add_argument("--load-inc", type=float, default=1e-4, help="--mode loadsteps: top displacement increment")
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
     ap.add_argument("--fp64-mode", type=int, default=1,
                     help="FP64 Jacobian applies: 0 native FP64, 1 double-word arithmetic on the FP32 pipe (2D)")
@@ -416,6 +418,51 @@ def run_pdas(a):
     return out
 
 
+def run_loadsteps(a):
+    """Quasi-static loading from rest: --load-steps steps of --load-inc on the top face, each a full
+    active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = argparse.Namespace(**vars(a))
+    b.state = "tension"
+    out = {"mode": "loadsteps", "workload": workload_name(a), "load_steps": a.load_steps, "load_inc": a.load_inc,
+           "newton_rtol": a.newton_rtol}
+    finals = {}
+    for prec in (32, 64):
+        ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+        U_h, po_h = make_state(ctx, b, seed=0)
+        U = torch.from_numpy(U_h).to(dev)
+        po = torch.from_numpy(po_h).to(dev)
+        U[(a.dim - 1) * ctx.n_nodes:a.dim * ctx.n_nodes] = 0.0  # start from rest: no load yet
+        # warm-up: one load step (graph capture, kernel attributes), then restart from rest
+        ctx.set_state(U, po, po, None)
+        ctx.solve_load_step(a.load_inc, check=False)
+        ctx.set_state(U, po, po, None)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        steps, newton, iters, status = [], 0, 0, 0
+        for k in range(1, a.load_steps + 1):
+            t0 = time.perf_counter()
+            st, reps = ctx.solve_load_step(k * a.load_inc, check=False)
+            steps.append({"load": k * a.load_inc, "status": st, "newton_steps": len(reps),
+                          "gmres_iters": [r["gmres_iters"] for r in reps], "seconds": time.perf_counter() - t0,
+                          "n_active": reps[-1]["n_active"] if reps else None})
+            newton += len(reps)
+            status = status or st
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        finals[prec] = ctx.get_state()
+        out["mg_fp%d" % prec] = {"status": status, "seconds": dt, "newton_steps": newton,
+                                 "s_per_newton_step": dt / max(1, newton), "steps": steps}
+        out["n_dofs"] = ctx.n_dofs
+        ctx.close()
+    out["rel_diff_mixed_vs_fp64"] = float((finals[32] - finals[64]).norm() / max(float(finals[64].norm()), 1e-300))
+    return out
+
+
 # ---- CPU oracle baseline ----------------------------------------------------------------------
 CPU_SAMPLE_CELLS = 32
 
@@ -495,6 +542,10 @@ def main():
     if a.mode == "pdas":
         torch.cuda.set_device(local if world > 1 else 0)
         print(json.dumps(run_pdas(a)))
+        return
+    if a.mode == "loadsteps":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_loadsteps(a)))
         return
     if world > 1:
         torch.cuda.set_device(local)

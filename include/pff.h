@@ -195,6 +195,15 @@ int pff_solve_newton_step(pff_ctx* ctx, double* U_out, pff_report* rep);
  * The final state is the context's state (and is copied to U_out when non-NULL). Synchronous. */
 int pff_solve_pdas(pff_ctx* ctx, int max_iters, double newton_rtol, double* U_out, pff_report* reps, int* n_steps);
 
+/* One quasi-static load step of the tension test (Sec. 5.1) from the current state: the displacement
+ * component u_dim on the top face is set to `load` (all other Dirichlet values kept), phi_old becomes
+ * the phase field of the previous load step and phi~ its linear extrapolation from the last two
+ * steps, clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2; phi^{n-1} while only one is known); then
+ * pff_solve_pdas. The phase-field history starts from the state of the last pff_set_state and
+ * advances only when the step converges. Same outputs and errors as pff_solve_pdas. */
+int pff_solve_load_step(pff_ctx* ctx, double load, int max_iters, double newton_rtol, pff_report* reps,
+                        int* n_steps);
+
 /* Parameter gradients of the residual (not in the paper; needed for adjoints): for a test vector v
  * (DoF layout), g_gc = (dR/dG_c)^T v, g_lambda = (dR/dlambda)^T v, g_mu = (dR/dmu)^T v with the
  * material parameters as nodal fields, one value per node each, at the current state. Entries of v

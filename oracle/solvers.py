@@ -342,3 +342,28 @@ def pdas_step(mesh, prm, U, phi_old, phi_tilde, c=1.0, solve="direct", levels_kw
         dU, its, rel = fgmres(lambda v: G @ v, rhs, lambda v: vcycle(levels, v), tol=1e-6)
         info.update(gmres_iters=its, gmres_rel=rel)
     return U + dU, act, float(np.linalg.norm(rhs)), info
+
+
+def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, **fields):
+    """Quasi-static loading of the tension test (Sec. 5.1): for each load, u_d := load on the top face,
+    phi_old := the previous step's phase field, phi~ := clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2:
+    linear extrapolation from the last two steps, dt = 1; phi^{n-1} for the first step), then Alg. 1
+    repeated until the active set is unchanged and ||R~|| <= rtol ||R~_0||. Returns the states."""
+    d, nn = mesh.dim, mesh.n_nodes
+    U = U.copy()
+    h1, h2 = U[d * nn:].copy(), None
+    out = []
+    for load in loads:
+        U[mesh.dof(d - 1, mesh.top_nodes())] = load
+        phi_old = h1.copy()
+        phit = h1.copy() if h2 is None else np.clip(2.0 * h1 - h2, 0.0, 1.0)
+        norms, prev = [], None
+        for _ in range(max_iters):
+            U, act, rn, _ = pdas_step(mesh, prm, U, phi_old, phit, **fields)
+            norms.append(rn)
+            if prev is not None and np.array_equal(prev, act) and rn <= rtol * norms[0]:
+                break
+            prev = act
+        h2, h1 = h1, U[d * nn:].copy()
+        out.append(U.copy())
+    return out

@@ -125,6 +125,9 @@ struct pff_ctx {
   XferTab xt{};
   bool has_state = false, qp_valid = false, mg_ready = false, has_fields = false;
   double* phi_old = nullptr;
+  double* hist1 = nullptr;  // phase field of the previous load step
+  double* hist2 = nullptr;  // ... and of the one before
+  int nhist = 0;
   double* mass = nullptr;
   double* R = nullptr;
   double* rhs = nullptr;
@@ -956,6 +959,8 @@ static int setup_impl(pff_ctx* c) {
   }
   LevelData& F = c->lv[0];
   CR(dalloc(c, &c->phi_old, F.nn));
+  CR(dalloc(c, &c->hist1, F.nn));
+  CR(dalloc(c, &c->hist2, F.nn));
   CR(dalloc(c, &c->mass, F.nn));
   CR(dalloc(c, &c->R, F.nd));
   CR(dalloc(c, &c->rhs, F.nd));
@@ -1068,6 +1073,7 @@ int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const doub
   c->has_state = true;
   c->qp_valid = false;
   c->mg_ready = false;
+  c->nhist = 0;
   if (active) {
     CK(launch_set_active(c->dim, L.nn, active, L.flags, c->s));
   } else {
@@ -1280,6 +1286,30 @@ int pff_solve_pdas(pff_ctx* c, int max_iters, double newton_rtol, double* U_out,
   if (n_steps) *n_steps = k;
   if (U_out) CK(cudaMemcpyAsync(U_out, c->lv[0].U, sizeof(double) * c->lv[0].nd, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
+  return st;
+}
+
+int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rtol, pff_report* reps,
+                        int* n_steps) {
+  if (!c || max_iters < 1 || !(newton_rtol > 0)) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  LevelData& L = c->lv[0];
+  const long long nn = L.nn;
+  if (c->nhist == 0) {
+    CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+    c->nhist = 1;
+  }
+  CK(launch_load_step_prep(c->dim, nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr, L.phit,
+                           c->phi_old, c->s));
+  c->qp_valid = false;
+  c->mg_ready = false;
+  const int st = pff_solve_pdas(c, max_iters, newton_rtol, nullptr, reps, n_steps);
+  if (st == PFF_OK) {
+    std::swap(c->hist1, c->hist2);
+    CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+    c->nhist = 2;
+    CK(cudaStreamSynchronize(c->s));
+  }
   return st;
 }
 

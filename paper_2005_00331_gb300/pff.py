@@ -72,6 +72,7 @@ _SIGS = {
     "pff_solve_linear": (_I, [_P, _P, _P, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "pff_solve_newton_step": (_I, [_P, _P, ctypes.POINTER(Report)]),
     "pff_solve_pdas": (_I, [_P, _I, _D, _P, ctypes.POINTER(Report), ctypes.POINTER(_I)]),
+    "pff_solve_load_step": (_I, [_P, _D, _I, _D, ctypes.POINTER(Report), ctypes.POINTER(_I)]),
     "pff_param_grad": (_I, [_P, _P, _P, _P, _P]),
     "pff_param_grad_noalloc": (_I, [_P, _P, _P, _P, _P]),
     "pff_strerror": (ctypes.c_char_p, [_I]),
@@ -300,6 +301,15 @@ class Context:
                                       ctypes.byref(n))
         if check:
             _check(st, "pff_solve_pdas")
+        return st, [reps[i].as_dict() for i in range(n.value)]
+
+    def solve_load_step(self, load, max_iters=30, newton_rtol=1e-8, check=True):
+        """One quasi-static load step (top displacement `load`, phi~ extrapolated, Alg. 1 to tolerance)."""
+        reps = (Report * max_iters)()
+        n = _I()
+        st = self._lib.pff_solve_load_step(self._h, load, max_iters, newton_rtol, reps, ctypes.byref(n))
+        if check:
+            _check(st, "pff_solve_load_step")
         return st, [reps[i].as_dict() for i in range(n.value)]
 
     def param_grad(self, v):

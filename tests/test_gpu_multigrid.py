@@ -176,3 +176,24 @@ def test_param_grad_and_adjoint(dim, p, N, split):
     from paper_2005_00331_gb300 import PFF_MASK_ADJOINT, PFF_MODE_TRANSPOSE
     gU = ctx.apply_jacobian(cuda(v), mode=PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT).cpu().numpy()
     assert rel(gU, pr.G().T @ vm) <= 1e-12
+
+
+def test_load_steps_against_oracle():
+    """Three quasi-static load steps with the extrapolated phase field: GPU (FGMRES + mixed GMG) against
+    the oracle (direct solves), 2D Q1 16 x 16, Miehe split."""
+    from oracle import mesh as M
+    from paper_2005_00331_gb300 import setup_mesh
+    m = M.Mesh(2, 1, 16)
+    prm = fe.Params(121.15, 80.77, 2.7e-3, 2.0 / 16, 1e-10, 1)
+    U = m.dirichlet_values(0.0)
+    phi = np.ones(m.n_nodes)
+    phi[m.slit_nodes()] = 0.0
+    U[2 * m.n_nodes:] = phi
+    loads = [4e-3, 8e-3, 1.2e-2]
+    ref = S.load_steps(m, prm, U, loads)
+    ctx = setup_mesh(dim=2, degree=1, n_cells_1d=16, split=1, eps=2.0 / 16, mg_precision=32, lin_rtol=1e-10)
+    ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
+    for k, load in enumerate(loads):
+        st, reps = ctx.solve_load_step(load)
+        Ug = ctx.get_state().cpu().numpy()
+        assert rel(Ug, ref[k]) <= 1e-6
