@@ -91,17 +91,20 @@ def _chunks(n, size=2048):
 
 
 def residual(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=None,
-             zero_dirichlet=True):
+             zero_dirichlet=True, cells=None):
     """R(U)(w, psi) of Eq. (residual) for every test basis function, as a global vector.
 
     u-rows:   int (g(phi~) sigma^+ + sigma^-) : e(w)
     phi-rows: int g'(phi) E_s^+ psi - (G_c/eps)(1 - phi) psi + G_c eps grad phi . grad psi
-    Rows of Dirichlet DoFs are set to 0 when ``zero_dirichlet``.
+    Rows of Dirichlet DoFs are set to 0 when ``zero_dirichlet``. With ``cells`` only those cells are
+    summed (exact at nodes all of whose cells are listed).
     """
     T = Tables(mesh)
     d, nn = mesh.dim, mesh.n_nodes
     R = np.zeros(mesh.n_dofs)
-    for cells in _chunks(mesh.n_cells):
+    all_cells = np.arange(mesh.n_cells) if cells is None else np.asarray(cells)
+    for s in range(0, len(all_cells), 2048):
+        cells = all_cells[s:s + 2048]
         grad_u, phi, grad_phi, phit = qp_state(mesh, U, phi_tilde, cells, T)
         gc, lam, mu = _fields(mesh, prm, gc_field, lam_field, mu_field, cells, T)
         e = mat.sym(grad_u)
