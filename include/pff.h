@@ -170,8 +170,10 @@ int pff_restrict(pff_ctx* ctx, int level, const void* x_fine, void* y_coarse, in
  * guess: x = S(G_uu, G_phiphi) f (Sec. 3.3). */
 int pff_smooth(pff_ctx* ctx, int level, const void* f, void* x, int precision);
 
-/* Coarse-level solve (FP64): z = G_c^{-1} r by block forward substitution over the block lower
- * triangular coarse matrix (Sec. 3.3), r and z in the coarsest level's layout. */
+/* Coarse-level solve: z = G_c^{-1} r by block forward substitution over the block lower triangular
+ * coarse matrix (Sec. 3.3), r and z FP64 in the coarsest level's layout. The dense inverses of the
+ * diagonal blocks are held in the params' mg_precision: with mg_precision 32 they are computed and
+ * applied in FP32 (r is rounded to FP32 on entry), as inside the FP32 V-cycle. */
 int pff_coarse_solve(pff_ctx* ctx, const double* r, double* z);
 
 /* One V-cycle of GMG(G) (Sec. 3.3) on the finest level: z = M^{-1} r, FP64 in and out; inside it

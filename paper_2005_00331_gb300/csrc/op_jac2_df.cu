@@ -29,8 +29,8 @@ static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* 
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa, ce); }
-  return cudaGetLastError();
+  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce);
+  return cudaSuccess;
 }
 
 cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,

@@ -28,8 +28,8 @@ static cudaError_t run_jac2(const double* x, double* y, const unsigned char* fla
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) { count_launch(); kern<<<(unsigned)grid, blk, smem, s>>>(x, y, flags, g, tb, qp, mode, oa, ce); }
-  return cudaGetLastError();
+  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce);
+  return cudaSuccess;
 }
 
 cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags, const Geom& g,
@@ -48,12 +48,11 @@ cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y,
 }
 
 template <>
-cudaError_t launch_cheb_seam<double>(const Geom& g, const double* y, const ChebEpi<double>& ce, cudaStream_t s) {
+cudaError_t launch_cheb_seam<double>(const Geom& g, double* y, const ChebEpi<double>& ce, cudaStream_t s) {
   const long long n = (long long)(g.ntile[0] - 1 + g.ntile[1] - 1) * g.n1;
   if (n <= 0) return cudaSuccess;
-  count_launch();
-  k_cheb_seam2<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, g.tdim[0] * g.p, g.tdim[1] * g.p, y, ce);
-  return cudaGetLastError();
+  return launch_k(k_cheb_seam2<double>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, g, g.tdim[0] * g.p,
+                  g.tdim[1] * g.p, y, ce);
 }
 
 }  // namespace pff

@@ -22,8 +22,8 @@ static cudaError_t run_jac3(const double* x, double* y, const unsigned char* fla
   pw.mode = mode;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
-  if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(x, y, flags, g, tb, pw, oa); }
-  return cudaGetLastError();
+  if (g.ntiles > 0) return launch_k(kern, dim3((unsigned)g.ntiles), blk, smem, s, x, y, flags, g, tb, pw, oa);
+  return cudaSuccess;
 }
 
 cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags, const Geom& g,

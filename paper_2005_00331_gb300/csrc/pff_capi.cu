@@ -104,6 +104,7 @@ struct LevelData {
   double* st64 = nullptr;
   double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
   double* di64 = nullptr;   // its inverse (Jacobi scaling)
+  float* d32 = nullptr;     // the diagonal computed in FP32 from the FP32 per-point data (FP32 multigrid)
   float* di32 = nullptr;
   double* lam = nullptr;    // device [lmax_u, lmax_phi, lower bounds]
   // per-level reduction scratch, so that the levels' setup branches can run concurrently
@@ -124,6 +125,8 @@ struct pff_ctx {
   std::vector<LevelData> lv;
   XferTab xt{};
   bool has_state = false, qp_valid = false, mg_ready = false, has_fields = false;
+  bool st_valid = false;    // per-point residual state (depends on phi~ and the fields, not on U)
+  bool diag64_ok = false;   // FP64 diagonals present (always with the FP64 multigrid; on demand with FP32)
   double* phi_old = nullptr;
   double* hist1 = nullptr;  // phase field of the previous load step
   double* hist2 = nullptr;  // ... and of the one before
@@ -141,6 +144,9 @@ struct pff_ctx {
   double* pgrad_tmp = nullptr;
   // coarse dense blocks
   double *Au = nullptr, *Ap = nullptr, *Bc = nullptr, *gjbuf = nullptr, *cr = nullptr, *ce = nullptr, *ct = nullptr;
+  // FP32 copies of the coarse blocks and their inverses (multigrid in FP32)
+  float *Au32 = nullptr, *Ap32 = nullptr, *Bc32 = nullptr, *gjbuf32 = nullptr, *cr32 = nullptr, *ce32 = nullptr,
+        *ct32 = nullptr;
   // FGMRES
   double *V = nullptr, *Z = nullptr, *w = nullptr, *hdev = nullptr, *ydev = nullptr;
   std::vector<void*> allocs;
@@ -333,7 +339,10 @@ int ensure_work(pff_ctx* c, int l) {
   LevelData& L = c->lv[l];
   Real** w = work_of<Real>(L);
   if (w[0]) return PFF_OK;
-  for (int i = 0; i < 6; ++i) CR(dalloc(c, &w[i], L.nd));
+  for (int i = 0; i < 6; ++i) {
+    CR(dalloc(c, &w[i], L.nd));
+    CK(cudaMemsetAsync(w[i], 0, sizeof(Real) * L.nd, c->s));
+  }
   return PFF_OK;
 }
 
@@ -379,9 +388,9 @@ bool prof_jac(pff_ctx* c, int l) {
 // launches are not timed by pff_profile (they move more than the apply's bytes).
 template <typename Real>
 int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask, int outmask,
-                const ChebEpi<Real>* ce = nullptr) {
+                const ChebEpi<Real>* ce = nullptr, bool y_is_zero = false) {
   LevelData& L = c->lv[l];
-  CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
+  if (!y_is_zero) CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
   const bool timed = !ce && prof_jac<Real>(c, l);
   if (timed) CR(prof_mark(c));
   if (sizeof(Real) == 8 && c->prm.fp64_mode == 1) {
@@ -410,17 +419,47 @@ int qp_setup_level(pff_ctx* c, int l) {
   return PFF_OK;
 }
 
+// Tangent per-point data of the finest level (and the residual state with it).
 int ensure_qp(pff_ctx* c) {
   if (!c->has_state) return PFF_ERR_NO_STATE;
   if (!c->qp_valid) {
     CR(qp_setup_level(c, 0));
     c->qp_valid = true;
+    c->st_valid = true;
   }
   return PFF_OK;
 }
 
+// Residual state per point only (g(phi~), G_c, lambda, mu): what the residual and the parameter
+// gradient read; it does not change with U, so Newton iterations do not recompute it.
+int ensure_st(pff_ctx* c) {
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  if (!c->st_valid) {
+    LevelData& L = c->lv[0];
+    MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+    const double* F = L.fields;
+    CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
+                       c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
+                       nullptr, nullptr, nullptr, L.st64, c->s));
+    c->st_valid = true;
+  }
+  return PFF_OK;
+}
+
+// FP64 diagonals of every level when the multigrid runs in FP32 (for FP64 queries and smoothing).
+int ensure_diag64(pff_ctx* c) {
+  if (c->diag64_ok) return PFF_OK;
+  for (int l = 0; l < c->nlev; ++l) {
+    LevelData& L = c->lv[l];
+    CK(launch_diagonal<double>(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, c->s));
+    CK(launch_inv_diag(L.nd, L.d64, L.di64, nullptr, c->s));
+  }
+  c->diag64_ok = true;
+  return PFF_OK;
+}
+
 int residual_into(pff_ctx* c, double* r) {
-  CR(ensure_qp(c));
+  CR(ensure_st(c));
   LevelData& L = c->lv[0];
   CK(cudaMemsetAsync(r, 0, sizeof(double) * L.nd, c->s));
   const bool timed = prof_on(c, PFF_PROF_RESIDUAL);
@@ -439,24 +478,23 @@ int eig_estimate(pff_ctx* c, int l) {
   CR(ensure_work<Real>(c, l));
   Real** w = work_of<Real>(L);
   Real *r = w[0], *z = w[1], *pv = w[2], *Ap = w[3];
-  double* scal = L.lscal;  // 12 doubles
+  double* scal = L.lscal;  // 12 doubles and the reduction counter
   const int it_max = c->prm.eig_iters;
   double* ah = L.lhist;
   double* bh = L.lhist + 2 * it_max;
-  CK(cudaMemsetAsync(scal, 0, 12 * sizeof(double), c->s));
+  CK(cudaMemsetAsync(scal, 0, 16 * sizeof(double), c->s));
   CK(cudaMemsetAsync(L.lhist, 0, 4 * it_max * sizeof(double), c->s));
-  CK(launch_cg_init<Real>(n, nu, c->prm.eig_seed, L.flags, c->dim, L.nn, dinv_of<Real>(L), r, z, pv, c->s));
-  CK(launch_dot2<Real>(n, nu, r, z, L.lpart, scal + 0, c->s));
+  CK(cudaMemsetAsync(Ap, 0, sizeof(Real) * n, c->s));
+  CK(launch_cg_init<Real>(n, nu, c->prm.eig_seed, L.flags, L.nn, dinv_of<Real>(L), r, z, pv, L.lpart, scal, c->s));
   for (int it = 0; it < it_max; ++it) {
-    CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
-    CK(launch_dot2<Real>(n, nu, pv, Ap, L.lpart, scal + 2, c->s));
-    CK(launch_cg_scalars(0, it, it_max, scal, ah, bh, c->s));
-    CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, c->s));
-    CK(launch_dot2<Real>(n, nu, r, z, L.lpart, scal + 8, c->s));
-    CK(launch_cg_scalars(1, it, it_max, scal, ah, bh, c->s));
+    // Ap is zero here: zeroed above, then by every update
+    CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, nullptr, true));
+    CK(launch_cg_pap<Real>(n, nu, pv, Ap, L.lpart, scal, ah, it, it_max, c->s));
+    CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, L.lpart, bh, it, it_max, c->s));
     CK(launch_cg_pupdate<Real>(n, nu, z, scal, pv, c->s));
   }
   CK(launch_tridiag_eig(it_max, ah, bh, L.lam, c->s));
+  CK(cudaMemsetAsync(pv, 0, sizeof(Real) * n, c->s));  // w[2] is the smoother's zeroed apply buffer
   return PFF_OK;
 }
 
@@ -466,8 +504,14 @@ int eig_estimate(pff_ctx* c, int l) {
 int mg_level_branch(pff_ctx* c, int l) {
   LevelData& L = c->lv[l];
   if (l > 0) CR(qp_setup_level(c, l));
-  CK(launch_diagonal(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, nullptr, c->s));
-  CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
+  if (c->prm.mg_precision == 32) {
+    // the FP32 multigrid's Jacobi scaling, computed in FP32 from the FP32 per-point data
+    CK(launch_diagonal<float>(c->dim, c->p, c->prm.split, L.qp32, L.flags, L.g, L.t32, L.d32, c->s));
+    CK(launch_inv_diag32(L.nd, L.d32, L.di32, c->s));
+  } else {
+    CK(launch_diagonal<double>(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, L.d64, c->s));
+    CK(launch_inv_diag(L.nd, L.d64, L.di64, L.di32, c->s));
+  }
   if (l < c->nlev - 1) {
     if (c->prm.mg_precision == 32) CR(eig_estimate<float>(c, l));
     else CR(eig_estimate<double>(c, l));
@@ -475,8 +519,17 @@ int mg_level_branch(pff_ctx* c, int l) {
     // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
     const int nn = (int)L.nn, nu = c->dim * nn;
     CK(launch_coarse_assemble(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, c->Au, c->Ap, c->Bc, c->s));
-    CK(launch_gj_inverse(c->Au, nu, c->gjbuf, c->s));
-    CK(launch_gj_inverse(c->Ap, nn, c->gjbuf + 4 * nu, c->s));
+    if (c->prm.mg_precision == 32) {
+      // the FP32 multigrid inverts FP32 copies (its coarse solve runs in FP32 like the rest of the cycle)
+      CK(launch_cast<double, float>((long long)nu * nu, c->Au, c->Au32, c->s));
+      CK(launch_cast<double, float>((long long)nn * nn, c->Ap, c->Ap32, c->s));
+      CK(launch_cast<double, float>((long long)nn * nu, c->Bc, c->Bc32, c->s));
+      CK(launch_gj_inverse<float>(c->Au32, nu, c->gjbuf32, c->s));
+      CK(launch_gj_inverse<float>(c->Ap32, nn, c->gjbuf32 + gj_buffer_size(nu), c->s));
+    } else {
+      CK(launch_gj_inverse<double>(c->Au, nu, c->gjbuf, c->s));
+      CK(launch_gj_inverse<double>(c->Ap, nn, c->gjbuf + gj_buffer_size(nu), c->s));
+    }
   }
   return PFF_OK;
 }
@@ -560,6 +613,7 @@ int mg_setup(pff_ctx* c) {
       c->use_graph = false;
       CR(mg_build(c));
       c->mg_ready = true;
+      c->diag64_ok = c->prm.mg_precision != 32;
       return PFF_OK;
     }
     if (!c->sgraph[key][pv]) return PFF_ERR_CUDA;
@@ -570,17 +624,20 @@ int mg_setup(pff_ctx* c) {
       for (auto& r : c->srange[key][pv]) c->pending.push_back(r);
   }
   c->mg_ready = true;
+  c->diag64_ok = c->prm.mg_precision != 32;
   return PFF_OK;
 }
 
-// z = G_c^{-1} r on the coarsest level (FP64): z_u = Au^{-1} r_u, z_phi = Ap^{-1} (r_phi - B z_u).
-int coarse_solve64(pff_ctx* c, const double* r, double* z) {
+// z = G_c^{-1} r on the coarsest level, in the multigrid's precision:
+// z_u = Au^{-1} r_u, z_phi = Ap^{-1} (r_phi - B z_u) (block forward substitution).
+template <typename Real>
+int coarse_solve_blocks(pff_ctx* c, const Real* Au, const Real* Ap, const Real* Bc, Real* ct, const Real* r, Real* z) {
   LevelData& C = c->lv[c->nlev - 1];
   const int nn = (int)C.nn, nu = c->dim * nn;
-  CK(launch_gemv(c->Au, nu, nu, r, z, 1.0, 0.0, c->s));
-  CK(cudaMemcpyAsync(c->ct, r + nu, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
-  CK(launch_gemv(c->Bc, nn, nu, z, c->ct, -1.0, 1.0, c->s));
-  CK(launch_gemv(c->Ap, nn, nn, c->ct, z + nu, 1.0, 0.0, c->s));
+  CK(launch_gemv<Real>(Au, nu, nu, r, z, 1.0, 0.0, c->s));
+  CK(cudaMemcpyAsync(ct, r + nu, sizeof(Real) * nn, cudaMemcpyDeviceToDevice, c->s));
+  CK(launch_gemv<Real>(Bc, nn, nu, z, ct, -1.0, 1.0, c->s));
+  CK(launch_gemv<Real>(Ap, nn, nn, ct, z + nu, 1.0, 0.0, c->s));
   return PFF_OK;
 }
 
@@ -588,13 +645,19 @@ template <typename Real>
 int coarse_solve(pff_ctx* c, const Real* r, Real* z);
 template <>
 int coarse_solve<double>(pff_ctx* c, const double* r, double* z) {
-  return coarse_solve64(c, r, z);
+  if (c->prm.mg_precision != 32) return coarse_solve_blocks<double>(c, c->Au, c->Ap, c->Bc, c->ct, r, z);
+  const long long n = c->lv[c->nlev - 1].nd;
+  CK(launch_cast<double, float>(n, r, c->cr32, c->s));
+  CR(coarse_solve_blocks<float>(c, c->Au32, c->Ap32, c->Bc32, c->ct32, c->cr32, c->ce32));
+  CK(launch_cast<float, double>(n, c->ce32, z, c->s));
+  return PFF_OK;
 }
 template <>
 int coarse_solve<float>(pff_ctx* c, const float* r, float* z) {
+  if (c->prm.mg_precision == 32) return coarse_solve_blocks<float>(c, c->Au32, c->Ap32, c->Bc32, c->ct32, r, z);
   const long long n = c->lv[c->nlev - 1].nd;
   CK(launch_cast<float, double>(n, r, c->cr, c->s));
-  CR(coarse_solve64(c, c->cr, c->ce));
+  CR(coarse_solve_blocks<double>(c, c->Au, c->Ap, c->Bc, c->ct, c->cr, c->ce));
   CK(launch_cast<double, float>(n, c->ce, z, c->s));
   return PFF_OK;
 }
@@ -623,7 +686,8 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
       ce.c1 = rho_new * rho;
       ce.rho_k = rho_new;
       ce.on = 1;
-      CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce));
+      // t is all zero on entry (work vectors start zeroed; every use below leaves it zeroed)
+      CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce, true));
       CK(launch_cheb_seam<Real>(L.g, t, ce, c->s));
     } else {
       CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
@@ -645,17 +709,16 @@ int vcycle_level(pff_ctx* c, int l, const Real* r, Real* e) {
   Real** w = work_of<Real>(L);
   Real** wc = work_of<Real>(Lc);
   Real *t = w[2], *res = w[3], *dv = w[4], *sx = w[5];
+  const bool zt = c->dim == 2;  // in 2D the apply buffer t is kept zeroed between uses
   CR(smooth<Real>(c, l, r, e, t, dv));
-  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
-  CK(cudaMemcpyAsync(res, r, sizeof(Real) * L.nd, cudaMemcpyDeviceToDevice, c->s));
-  CK(launch_axpby<Real>(L.nd, -1.0, t, 1.0, res, c->s));
+  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY, nullptr, zt));
+  CK(launch_res_update<Real>(L.nd, r, t, res, c->s));
   // res is zero on masked fine rows (r is, and G has identity rows there with e = 0): no Z_f needed
   CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s, false));
   CR(vcycle_level<Real>(c, l + 1, wc[0], wc[1]));
   CK(launch_prolong<Real>(c->dim, c->p, wc[1], e, L.flags, Lc.g, L.g, c->xt, true, c->s));
-  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY));
-  CK(cudaMemcpyAsync(res, r, sizeof(Real) * L.nd, cudaMemcpyDeviceToDevice, c->s));
-  CK(launch_axpby<Real>(L.nd, -1.0, t, 1.0, res, c->s));
+  CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY, nullptr, zt));
+  CK(launch_res_update<Real>(L.nd, r, t, res, c->s));
   CR(smooth<Real>(c, l, res, sx, t, dv));
   CK(launch_axpby<Real>(L.nd, 1.0, sx, 1.0, e, c->s));
   return PFF_OK;
@@ -946,6 +1009,7 @@ static int setup_impl(pff_ctx* c) {
     }
     CR(dalloc(c, &L.d64, L.nd));
     CR(dalloc(c, &L.di64, L.nd));
+    CR(dalloc(c, &L.d32, L.nd));
     CR(dalloc(c, &L.di32, L.nd));
     CR(dalloc(c, &L.lam, 4));
     CR(dalloc(c, &L.lscal, 16));
@@ -982,7 +1046,17 @@ static int setup_impl(pff_ctx* c) {
   CR(dalloc(c, &c->Au, nuc * nuc));
   CR(dalloc(c, &c->Ap, nnc * nnc));
   CR(dalloc(c, &c->Bc, nnc * nuc));
-  CR(dalloc(c, &c->gjbuf, 4 * nuc + 4 * nnc));
+  if (c->prm.mg_precision == 32) {
+    CR(dalloc(c, &c->Au32, nuc * nuc));
+    CR(dalloc(c, &c->Ap32, nnc * nnc));
+    CR(dalloc(c, &c->Bc32, nnc * nuc));
+    CR(dalloc(c, &c->gjbuf32, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc)));
+    CR(dalloc(c, &c->cr32, C.nd));
+    CR(dalloc(c, &c->ce32, C.nd));
+    CR(dalloc(c, &c->ct32, C.nd));
+  } else {
+    CR(dalloc(c, &c->gjbuf, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc)));
+  }
   CR(dalloc(c, &c->cr, C.nd));
   CR(dalloc(c, &c->ce, C.nd));
   CR(dalloc(c, &c->ct, C.nd));
@@ -1072,6 +1146,7 @@ int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const doub
   }
   c->has_state = true;
   c->qp_valid = false;
+  c->st_valid = false;
   c->mg_ready = false;
   c->nhist = 0;
   if (active) {
@@ -1086,7 +1161,6 @@ int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const doub
     CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
     c->qp_valid = false;
   }
-  CR(ensure_qp(c));
   return PFF_OK;
 }
 
@@ -1131,10 +1205,14 @@ int pff_diagonal(pff_ctx* c, int level, void* diag, int precision) {
   if (!c || !diag || level < 0 || level >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
   CR(mg_setup(c));
   LevelData& L = c->lv[level];
-  if (precision == 64)
+  if (precision == 64) {
+    CR(ensure_diag64(c));
     CK(cudaMemcpyAsync(diag, L.d64, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
-  else
+  } else if (c->prm.mg_precision == 32) {
+    CK(cudaMemcpyAsync(diag, L.d32, sizeof(float) * L.nd, cudaMemcpyDeviceToDevice, c->s));
+  } else {
     CK(launch_cast<double, float>(L.nd, L.d64, static_cast<float*>(diag), c->s));
+  }
   return PFF_OK;
 }
 
@@ -1185,6 +1263,7 @@ int pff_smooth(pff_ctx* c, int level, const void* f, void* x, int precision) {
   if (!c || !f || !x || level < 0 || level >= c->nlev || !valid_prec(precision)) return PFF_ERR_INVALID_ARG;
   CR(mg_setup(c));
   if (precision == 64) {
+    CR(ensure_diag64(c));
     CR(ensure_work<double>(c, level));
     LevelData& L = c->lv[level];
     return smooth<double>(c, level, static_cast<const double*>(f), static_cast<double*>(x), L.w64[2], L.w64[4]);
@@ -1197,7 +1276,7 @@ int pff_smooth(pff_ctx* c, int level, const void* f, void* x, int precision) {
 int pff_coarse_solve(pff_ctx* c, const double* r, double* z) {
   if (!c || !r || !z) return PFF_ERR_INVALID_ARG;
   CR(mg_setup(c));
-  return coarse_solve64(c, r, z);
+  return coarse_solve<double>(c, r, z);
 }
 
 int pff_vcycle(pff_ctx* c, const double* r, double* z) {
@@ -1302,6 +1381,7 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
   CK(launch_load_step_prep(c->dim, nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr, L.phit,
                            c->phi_old, c->s));
   c->qp_valid = false;
+  c->st_valid = false;
   c->mg_ready = false;
   const int st = pff_solve_pdas(c, max_iters, newton_rtol, nullptr, reps, n_steps);
   if (st == PFF_OK) {
@@ -1315,7 +1395,7 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
 
 int pff_param_grad(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
   if (!c || !v) return PFF_ERR_INVALID_ARG;
-  CR(ensure_qp(c));
+  CR(ensure_st(c));
   LevelData& L = c->lv[0];
   if (!c->pgrad_tmp) {
     const long long ncell = c->dim == 2 ? (long long)L.N * L.N : (long long)L.N * L.N * L.N;
@@ -1402,7 +1482,7 @@ extern "C" int pff_param_grad_noalloc(pff_ctx* c, const double* v, double* g_gc,
   if (3 * ncell * nq > PFF_NOALLOC_SCRATCH_DOUBLES) return PFF_ERR_TOO_LARGE;
   double* tmp = nullptr;
   CR(noalloc_scratch(&tmp));
-  CR(ensure_qp(c));
+  CR(ensure_st(c));
   MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
   double* vm = c->scratch;  // allocated with the context
   CK(launch_masked_copy(c->dim, L.nn, 1.0, v, L.flags, (1u << c->dim) - 1u, vm, c->s));

@@ -40,14 +40,34 @@ template <> struct TileCfg<3, 2> { static constexpr int TX = 4, TY = 2, TZ = 2; 
 template <> struct TileCfg<3, 3> { static constexpr int TX = 2, TY = 2, TZ = 2; };
 template <> struct TileCfg<3, 4> { static constexpr int TX = 2, TY = 2, TZ = 1; };
 
-// Host-visible copy of the tile shapes (same numbers as TileCfg).
+// Programmatic dependent launch: a kernel launched with launch_k (below) may be scheduled while its
+// predecessor in the stream is still running; it must call pdl_wait() before its first access to
+// global memory, which returns once the predecessor grid has completed and its writes are visible.
+// Without a programmatic predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+// Host-side lookup of TileCfg.
+template <int DIM, int P>
+inline void tile_shape_of(int* t) {
+  t[0] = TileCfg<DIM, P>::TX;
+  t[1] = TileCfg<DIM, P>::TY;
+  t[2] = TileCfg<DIM, P>::TZ;
+}
 inline void tile_shape(int dim, int p, int* t) {
-  static const int t2[4][3] = {{8, 16, 1}, {8, 8, 1}, {8, 4, 1}, {8, 4, 1}};
-  static const int t3[4][3] = {{4, 4, 2}, {4, 2, 2}, {2, 2, 2}, {2, 2, 1}};
-  const int(*tt)[3] = dim == 2 ? t2 : t3;
-  t[0] = tt[p - 1][0];
-  t[1] = tt[p - 1][1];
-  t[2] = tt[p - 1][2];
+  switch (dim * 10 + p) {
+    case 21: tile_shape_of<2, 1>(t); break;
+    case 22: tile_shape_of<2, 2>(t); break;
+    case 23: tile_shape_of<2, 3>(t); break;
+    case 24: tile_shape_of<2, 4>(t); break;
+    case 31: tile_shape_of<3, 1>(t); break;
+    case 32: tile_shape_of<3, 2>(t); break;
+    case 33: tile_shape_of<3, 3>(t); break;
+    default: tile_shape_of<3, 4>(t); break;
+  }
 }
 
 // Geometry of one level as the kernels see it.

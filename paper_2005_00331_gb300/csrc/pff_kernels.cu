@@ -54,13 +54,14 @@ struct CellQP {
     return nd;
   }
   // N_a and grad N_a at this point
-  __device__ void shape(int a, const Tab<double>& tb, double& N, double dN[DIM]) const {
+  template <typename Real>
+  __device__ void shape(int a, const Tab<Real>& tb, Real& N, Real dN[DIM]) const {
     constexpr int n = P + 1;
     const int aa[3] = {a % n, (a / n) % n, DIM == 3 ? a / (n * n) : 0};
-    N = 1.0;
-    for (int t = 0; t < DIM; ++t) dN[t] = 1.0;
+    N = Real(1);
+    for (int t = 0; t < DIM; ++t) dN[t] = Real(1);
     for (int s = 0; s < DIM; ++s) {
-      const double Sv = tb.S[q[s]][aa[s]], Dv = tb.D[q[s]][aa[s]];
+      const Real Sv = tb.S[q[s]][aa[s]], Dv = tb.D[q[s]][aa[s]];
       N *= Sv;
       for (int t = 0; t < DIM; ++t) dN[t] *= (t == s ? Dv : Sv);
     }
@@ -126,14 +127,23 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
   if (t >= ncell * NQ) return;
   CellQP<DIM, P> cq;
   cq.set(t / NQ, int(t % NQ), g);
-  double gu[DIM][DIM], ph, gph[DIM];
-  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
   const double pt = eval_scalar<DIM, P>(cq, phit, g, tb);
   const double gc = gcf ? eval_scalar<DIM, P>(cq, gcf, g, tb) : mc.gc;
   const double lam = lamf ? eval_scalar<DIM, P>(cq, lamf, g, tb) : mc.lambda;
   const double mu = muf ? eval_scalar<DIM, P>(cq, muf, g, tb) : mc.mu;
+  const double gt = deg_g(pt, mc.kappa);
+  if (st64) {
+    const long long sb = cq.tile * ST_NV * g.qpt + cq.qidx;
+    st64[sb] = gt;
+    st64[sb + g.qpt] = gc;
+    st64[sb + 2 * g.qpt] = lam;
+    st64[sb + 3 * g.qpt] = mu;
+  }
+  if (!qp64) return;  // residual state only (it does not depend on U)
+  double gu[DIM][DIM], ph, gph[DIM];
+  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
   const double jxw = cq.jxw(tb);
-  const double gt = deg_g(pt, mc.kappa), dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
+  const double dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
 
   double e[DIM][DIM], tr = 0.0;
   for (int i = 0; i < DIM; ++i) {
@@ -203,13 +213,6 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
     if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
     if (qpdf) qpdf[base + v * g.qpt] = df_from(vals[v]);
   }
-  if (st64) {
-    const long long sb = cq.tile * ST_NV * g.qpt + cq.qidx;
-    st64[sb] = gt;
-    st64[sb + g.qpt] = gc;
-    st64[sb + 2 * g.qpt] = lam;
-    st64[sb + 3 * g.qpt] = mu;
-  }
 }
 
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
@@ -234,80 +237,78 @@ cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const do
 // ===========================================================================================
 // Diagonal of diag(G_uu, G_phiphi): for a basis function N_a e_k the quadratic form
 // e(N_a e_k) : C_eff : e(N_a e_k), and c N_a^2 + k |grad N_a|^2 for the phase field.
-template <int DIM, int P, int SPLIT>
-__global__ void k_diagonal(const double* __restrict__ qp64, Geom g, Tab<double> tb, double* __restrict__ d64) {
+template <int DIM, int P, int SPLIT, typename Real>
+__global__ void k_diagonal(const Real* __restrict__ qp, Geom g, Tab<Real> tb, Real* __restrict__ d) {
   constexpr int NA = ipow<DIM>(P + 1), NQ = NA;
   constexpr int NM = Mandel<DIM>::NM;
   constexpr int NV = qp_nv(DIM, SPLIT);
   constexpr int OFFB = SPLIT == 0 ? 2 : NM * (NM + 1) / 2;
+  constexpr Real R2 = Real(RS2);
   const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= ncell * NA) return;
   const long long cell = t / NA;
   const int a = int(t % NA);
-  double acc[DIM + 1];
-  for (int f = 0; f <= DIM; ++f) acc[f] = 0.0;
+  Real acc[DIM + 1];
+  for (int f = 0; f <= DIM; ++f) acc[f] = Real(0);
   CellQP<DIM, P> cq;
   long long nd = 0;
   for (int q = 0; q < NQ; ++q) {
     cq.set(cell, q, g);
     if (q == 0) nd = cq.node(a, g);
-    double N, dN[DIM];
+    Real N, dN[DIM];
     cq.shape(a, tb, N, dN);
-    const double* v = qp64 + cq.tile * NV * g.qpt + cq.qidx;
+    const Real* v = qp + cq.tile * NV * g.qpt + cq.qidx;
     for (int k = 0; k < DIM; ++k) {
-      double em[NM];
+      Real em[NM];
       for (int m = 0; m < NM; ++m) {
         const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
-        if (i == j) em[m] = (i == k) ? dN[k] : 0.0;
-        else em[m] = (i == k ? dN[j] : (j == k ? dN[i] : 0.0)) * RS2;
+        if (i == j) em[m] = (i == k) ? dN[k] : Real(0);
+        else em[m] = (i == k ? dN[j] : (j == k ? dN[i] : Real(0))) * R2;
       }
-      double val = 0.0;
+      Real val = Real(0);
       if constexpr (SPLIT == 0) {
-        double ee = 0.0;
+        Real ee = Real(0);
         for (int m = 0; m < NM; ++m) ee += em[m] * em[m];
-        val = v[0] * dN[k] * dN[k] + 2.0 * v[g.qpt] * ee;
+        val = v[0] * dN[k] * dN[k] + Real(2) * v[g.qpt] * ee;
       } else {
         for (int i = 0; i < NM; ++i)
           for (int j = i; j < NM; ++j) {
-            const double cij = v[sym_index(NM, i, j) * g.qpt];
-            val += (i == j ? 1.0 : 2.0) * cij * em[i] * em[j];
+            const Real cij = v[sym_index(NM, i, j) * g.qpt];
+            val += (i == j ? Real(1) : Real(2)) * cij * em[i] * em[j];
           }
       }
       acc[k] += val;
     }
-    double gg = 0.0;
+    Real gg = Real(0);
     for (int j = 0; j < DIM; ++j) gg += dN[j] * dN[j];
     acc[DIM] += v[(OFFB + NM) * g.qpt] * N * N + v[(OFFB + NM + 1) * g.qpt] * gg;
   }
-  for (int f = 0; f <= DIM; ++f) atomicAdd(d64 + f * g.nn + nd, acc[f]);
+  for (int f = 0; f <= DIM; ++f) atomicAdd(d + f * g.nn + nd, acc[f]);
 }
 
-__global__ void k_diag_finish(long long n, long long nn, const unsigned char* __restrict__ flags,
-                              double* __restrict__ d64, float* __restrict__ d32) {
+template <typename Real>
+__global__ void k_diag_finish(long long n, long long nn, const unsigned char* __restrict__ flags, Real* __restrict__ d) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= n) return;
   const int f = int(e / nn);
-  const long long nd = e % nn;
-  double v = d64[e];
-  if ((flags[nd] >> f) & 1u) v = 1.0;
-  d64[e] = v;
-  if (d32) d32[e] = (float)v;
+  if ((flags[e % nn] >> f) & 1u) d[e] = Real(1);
 }
 
-cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const unsigned char* flags,
-                            const Geom& g, const Tab<double>& tb, double* d64, float* d32, cudaStream_t s) {
+template <typename Real>
+cudaError_t launch_diagonal(int dim, int p, int split, const Real* qp, const unsigned char* flags, const Geom& g,
+                            const Tab<Real>& tb, Real* d, cudaStream_t s) {
   const long long n = (dim + 1) * g.nn;
-  cudaError_t e = cudaMemsetAsync(d64, 0, sizeof(double) * n, s);
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(Real) * n, s);
   if (e != cudaSuccess) return e;
   const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
   const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
   const unsigned gr = grid_for(tot, 128);
   bool done = false;
-#define PFF_CASE(DD, PP, SS)                                                   \
-  if (!done && dim == DD && p == PP && split == SS) {                         \
-    count_launch(); k_diagonal<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, d64);              \
-    done = true;                                                               \
+#define PFF_CASE(DD, PP, SS)                                                         \
+  if (!done && dim == DD && p == PP && split == SS) {                               \
+    count_launch(); k_diagonal<DD, PP, SS, Real><<<gr, 128, 0, s>>>(qp, g, tb, d);  \
+    done = true;                                                                     \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
   PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
@@ -315,9 +316,13 @@ cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const
   PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
 #undef PFF_CASE
   if (!done) return cudaErrorInvalidValue;
-  count_launch(); k_diag_finish<<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d64, d32);
+  count_launch(); k_diag_finish<Real><<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d);
   return cudaGetLastError();
 }
+template cudaError_t launch_diagonal<double>(int, int, int, const double*, const unsigned char*, const Geom&,
+                                             const Tab<double>&, double*, cudaStream_t);
+template cudaError_t launch_diagonal<float>(int, int, int, const float*, const unsigned char*, const Geom&,
+                                            const Tab<float>&, float*, cudaStream_t);
 
 // ===========================================================================================
 // Parameter gradients: per point the partial derivatives of the residual's pointwise terms with
@@ -533,61 +538,135 @@ cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64
   return cudaGetLastError();
 }
 
-// In-place Gauss-Jordan inversion. Step k reads pivot row and column k from buf[k & 1] and, while
-// updating, stores the updated row and column k + 1 into buf[(k + 1) & 1] for the next step.
-__global__ void k_gj_save(double* __restrict__ A, int n, int k, double* __restrict__ buf) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  buf[i] = A[(long long)i * n + k];
-  buf[n + i] = A[(long long)k * n + i];
-}
-__global__ void k_gj_update(double* __restrict__ A, int n, int k, const double* __restrict__ cur,
-                            double* __restrict__ nxt) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || j >= n) return;
-  const double piv = cur[n + k];
-  double* aij = A + (long long)i * n + j;
-  double v;
-  if (i == k) v = (j == k) ? 1.0 / piv : cur[n + j] / piv;
-  else if (j == k) v = -cur[i] / piv;
-  else v = *aij - cur[i] * cur[n + j] / piv;
-  *aij = v;
-  if (j == k + 1) nxt[i] = v;
-  if (i == k + 1) nxt[n + j] = v;
+// In-place Gauss-Jordan inversion without pivoting, blocked by GJB pivots. One block step with
+// pivot block K (rows/columns k0 .. k0+bk-1) and P = A_KK^{-1} performs
+//   A_ij -= A_iK P A_Kj (i, j outside K),  A_Kj = P A_Kj,  A_iK = -A_iK P,  A_KK = P,
+// which is bk consecutive pointwise Gauss-Jordan steps at once. Three launches per step: the
+// pivot block inverse (one CTA), the panels W = P A_K* and C = A_*K, and the rank-bk update.
+constexpr int GJB = 32;
+
+template <typename Real>
+__global__ void __launch_bounds__(GJB * GJB) k_gj_pivot(const Real* __restrict__ A, int n, int k0, int bk,
+                                                         Real* __restrict__ P) {
+  __shared__ Real s[GJB][GJB + 1];
+  const int i = threadIdx.y, j = threadIdx.x;
+  const bool in = i < bk && j < bk;
+  s[i][j] = in ? A[(long long)(k0 + i) * n + k0 + j] : Real(0);
+  __syncthreads();
+  __shared__ Real inv;
+  for (int m = 0; m < bk; ++m) {
+    // one division per step (FP64 division is slow on this part): the other threads multiply
+    if (i == 0 && j == 0) inv = Real(1) / s[m][m];
+    __syncthreads();
+    const Real r = inv, aim = s[i][m], amj = s[m][j], aij = s[i][j];
+    __syncthreads();
+    Real v;
+    if (i == m) v = (j == m) ? r : amj * r;
+    else if (j == m) v = -aim * r;
+    else v = aij - aim * (amj * r);
+    if (in) s[i][j] = v;
+    __syncthreads();
+  }
+  if (in) P[i * GJB + j] = s[i][j];
 }
 
-cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s) {
-  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
-  count_launch(); k_gj_save<<<grid_for(n), BLK, 0, s>>>(A, n, 0, buf);
-  for (int k = 0; k < n; ++k) {
-    count_launch(); k_gj_update<<<grd, blk, 0, s>>>(A, n, k, buf + (k & 1) * 2 * n, buf + ((k + 1) & 1) * 2 * n);
+// W[m][j] = (P A_K*)[m][j] for j outside K and P[m][j - k0] inside; C[i][m] = A[i][k0 + m].
+template <typename Real>
+__global__ void k_gj_panels(const Real* __restrict__ A, int n, int k0, int bk, const Real* __restrict__ P,
+                            Real* __restrict__ W, Real* __restrict__ C) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < (long long)bk * n) {
+    const int m = int(t / n), j = int(t % n);
+    Real v;
+    if (j >= k0 && j < k0 + bk) {
+      v = P[m * GJB + (j - k0)];
+    } else {
+      v = Real(0);
+      for (int l = 0; l < bk; ++l) v = fmac(P[m * GJB + l], A[(long long)(k0 + l) * n + j], v);
+    }
+    W[(long long)m * n + j] = v;
+  } else if (t < 2LL * bk * n) {
+    const long long u = t - (long long)bk * n;
+    const int i = int(u / bk), m = int(u % bk);
+    C[(long long)i * GJB + m] = A[(long long)i * n + k0 + m];
+  }
+}
+
+// Rank-bk update on 16 x 16 tiles of A.
+template <typename Real>
+__global__ void __launch_bounds__(256) k_gj_rank(Real* __restrict__ A, int n, int k0, int bk,
+                                                 const Real* __restrict__ W, const Real* __restrict__ C) {
+  __shared__ Real cs[16][GJB + 1];
+  __shared__ Real ws[GJB][17];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int tid = ty * 16 + tx;
+  for (int e = tid; e < 16 * GJB; e += 256) {
+    const int r = e / GJB, m = e % GJB;
+    cs[r][m] = (i0 + r < n && m < bk) ? C[(long long)(i0 + r) * GJB + m] : Real(0);
+    const int mm = e / 16, cc = e % 16;
+    ws[mm][cc] = (j0 + cc < n && mm < bk) ? W[(long long)mm * n + j0 + cc] : Real(0);
+  }
+  __syncthreads();
+  const int i = i0 + ty, j = j0 + tx;
+  if (i >= n || j >= n) return;
+  Real* aij = A + (long long)i * n + j;
+  if (i >= k0 && i < k0 + bk) {
+    *aij = ws[i - k0][tx];
+    return;
+  }
+  Real sum = Real(0);
+  for (int m = 0; m < bk; ++m) sum = fmac(cs[ty][m], ws[m][tx], sum);
+  *aij = (j >= k0 && j < k0 + bk) ? -sum : *aij - sum;
+}
+
+long long gj_buffer_size(int n) { return (long long)GJB * GJB + 2LL * GJB * n; }
+
+template <typename Real>
+cudaError_t launch_gj_inverse(Real* A, int n, Real* buf, cudaStream_t s) {
+  Real* P = buf;
+  Real* W = buf + GJB * GJB;
+  Real* C = W + (long long)GJB * n;
+  const dim3 tile(16, 16), grid((n + 15) / 16, (n + 15) / 16);
+  for (int k0 = 0; k0 < n; k0 += GJB) {
+    const int bk = n - k0 < GJB ? n - k0 : GJB;
+    count_launch(); k_gj_pivot<Real><<<1, dim3(GJB, GJB), 0, s>>>(A, n, k0, bk, P);
+    count_launch(); k_gj_panels<Real><<<grid_for(2LL * bk * n, 64), 64, 0, s>>>(A, n, k0, bk, P, W, C);
+    count_launch(); k_gj_rank<Real><<<grid, tile, 0, s>>>(A, n, k0, bk, W, C);
   }
   return cudaGetLastError();
 }
+template cudaError_t launch_gj_inverse<double>(double*, int, double*, cudaStream_t);
+template cudaError_t launch_gj_inverse<float>(float*, int, float*, cudaStream_t);
 
-__global__ void k_gemv(const double* __restrict__ A, int n, int m, const double* __restrict__ x,
-                       double* __restrict__ y, double alpha, double beta) {
+template <typename Real>
+__global__ void k_gemv(const Real* __restrict__ A, int n, int m, const Real* __restrict__ x, Real* __restrict__ y,
+                       double alpha, double beta) {
+  pdl_wait();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
-  const double* row = A + (long long)warp * m;
-  double s = 0.0;
-  for (int j = lane; j < m; j += 32) s += row[j] * x[j];
+  const Real* row = A + (long long)warp * m;
+  Real s = Real(0);
+  for (int j = lane; j < m; j += 32) s = fmac(row[j], x[j], s);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[warp] = (beta == 0.0 ? 0.0 : beta * y[warp]) + alpha * s;
+  if (lane == 0) y[warp] = (beta == 0.0 ? Real(0) : Real(beta) * y[warp]) + Real(alpha) * s;
 }
 
-cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
+template <typename Real>
+cudaError_t launch_gemv(const Real* A, int n, int m, const Real* x, Real* y, double alpha, double beta,
                         cudaStream_t s) {
-  count_launch(); k_gemv<<<grid_for((long long)n * 32), BLK, 0, s>>>(A, n, m, x, y, alpha, beta);
-  return cudaGetLastError();
+  return launch_k(k_gemv<Real>, dim3(grid_for((long long)n * 32)), dim3(BLK), 0, s, A, n, m, x, y, alpha, beta);
 }
+template cudaError_t launch_gemv<double>(const double*, int, int, const double*, double*, double, double,
+                                         cudaStream_t);
+template cudaError_t launch_gemv<float>(const float*, int, int, const float*, float*, double, double, cudaStream_t);
 
 // ===========================================================================================
 // Transfers between a coarse level (Nc cells) and its fine level (2 Nc cells), same degree.
 template <int DIM, int P, typename Real>
 __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, const unsigned char* __restrict__ flf,
                           Geom gc, Geom gf, XferTab xt, int accumulate) {
+  pdl_wait();
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gf.nn) return;
   long long rem = nd;
@@ -636,6 +715,7 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
 template <int DIM, int P, typename Real>
 __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
                            const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine) {
+  pdl_wait();
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gc.nn) return;
   constexpr int MAXL = 2 * (2 * P + 1);
@@ -689,11 +769,10 @@ template <typename Real>
 cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f, const Geom& gc,
                            const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s) {
   const unsigned gr = grid_for(gf.nn);
-#define PFF_CASE(DD, PP)                                                                            \
-  if (dim == DD && p == PP) {                                                                       \
-    count_launch(); k_prolong<DD, PP, Real><<<gr, BLK, 0, s>>>(xc, yf, flags_f, gc, gf, xt, accumulate ? 1 : 0); \
-    return cudaGetLastError();                                                                      \
-  }
+#define PFF_CASE(DD, PP)                                                                                 \
+  if (dim == DD && p == PP)                                                                              \
+    return launch_k(k_prolong<DD, PP, Real>, dim3(gr), dim3(BLK), 0, s, xc, yf, flags_f, gc, gf, xt,     \
+                    accumulate ? 1 : 0);
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
   PFF_CASE(3, 1) PFF_CASE(3, 2) PFF_CASE(3, 3) PFF_CASE(3, 4)
 #undef PFF_CASE
@@ -705,11 +784,10 @@ cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsi
                             const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
                             cudaStream_t s, bool mask_fine) {
   const unsigned gr = grid_for(gc.nn, 128);
-#define PFF_CASE(DD, PP)                                                                  \
-  if (dim == DD && p == PP) {                                                             \
-    count_launch(); k_restrict<DD, PP, Real><<<gr, 128, 0, s>>>(xf, yc, flags_f, flags_c, gf, gc, xt, mask_fine ? 1 : 0); \
-    return cudaGetLastError();                                                            \
-  }
+#define PFF_CASE(DD, PP)                                                                                 \
+  if (dim == DD && p == PP)                                                                              \
+    return launch_k(k_restrict<DD, PP, Real>, dim3(gr), dim3(128), 0, s, xf, yc, flags_f, flags_c, gf, gc, \
+                    xt, mask_fine ? 1 : 0);
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
   PFF_CASE(3, 1) PFF_CASE(3, 2) PFF_CASE(3, 3) PFF_CASE(3, 4)
 #undef PFF_CASE
@@ -803,11 +881,13 @@ cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, u
 // Vector kernels.
 template <typename Real>
 __global__ void k_axpby(long long n, double a, const Real* __restrict__ x, double b, Real* __restrict__ y) {
+  pdl_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     y[e] = Real(a * (double)x[e] + (b == 0.0 ? 0.0 : b * (double)y[e]));
 }
 template <>
 __global__ void k_axpby<float>(long long n, double a, const float* __restrict__ x, double b, float* __restrict__ y) {
+  pdl_wait();
   const float af = (float)a, bf = (float)b;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     y[e] = af * x[e] + (bf == 0.0f ? 0.0f : bf * y[e]);
@@ -818,14 +898,33 @@ cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  count_launch(); k_axpby<Real><<<(unsigned)g, BLK, 0, s>>>(n, a, x, b, y);
-  return cudaGetLastError();
+  return launch_k(k_axpby<Real>, dim3((unsigned)g), dim3(BLK), 0, s, n, a, x, b, y);
 }
 template cudaError_t launch_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
 template cudaError_t launch_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
 
+// res = r - t, then t = 0 (the V-cycle's residual; leaves the apply buffer zeroed for the next apply).
+template <typename Real>
+__global__ void k_res_update(long long n, const Real* __restrict__ r, Real* __restrict__ t, Real* __restrict__ res) {
+  pdl_wait();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    res[e] = r[e] - t[e];
+    t[e] = Real(0);
+  }
+}
+template <typename Real>
+cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  return launch_k(k_res_update<Real>, dim3((unsigned)g), dim3(BLK), 0, s, n, r, t, res);
+}
+template cudaError_t launch_res_update<double>(long long, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_res_update<float>(long long, const float*, float*, float*, cudaStream_t);
+
 template <typename Ti, typename To>
 __global__ void k_cast(long long n, const Ti* __restrict__ x, To* __restrict__ y) {
+  pdl_wait();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     y[e] = To(x[e]);
 }
@@ -834,8 +933,7 @@ cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  count_launch(); k_cast<Ti, To><<<(unsigned)g, BLK, 0, s>>>(n, x, y);
-  return cudaGetLastError();
+  return launch_k(k_cast<Ti, To>, dim3((unsigned)g), dim3(BLK), 0, s, n, x, y);
 }
 template cudaError_t launch_cast<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t launch_cast<float, double>(long long, const float*, double*, cudaStream_t);
@@ -976,6 +1074,7 @@ template <typename Real>
 __global__ void k_cheb(int step, long long n, long long nu, const Real* __restrict__ f, const Real* __restrict__ Ax,
                        const Real* __restrict__ dinv, Real* __restrict__ d, Real* __restrict__ x,
                        const double* __restrict__ lam_max, double lo, double hi, double c1, double rho_k) {
+  pdl_wait();
   const double l0 = lam_max[0], l1 = lam_max[1];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double lm = e < nu ? l0 : l1;
@@ -999,6 +1098,7 @@ __global__ void k_cheb<float>(int step, long long n, long long nu, const float* 
                               const float* __restrict__ Ax, const float* __restrict__ dinv, float* __restrict__ d,
                               float* __restrict__ x, const double* __restrict__ lam_max, double lo, double hi,
                               double c1, double rho_k) {
+  pdl_wait();
   __shared__ float coef[2][3];
   if (threadIdx.x < 2) {
     const double lm = lam_max[threadIdx.x];
@@ -1030,8 +1130,8 @@ cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, cons
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  count_launch(); k_cheb<Real><<<(unsigned)g, BLK, 0, s>>>(step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1, rho_k);
-  return cudaGetLastError();
+  return launch_k(k_cheb<Real>, dim3((unsigned)g), dim3(BLK), 0, s, step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1,
+                  rho_k);
 }
 template cudaError_t launch_cheb<double>(int, long long, long long, const double*, const double*, const double*,
                                          double*, double*, const double*, double, double, double, double,
@@ -1047,10 +1147,45 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+// CG-Lanczos kernels. Each one also reduces a pair of block dot products: every CTA writes its
+// partial sums, and the CTA that finishes last (counted on *cnt) adds the partials in a fixed order
+// and performs the scalar step, so one iteration takes the apply and three kernels.
+// scal: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1 | counter]
+constexpr int CG_GRID = DOT_GRID;
+
+__device__ __forceinline__ bool cg_reduce_last(double s0, double s1, double* __restrict__ part, unsigned* cnt,
+                                               double& r0, double& r1) {
+  __shared__ double sh[32];
+  __shared__ int last;
+  r0 = block_sum(s0, sh);
+  r1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r0;
+    part[2 * blockIdx.x + 1] = r1;
+    __threadfence();
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double t0 = 0.0, t1 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    t0 += __ldcg(part + 2 * b);
+    t1 += __ldcg(part + 2 * b + 1);
+  }
+  r0 = block_sum(t0, sh);
+  r1 = block_sum(t1, sh);
+  if (threadIdx.x == 0) *cnt = 0u;
+  return true;  // sums valid in thread 0
+}
+
 template <typename Real>
-__global__ void k_cg_init(long long n, unsigned long long seed, const unsigned char* __restrict__ flags, long long nn,
-                          const Real* __restrict__ dinv, Real* __restrict__ r, Real* __restrict__ z,
-                          Real* __restrict__ pv) {
+__global__ void __launch_bounds__(BLK) k_cg_init(long long n, long long nu, unsigned long long seed,
+                                                 const unsigned char* __restrict__ flags, long long nn,
+                                                 const Real* __restrict__ dinv, Real* __restrict__ r,
+                                                 Real* __restrict__ z, Real* __restrict__ pv, double* __restrict__ part,
+                                                 double* __restrict__ scal) {
+  double s0 = 0.0, s1 = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int f = int(e / nn);
     const bool masked = (flags[e % nn] >> f) & 1u;
@@ -1059,44 +1194,109 @@ __global__ void k_cg_init(long long n, unsigned long long seed, const unsigned c
     const Real zz = dinv[e] * Real(v);
     z[e] = zz;
     pv[e] = zz;
+    const double q = (double)Real(v) * (double)zz;
+    if (e < nu) s0 += q;
+    else s1 += q;
+  }
+  double r0, r1;
+  if (cg_reduce_last(s0, s1, part, reinterpret_cast<unsigned*>(scal + 12), r0, r1) && threadIdx.x == 0) {
+    scal[0] = r0;
+    scal[1] = r1;
   }
 }
+
+// <p, Ap> of both blocks, then alpha = rz / pAp (a block whose recurrence broke down stays dead).
 template <typename Real>
-cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags, int dim,
-                           long long nn, const Real* dinv, Real* r, Real* z, Real* pv, cudaStream_t s) {
-  (void)nu;
-  (void)dim;
-  long long g = (n + BLK - 1) / BLK;
-  if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_cg_init<Real><<<(unsigned)g, BLK, 0, s>>>(n, seed, flags, nn, dinv, r, z, pv);
-  return cudaGetLastError();
+__global__ void __launch_bounds__(BLK) k_cg_pap(long long n, long long nu, const Real* __restrict__ pv,
+                                                const Real* __restrict__ Ap, double* __restrict__ part,
+                                                double* __restrict__ scal, double* __restrict__ ah, int it,
+                                                int iters) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)pv[e] * (double)Ap[e];
+    if (e < nu) s0 += v;
+    else s1 += v;
+  }
+  double r0, r1;
+  if (cg_reduce_last(s0, s1, part, reinterpret_cast<unsigned*>(scal + 12), r0, r1) && threadIdx.x == 0) {
+    scal[2] = r0;
+    scal[3] = r1;
+    for (int b = 0; b < 2; ++b) {
+      const double rz = scal[b], pAp = scal[2 + b];
+      double al = 0.0;
+      if (scal[10 + b] == 0.0 && pAp > 0.0 && rz > 0.0 && pAp < 1e300) al = rz / pAp;
+      else scal[10 + b] = 1.0;
+      scal[4 + b] = al;
+      ah[b * iters + it] = al;
+    }
+  }
 }
 
+// r -= alpha Ap, z = D^{-1} r, Ap = 0 (the next apply accumulates into it), <r, z>, then
+// beta = rz_new / rz and rz = rz_new.
 template <typename Real>
-__global__ void k_cg_update(long long n, long long nu, const Real* __restrict__ Ap, const Real* __restrict__ dinv,
-                            const double* __restrict__ scal, Real* __restrict__ r, Real* __restrict__ z) {
+__global__ void __launch_bounds__(BLK) k_cg_update(long long n, long long nu, Real* __restrict__ Ap,
+                                                   const Real* __restrict__ dinv, double* __restrict__ scal,
+                                                   Real* __restrict__ r, Real* __restrict__ z, double* __restrict__ part,
+                                                   double* __restrict__ bh, int it, int iters) {
   const Real a0 = Real(scal[4]), a1 = Real(scal[5]);
+  double s0 = 0.0, s1 = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const Real al = e < nu ? a0 : a1;
     const Real rr = r[e] - al * Ap[e];
     r[e] = rr;
-    z[e] = dinv[e] * rr;
+    const Real zz = dinv[e] * rr;
+    z[e] = zz;
+    Ap[e] = Real(0);
+    const double q = (double)rr * (double)zz;
+    if (e < nu) s0 += q;
+    else s1 += q;
+  }
+  double r0, r1;
+  if (cg_reduce_last(s0, s1, part, reinterpret_cast<unsigned*>(scal + 12), r0, r1) && threadIdx.x == 0) {
+    scal[8] = r0;
+    scal[9] = r1;
+    for (int b = 0; b < 2; ++b) {
+      const double rzn = scal[8 + b], rz = scal[b];
+      double be = 0.0;
+      if (scal[10 + b] == 0.0) {
+        be = rzn / rz;
+        if (!(rzn > 0.0)) scal[10 + b] = 1.0;
+      }
+      scal[6 + b] = be;
+      bh[b * iters + it] = be;
+      scal[b] = rzn;
+    }
   }
 }
-template <typename Real>
-cudaError_t launch_cg_update(long long n, long long nu, const Real* Ap, const Real* dinv, const double* scal, Real* r,
-                             Real* z, cudaStream_t s) {
-  long long g = (n + BLK - 1) / BLK;
-  if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_cg_update<Real><<<(unsigned)g, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z);
-  return cudaGetLastError();
-}
+
 template <typename Real>
 __global__ void k_cg_pupdate(long long n, long long nu, const Real* __restrict__ z, const double* __restrict__ scal,
                              Real* __restrict__ pv) {
   const Real b0 = Real(scal[6]), b1 = Real(scal[7]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     pv[e] = z[e] + (e < nu ? b0 : b1) * pv[e];
+}
+
+template <typename Real>
+cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags,
+                           long long nn, const Real* dinv, Real* r, Real* z, Real* pv, double* part, double* scal,
+                           cudaStream_t s) {
+  count_launch(); k_cg_init<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, seed, flags, nn, dinv, r, z, pv, part, scal);
+  return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_cg_pap(long long n, long long nu, const Real* pv, const Real* Ap, double* part, double* scal,
+                          double* alpha_hist, int it, int iters, cudaStream_t s) {
+  count_launch(); k_cg_pap<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, pv, Ap, part, scal, alpha_hist, it, iters);
+  return cudaGetLastError();
+}
+template <typename Real>
+cudaError_t launch_cg_update(long long n, long long nu, Real* Ap, const Real* dinv, double* scal, Real* r, Real* z,
+                             double* part, double* beta_hist, int it, int iters, cudaStream_t s) {
+  count_launch();
+  k_cg_update<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z, part, beta_hist, it, iters);
+  return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const double* scal, Real* pv, cudaStream_t s) {
@@ -1105,65 +1305,55 @@ cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const do
   count_launch(); k_cg_pupdate<Real><<<(unsigned)g, BLK, 0, s>>>(n, nu, z, scal, pv);
   return cudaGetLastError();
 }
-#define PFF_INST_CG(R)                                                                                          \
-  template cudaError_t launch_cg_init<R>(long long, long long, unsigned long long, const unsigned char*, int,   \
-                                         long long, const R*, R*, R*, R*, cudaStream_t);                       \
-  template cudaError_t launch_cg_update<R>(long long, long long, const R*, const R*, const double*, R*, R*,     \
-                                           cudaStream_t);                                                      \
+#define PFF_INST_CG(R)                                                                                           \
+  template cudaError_t launch_cg_init<R>(long long, long long, unsigned long long, const unsigned char*,         \
+                                         long long, const R*, R*, R*, R*, double*, double*, cudaStream_t);      \
+  template cudaError_t launch_cg_pap<R>(long long, long long, const R*, const R*, double*, double*, double*, int, \
+                                        int, cudaStream_t);                                                     \
+  template cudaError_t launch_cg_update<R>(long long, long long, R*, const R*, double*, R*, R*, double*, double*, \
+                                           int, int, cudaStream_t);                                             \
   template cudaError_t launch_cg_pupdate<R>(long long, long long, const R*, const double*, R*, cudaStream_t);
 PFF_INST_CG(double)
 PFF_INST_CG(float)
 #undef PFF_INST_CG
 
-// scal: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1]
-__global__ void k_cg_scalars(int phase, int it, int iters, double* scal, double* ah, double* bh) {
-  const int b = threadIdx.x;
-  if (b >= 2) return;
-  double* dead = scal + 10;
-  if (phase == 0) {
-    const double rz = scal[b], pAp = scal[2 + b];
-    double al = 0.0;
-    if (dead[b] == 0.0 && pAp > 0.0 && rz > 0.0 && pAp < 1e300) al = rz / pAp;
-    else dead[b] = 1.0;
-    scal[4 + b] = al;
-    ah[b * iters + it] = al;
-  } else {
-    const double rzn = scal[8 + b], rz = scal[b];
-    double be = 0.0;
-    if (dead[b] == 0.0) {
-      be = rzn / rz;
-      if (!(rzn > 0.0)) dead[b] = 1.0;
-    }
-    scal[6 + b] = be;
-    bh[b * iters + it] = be;
-    scal[b] = rzn;
-  }
+// lambda_max of the Lanczos tridiagonal by multisection with Sturm counts. The counts run in
+// double-word arithmetic on the FP32 pipe (a full warp of FP64 divisions costs tens of times more
+// on this GPU): the matrix is first scaled by a power of two so that its Gershgorin interval lies
+// in [-1, 1], which keeps every quantity far inside the FP32 exponent range; the pivots d_j carry
+// about 44 significant bits, so the bracket still closes to about 1e-13 relative.
+__device__ __forceinline__ df64 df_div(df64 x, df64 y) {
+  const float th = __fdiv_rn(x.hi, y.hi);
+  float ph, pl;
+  ph = __fmul_rn(y.hi, th);
+  pl = __fmaf_rn(y.hi, th, -ph);
+  pl = __fmaf_rn(y.lo, th, pl);
+  const df64 r = x - df_make(ph, pl);
+  const float tl = __fdiv_rn(r.hi, y.hi);
+  float zh, zl;
+  fast_two_sum(th, tl, zh, zl);
+  return df_make(zh, zl);
 }
-cudaError_t launch_cg_scalars(int phase, int it, int iters, double* scal, double* alpha_hist, double* beta_hist,
-                              cudaStream_t s) {
-  count_launch(); k_cg_scalars<<<1, 32, 0, s>>>(phase, it, iters, scal, alpha_hist, beta_hist);
-  return cudaGetLastError();
-}
-
-// lambda_max / lambda_min of the Lanczos tridiagonal by bisection with Sturm counts.
-__device__ int sturm_count(int k, const double* a, const double* b2, double x) {
+// Number of eigenvalues below x of the tridiagonal (a, b2 = squared off-diagonals), all scaled.
+__device__ int sturm_count_df(int k, const df64* a, const df64* b2, df64 x) {
   int cnt = 0;
-  double d = a[0] - x;
-  if (d < 0.0) ++cnt;
+  df64 d = a[0] - x;
+  if (d.hi < 0.f) ++cnt;
   for (int j = 1; j < k; ++j) {
-    if (d == 0.0) d = 1e-300;
-    d = a[j] - x - b2[j - 1] / d;
-    if (d < 0.0) ++cnt;
+    if (fabsf(d.hi) < 1e-30f) d = df_make(d.hi < 0.f ? -1e-30f : 1e-30f, 0.f);  // keeps b2 / d finite
+    d = (a[j] - x) - df_div(b2[j - 1], d);
+    if (d.hi < 0.f) ++cnt;
   }
   return cnt;
 }
-// One warp per block b: the extreme eigenvalues of the Lanczos tridiagonal of the first k valid CG
-// steps, by multisection (each lane evaluates a Sturm count; the bracket shrinks 33-fold a round).
+// One warp per block b: the tridiagonal of the first k valid CG steps of block b, then
+// multisection (each lane evaluates a Sturm count; the bracket shrinks 33-fold a round).
 __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const double* __restrict__ bh,
                               double* __restrict__ lam) {
   const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (b >= 2) return;
   __shared__ double sa[2][64], sb2[2][64];
+  __shared__ df64 da[2][64], db2[2][64];
   __shared__ int sk[2];
   if (lane == 0) {
     int k = 0;
@@ -1180,8 +1370,6 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
   }
   __syncwarp();
   const int k = sk[b];
-  const double* a = sa[b];
-  const double* b2 = sb2[b];
   if (k == 0) {
     if (lane == 0) {
       lam[b] = 1.0;
@@ -1192,28 +1380,34 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
   double lo = 1e300, hi = -1e300;
   for (int j = 0; j < k; ++j) {
     double r = 0.0;
-    if (j > 0) r += sqrt(b2[j - 1]);
-    if (j + 1 < k) r += sqrt(b2[j]);
-    lo = fmin(lo, a[j] - r);
-    hi = fmax(hi, a[j] + r);
+    if (j > 0) r += sqrt(sb2[b][j - 1]);
+    if (j + 1 < k) r += sqrt(sb2[b][j]);
+    lo = fmin(lo, sa[b][j] - r);
+    hi = fmax(hi, sa[b][j] + r);
   }
-  // largest eigenvalue: the first point x with count(x) >= k (the smallest is not needed)
-  for (int which = 0; which < 1; ++which) {
-    const int target = k;
-    double l = lo, h = hi;
-    for (int round = 0; round < 12 && h - l > 1e-15 * fmax(fabs(l), fabs(h)); ++round) {
-      const double x = l + (h - l) * (lane + 1) / 33.0;
-      const unsigned ge = __ballot_sync(0xffffffffu, sturm_count(k, a, b2, x) >= target);
-      const int j = ge ? __ffs(ge) - 1 : 32;  // first lane whose point is at or above the eigenvalue
-      const double nl = j == 0 ? l : l + (h - l) * j / 33.0;
-      const double nh = j == 32 ? h : l + (h - l) * (j + 1) / 33.0;
-      l = nl;
-      h = nh;
-    }
-    if (lane == 0) {
-      lam[b] = h;
-      lam[2 + b] = lo;  // Gershgorin lower bound
-    }
+  // power-of-two scale s with max(|lo|, |hi|) * s in (0.5, 1]
+  int ex;
+  frexp(fmax(fabs(lo), fabs(hi)), &ex);
+  const double sc = ldexp(1.0, -ex);
+  for (int j = lane; j < k; j += 32) {
+    da[b][j] = df_from(sa[b][j] * sc);
+    if (j + 1 < k) db2[b][j] = df_from(sb2[b][j] * sc * sc);
+  }
+  __syncwarp();
+  // largest eigenvalue: the first point x with count(x) >= k
+  double l = lo * sc, h = hi * sc;
+  for (int round = 0; round < 12 && h - l > 1e-15 * fmax(fabs(l), fabs(h)); ++round) {
+    const double x = l + (h - l) * (lane + 1) / 33.0;
+    const unsigned ge = __ballot_sync(0xffffffffu, sturm_count_df(k, da[b], db2[b], df_from(x)) >= k);
+    const int j = ge ? __ffs(ge) - 1 : 32;  // first lane whose point is at or above the eigenvalue
+    const double nl = j == 0 ? l : l + (h - l) * j / 33.0;
+    const double nh = j == 32 ? h : l + (h - l) * (j + 1) / 33.0;
+    l = nl;
+    h = nh;
+  }
+  if (lane == 0) {
+    lam[b] = h / sc;
+    lam[2 + b] = lo;  // Gershgorin lower bound
   }
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
@@ -1227,8 +1421,19 @@ __global__ void k_inv_diag(long long n, const double* __restrict__ d, double* __
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const double v = 1.0 / d[e];
     di64[e] = v;
-    di32[e] = (float)v;
+    if (di32) di32[e] = (float)v;
   }
+}
+__global__ void k_inv_diag32(long long n, const float* __restrict__ d, float* __restrict__ di32) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    di32[e] = 1.0f / d[e];
+}
+cudaError_t launch_inv_diag32(long long n, const float* d, float* di32, cudaStream_t s) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > 152 * 16) g = 152 * 16;
+  if (g < 1) g = 1;
+  count_launch(); k_inv_diag32<<<(unsigned)g, BLK, 0, s>>>(n, d, di32);
+  return cudaGetLastError();
 }
 cudaError_t launch_inv_diag(long long n, const double* d, double* di64, float* di32, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;

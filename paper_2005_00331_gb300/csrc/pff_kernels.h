@@ -14,9 +14,11 @@ struct MatConst {
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
                             const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
                             const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s);
-// diag(G_uu, G_phiphi) of a level into d64 (zeroed here), masked rows set to 1; FP32 copy if d32.
-cudaError_t launch_diagonal(int dim, int p, int split, const double* qp64, const unsigned char* flags,
-                            const Geom& g, const Tab<double>& tb, double* d64, float* d32, cudaStream_t s);
+// diag(G_uu, G_phiphi) of a level into d (zeroed here), masked rows set to 1, from the per-point
+// data of the same precision.
+template <typename Real>
+cudaError_t launch_diagonal(int dim, int p, int split, const Real* qp, const unsigned char* flags, const Geom& g,
+                            const Tab<Real>& tb, Real* d, cudaStream_t s);
 // (dR/dparam)^T v, three nodal outputs (zeroed here); tmp has 3 * n_cells * n^dim doubles.
 cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const double* v, const double* st64,
                               const Geom& g, const Tab<double>& tb, const MatConst& mc, double* tmp,
@@ -25,10 +27,14 @@ cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const 
 cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64, const unsigned char* flags,
                                    const Geom& g, const Tab<double>& tb, double* Au, double* Ap, double* B,
                                    cudaStream_t s);
-// In-place Gauss-Jordan inverse of an n x n matrix (no pivoting; SPD input); buf: 4n doubles.
-cudaError_t launch_gj_inverse(double* A, int n, double* buf, cudaStream_t s);
+// In-place Gauss-Jordan inverse of an n x n matrix (no pivoting; SPD input), blocked;
+// buf: gj_buffer_size(n) elements of the matrix type.
+long long gj_buffer_size(int n);
+template <typename Real>
+cudaError_t launch_gj_inverse(Real* A, int n, Real* buf, cudaStream_t s);
 // y = A x (dense, row major, n rows, m cols); y = beta * y + alpha * A x.
-cudaError_t launch_gemv(const double* A, int n, int m, const double* x, double* y, double alpha, double beta,
+template <typename Real>
+cudaError_t launch_gemv(const Real* A, int n, int m, const Real* x, Real* y, double alpha, double beta,
                         cudaStream_t s);
 
 // Transfer tables of one degree (fine/coarse pair with ratio 2).
@@ -57,6 +63,9 @@ cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, u
 // ---- vectors ---------------------------------------------------------------------------
 template <typename Real>
 cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y, cudaStream_t s);
+// res = r - t; t = 0.
+template <typename Real>
+cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, cudaStream_t s);
 template <typename Ti, typename To>
 cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s);
 // Two-block dot products of x and y over [0, nu) and [nu, n): result res[0], res[1] (device, FP64).
@@ -80,26 +89,33 @@ cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, cons
                         Real* d, Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
                         cudaStream_t s);
 // CG-Lanczos on the two diagonal blocks (vectors in the multigrid precision, scalars in FP64).
+// scal holds 16 doubles: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1], then a
+// reduction counter that must be zero before the first call (every call leaves it zero); part holds
+// 2 * 304 doubles. The histories are [2][iters].
+// r = random start (0 on masked rows), z = pv = D^{-1} r, rz = <r, z>.
 template <typename Real>
 cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags,
-                           int dim, long long nn, const Real* dinv, Real* r, Real* z, Real* pv, cudaStream_t s);
+                           long long nn, const Real* dinv, Real* r, Real* z, Real* pv, double* part, double* scal,
+                           cudaStream_t s);
+// pAp = <p, Ap>, alpha = rz / pAp -> alpha_hist[.][it].
 template <typename Real>
-cudaError_t launch_cg_update(long long n, long long nu, const Real* Ap, const Real* dinv, const double* scal,
-                             Real* r, Real* z, cudaStream_t s);
+cudaError_t launch_cg_pap(long long n, long long nu, const Real* pv, const Real* Ap, double* part, double* scal,
+                          double* alpha_hist, int it, int iters, cudaStream_t s);
+// r -= alpha Ap, z = D^{-1} r, Ap = 0, beta = <r, z> / rz -> beta_hist[.][it], rz = <r, z>.
+template <typename Real>
+cudaError_t launch_cg_update(long long n, long long nu, Real* Ap, const Real* dinv, double* scal, Real* r, Real* z,
+                             double* part, double* beta_hist, int it, int iters, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const double* scal, Real* pv,
-                              cudaStream_t s);
-// scalar bookkeeping (single thread): phase 0 after <p,Ap>: alpha = rz/pAp; phase 1 after <r,z>_new:
-// beta = rz_new/rz, rz = rz_new. scal layout: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1
-// dead0 dead1]; the histories are [2][iters].
-cudaError_t launch_cg_scalars(int phase, int it, int iters, double* scal, double* alpha_hist, double* beta_hist,
                               cudaStream_t s);
 // lam_max[b] from the Lanczos tridiagonal of the first k_valid CG steps of each block.
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
                                cudaStream_t s);
 
-// di = 1 / d (FP64 and FP32 copies): the Jacobi scaling of the smoother.
+// di = 1 / d (FP64 and, when di32 is not null, FP32 copies): the Jacobi scaling of the smoother.
 cudaError_t launch_inv_diag(long long n, const double* d, double* di64, float* di32, cudaStream_t s);
+// di32 = 1 / d (FP32 diagonal of the FP32 multigrid).
+cudaError_t launch_inv_diag32(long long n, const float* d, float* di32, cudaStream_t s);
 
 // ---- Newton step helpers ----------------------------------------------------------------
 // Active set of Alg. 1 on the phase-field block: sets/clears the active bit (field dim), resets

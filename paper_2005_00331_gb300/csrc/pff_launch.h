@@ -11,6 +11,28 @@ void count_launch();
 void add_launches(long long n);
 long long launch_count();
 
+#ifndef PFF_PDL
+#define PFF_PDL 1
+#endif
+// Launch with programmatic stream serialisation (the kernel must begin with pdl_wait()); inside a
+// captured graph this becomes a programmatic edge, so the launch work of the kernel overlaps the
+// tail of its predecessor.
+template <typename... KP, typename... A>
+inline cudaError_t launch_k(void (*k)(KP...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+  count_launch();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = PFF_PDL;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KP>(args)...);
+}
+
 // y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be
 // zeroed by the caller (seam nodes are accumulated atomically). mode: JM_*; masks: In/OutMask.
 // With ce != nullptr (2D only) the block-diagonal apply finishes a Chebyshev step on the nodes of a
@@ -23,7 +45,7 @@ cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, cons
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
                        cudaStream_t s, const ChebEpi<float>* ce = nullptr);
 template <typename Store>
-cudaError_t launch_cheb_seam(const Geom& g, const Store* y, const ChebEpi<Store>& ce, cudaStream_t s);
+cudaError_t launch_cheb_seam(const Geom& g, Store* y, const ChebEpi<Store>& ce, cudaStream_t s);
 cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
                           cudaStream_t s, const ChebEpi<double>* ce);

@@ -10,6 +10,8 @@
 // atomics into an output the caller has zeroed. Rows masked on output (Dirichlet DoFs, the
 // active set) are written once, by the tile that owns the node.
 #pragma once
+#include <type_traits>
+
 #include "pff_common.cuh"
 #include "pff_df64.cuh"
 
@@ -212,7 +214,7 @@ __device__ __forceinline__ void cells_of_node(int r, int T, int& lo, int& hi) {
 // contractions of the cells sharing each node of the patch.
 template <int P>
 struct Tile2 {
-  static constexpr int TX = 8, TY = (P == 1 ? 16 : (P == 2 ? 8 : 4));
+  static constexpr int TX = TileCfg<2, P>::TX, TY = TileCfg<2, P>::TY;
   static constexpr int n = P + 1, NPX = TX * P + 1, NPY = TY * P + 1, QPX = TX * n, QPY = TY * n;
   static constexpr int NT = QPX * TY;
 };
@@ -403,9 +405,11 @@ constexpr size_t op2d_smem() {
 
 // ===========================================================================================
 // 2D Jacobian kernel, persistent and staged: each CTA walks tiles blockIdx.x, +gridDim.x, ... and
-// copies the next tile's node patch and per-point data into shared memory with cp.async while it
-// computes the current tile (NSTAGE = 2; with NSTAGE = 1 the copy for the next tile overlaps the
-// store phase only). The arithmetic is that of k_op2d.
+// copies the next tile's node patch and per-point data into shared memory with cp.async (with
+// NSTAGE = 2 under the whole computation of the current tile; with NSTAGE = 1 under its store phase,
+// which halves the shared memory per CTA: on GB300 the extra resident CTAs hide more latency than
+// the second stage, 0.199 vs 0.244 ms for the FP32 2D Q2 apply at 1024^2 cells). The arithmetic is
+// that of k_op2d.
 __device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, bool valid, int bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   if (bytes == 4)
@@ -425,13 +429,14 @@ __device__ __forceinline__ void cp_async_wait() {
 
 template <int P, typename Real>
 struct Stage2 {
-  static constexpr int NSTAGE = sizeof(Real) == 4 ? 2 : 1;
+  static constexpr int NSTAGE = 1;  // kept as a parameter: the kernel supports 2
 };
 
 template <int P, typename Real, typename Store, int SPLIT>
 __global__ void __launch_bounds__(Tile2<P>::NT)
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
               Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce) {
+  pdl_wait();
   using T = Tile2<P>;
   constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
   constexpr int NPX = T::NPX, NPY = T::NPY, QPX = T::QPX;
@@ -667,9 +672,11 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   cp_async_wait<0>();
 }
 
-// The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete.
+// The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete; y is
+// reset to 0 there, so y is all zero again afterwards (the fused applies write no other entry).
 template <typename Store>
-__global__ void k_cheb_seam2(Geom g, int tpx, int tpy, const Store* __restrict__ y, ChebEpi<Store> ce) {
+__global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, ChebEpi<Store> ce) {
+  pdl_wait();
   const long long nv = (long long)(g.ntile[0] - 1) * g.n1, nh = (long long)(g.ntile[1] - 1) * g.n1;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= nv + nh) return;
@@ -696,6 +703,7 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, const Store* __restrict__
     const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y[gi]));
     ce.d[gi] = dn;
     ce.x[gi] = ce.x[gi] + dn;
+    y[gi] = Store(0);
   }
 }
 
@@ -725,6 +733,7 @@ template <int P, typename Real, typename Store, class PW>
 __global__ void __launch_bounds__(Tile3<P>::NT)
 k_op3d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
        Geom g, Tab<Real> tb, PW pw, OpArgs oa) {
+  pdl_wait();
   using T = Tile3<P>;
   constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, n = T::n, NF = 4;
   constexpr int NPX = T::NPX, NPY = T::NPY, NPZ = T::NPZ, QPX = T::QPX, QPY = T::QPY;

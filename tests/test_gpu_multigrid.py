@@ -33,6 +33,18 @@ def oracle_levels(pr, cheb_degree=5):
 
 
 @pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_fp32_multigrid_diagonal(dim, p, N, split):
+    """With the FP32 multigrid the Jacobi diagonal is computed in FP32 from the FP32 per-point data;
+    the FP64 diagonal is still available on request."""
+    pr = Problem(dim, p, N, split=split, seed=3, active_frac=0.25)
+    lv = oracle_levels(pr)
+    ctx = pr.context(mg_precision=32)
+    for l, L in enumerate(lv):
+        assert rel(ctx.diagonal(l, precision=32).cpu().numpy().astype(np.float64), L.diag) <= 2e-6
+        assert rel(ctx.diagonal(l).cpu().numpy(), L.diag) <= 1e-12
+
+
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
 def test_levels_diagonal_transfers(dim, p, N, split):
     pr = Problem(dim, p, N, split=split, seed=3, active_frac=0.25)
     lv = oracle_levels(pr)
