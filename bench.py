@@ -73,6 +73,39 @@ def workload_name(a):
         "FP32 (mixed)" if a.mg_precision == 32 else "FP64")
 
 
+# ---- measured DRAM traffic of the roofline kernel (from a committed ncu summary) --------------
+TRAFFIC_SOURCES = ("pff_op.cuh", "pff_common.cuh", "pff_df64.cuh", "op_jac2_f32.cu", "op_jac3_f32.cu")
+
+
+def kernel_source_hash():
+    """sha256 over the sources of the FP32 Jacobian kernels: a traffic record counts only for them."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2005_00331_gb300", "csrc")
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(a, n_dofs):
+    """dram__bytes_read + dram__bytes_write per launch of the FP32 finest-level apply, from a
+    'traffic-record:' line of a profiles/*.md summary with the same kernel sources and workload
+    family (scaled by DoFs); None when no record matches the current kernel."""
+    import glob
+    want = {"dim": str(a.dim), "degree": str(a.degree), "split": str(a.split), "source": kernel_source_hash()}
+    here = os.path.dirname(os.path.abspath(__file__))
+    for fn in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
+        with open(fn) as fh:
+            for ln in fh:
+                if not ln.strip().startswith("traffic-record:"):
+                    continue
+                kv = dict(x.split("=", 1) for x in ln.split(":", 1)[1].split() if "=" in x)
+                if all(kv.get(k) == v for k, v in want.items()):
+                    return float(kv["bytes"]) * n_dofs / float(kv["dofs"])
+    return None
+
+
 # ---- synthetic state (inputs module + the library's own node flags) -------------------------
 def make_state(ctx, a, seed=0):
     import torch
@@ -588,7 +621,8 @@ def main():
         "roofline": {"kernel": "%s Jacobian apply, FP%d, finest level, inside the timed steps" % (
             "k_jac2_staged" if a.dim == 2 else "k_op3d", real_bytes * 8),
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None,
+                     "traffic": measured_traffic(a, r["n_dofs"]) if a.mg_precision == 32 else None,
                      "peak_kind": hbm_kind, "launches": r["kern_launches"], "avg_launch_ms": per_launch,
                      "bytes_per_dof": bpd},
         "e2e": {"value": r["n_dofs"] * world / r["e2e_s"], "unit": "DoF/s", "h2d_bytes_per_step": r["h2d"],

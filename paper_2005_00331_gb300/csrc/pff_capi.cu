@@ -329,6 +329,10 @@ template <> const Tab<double>& tab_of<double>(LevelData& L) { return L.t64; }
 template <> const Tab<float>& tab_of<float>(LevelData& L) { return L.t32; }
 template <typename Real> Real* dinv_of(LevelData& L);
 template <> double* dinv_of<double>(LevelData& L) { return L.di64; }
+// 1 / lambda_max of the two blocks in the given precision (written by the eigenvalue estimate)
+template <typename Real> const Real* inv_lam_of(LevelData& L);
+template <> const double* inv_lam_of<double>(LevelData& L) { return L.lam + 4; }
+template <> const float* inv_lam_of<float>(LevelData& L) { return reinterpret_cast<const float*>(L.lam + 6); }
 template <> float* dinv_of<float>(LevelData& L) { return L.di32; }
 template <typename Real> Real** work_of(LevelData& L);
 template <> double** work_of<double>(LevelData& L) { return L.w64; }
@@ -670,7 +674,9 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
   const double lo = c->prm.cheb_lo, hi = c->prm.cheb_hi;
   const double sigma = (hi + lo) / (hi - lo);
   double rho = 1.0 / sigma;
-  CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, L.lam, lo, hi, 0.0, 0.0, c->s));
+  const Real* il = inv_lam_of<Real>(L);
+  // theta_b = (hi + lo) lambda_b / 2, delta_b = (hi - lo) lambda_b / 2
+  CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, il, 2.0 / (hi + lo), 0.0, 0.0, c->s));
   for (int k = 1; k < c->prm.cheb_degree; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     if (c->dim == 2) {
@@ -680,18 +686,17 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
       ce.dinv = dinv_of<Real>(L);
       ce.d = dv;
       ce.x = x;
-      ce.lam_max = L.lam;
-      ce.lo = lo;
-      ce.hi = hi;
+      ce.inv_lam = il;
       ce.c1 = rho_new * rho;
-      ce.rho_k = rho_new;
+      ce.c2s = 4.0 * rho_new / (hi - lo);
       ce.on = 1;
       // t is all zero on entry (work vectors start zeroed; every use below leaves it zeroed)
       CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce, true));
       CK(launch_cheb_seam<Real>(L.g, t, ce, c->s));
     } else {
       CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
-      CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, L.lam, lo, hi, rho_new * rho, rho_new, c->s));
+      CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, il, 0.0, rho_new * rho, 4.0 * rho_new / (hi - lo),
+                           c->s));
     }
     rho = rho_new;
   }
@@ -1011,7 +1016,7 @@ static int setup_impl(pff_ctx* c) {
     CR(dalloc(c, &L.di64, L.nd));
     CR(dalloc(c, &L.d32, L.nd));
     CR(dalloc(c, &L.di32, L.nd));
-    CR(dalloc(c, &L.lam, 4));
+    CR(dalloc(c, &L.lam, 8));
     CR(dalloc(c, &L.lscal, 16));
     CR(dalloc(c, &L.lhist, 4 * P.eig_iters));
     CR(dalloc(c, &L.lpart, 2 * 152 * 2));

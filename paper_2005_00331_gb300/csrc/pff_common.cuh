@@ -85,14 +85,17 @@ struct Geom {
 // only this tile touches, y = (G x)_i is final in registers, so the update
 //   d_i <- c1 d_i + (2 rho_k / delta_b) dinv_i (f_i - y_i),   x_i <- x_i + d_i
 // is done in place and y_i is never stored; seam nodes go through y and k_cheb_seam afterwards.
+// With delta_b = (hi - lo) lambda_b / 2 the coefficient is c2s / lambda_b, c2s = 4 rho_k / (hi - lo)
+// from the host and 1 / lambda_b from the device (inv_lam, 0 for an unusable estimate): no division
+// (and, for FP32, no FP64 arithmetic) in the kernels.
 template <typename Store>
 struct ChebEpi {
   const Store* f;
   const Store* dinv;
   Store* d;
   Store* x;
-  const double* lam_max;  // [2]: u block, phi block
-  double lo, hi, c1, rho_k;
+  const Store* inv_lam;  // [2]: 1 / lambda_max of the u block and of the phi block
+  double c1, c2s;
   int on;
 };
 

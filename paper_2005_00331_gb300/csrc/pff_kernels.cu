@@ -663,14 +663,22 @@ template cudaError_t launch_gemv<float>(const float*, int, int, const float*, fl
 
 // ===========================================================================================
 // Transfers between a coarse level (Nc cells) and its fine level (2 Nc cells), same degree.
+// The 1D tables live in shared memory in the vector precision: indexed per thread (the fine offset and
+// the coarse local node differ across a warp), they would be divergent constant-bank reads as kernel
+// parameters, and double entries would need conversions on the FP64 pipe.
 template <int DIM, int P, typename Real>
 __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, const unsigned char* __restrict__ flf,
                           Geom gc, Geom gf, XferTab xt, int accumulate) {
+  constexpr int NO = 2 * P + 1, NK = P + 1;
+  __shared__ Real E[NO][NK];
+  for (int i = threadIdx.x; i < NO * NK; i += blockDim.x) E[i / NK][i % NK] = Real(xt.E[i / NK][i % NK]);
   pdl_wait();
+  __syncthreads();
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gf.nn) return;
   long long rem = nd;
   int C[3] = {0, 0, 0}, o[3] = {0, 0, 0};
+#pragma unroll
   for (int t = 0; t < DIM; ++t) {
     const int i = int(rem % gf.n1);
     rem /= gf.n1;
@@ -679,90 +687,96 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
     C[t] = c;
     o[t] = i - 2 * P * c;
   }
+  Real wx[NK], wy[NK], wz[NK];
+#pragma unroll
+  for (int k = 0; k < NK; ++k) {
+    wx[k] = E[o[0]][k];
+    wy[k] = E[o[1]][k];
+    wz[k] = DIM == 3 ? E[o[2]][k] : Real(1);
+  }
   const unsigned char fl = flf[nd];
+  const long long cbase = (long long)C[0] * P + (long long)gc.n1 * (C[1] * P + (DIM == 3 ? (long long)gc.n1 * C[2] * P : 0));
+#pragma unroll
   for (int f = 0; f <= DIM; ++f) {
     Real v = Real(0);
     if (!((fl >> f) & 1u)) {
-      if constexpr (DIM == 2) {
-        for (int ky = 0; ky <= P; ++ky) {
-          const Real wy = Real(xt.E[o[1]][ky]);
-          if (wy == Real(0)) continue;
-          const Real* row = xc + f * gc.nn + (long long)(C[1] * P + ky) * gc.n1 + C[0] * P;
+      const Real* xb = xc + f * gc.nn + cbase;
+#pragma unroll
+      for (int kz = 0; kz < (DIM == 3 ? NK : 1); ++kz)
+#pragma unroll
+        for (int ky = 0; ky < NK; ++ky) {
+          const Real* row = xb + (long long)ky * gc.n1 + (DIM == 3 ? (long long)kz * gc.n1 * gc.n1 : 0);
           Real sx = Real(0);
-          for (int kx = 0; kx <= P; ++kx) sx += Real(xt.E[o[0]][kx]) * row[kx];
-          v += wy * sx;
+#pragma unroll
+          for (int kx = 0; kx < NK; ++kx) sx += wx[kx] * row[kx];
+          v += wz[kz] * wy[ky] * sx;
         }
-      } else {
-        for (int kz = 0; kz <= P; ++kz) {
-          const Real wz = Real(xt.E[o[2]][kz]);
-          if (wz == Real(0)) continue;
-          for (int ky = 0; ky <= P; ++ky) {
-            const Real wy = Real(xt.E[o[1]][ky]);
-            if (wy == Real(0)) continue;
-            const Real* row = xc + f * gc.nn + ((long long)(C[2] * P + kz) * gc.n1 + (C[1] * P + ky)) * gc.n1 + C[0] * P;
-            Real sx = Real(0);
-            for (int kx = 0; kx <= P; ++kx) sx += Real(xt.E[o[0]][kx]) * row[kx];
-            v += wz * wy * sx;
-          }
-        }
-      }
     }
     Real* y = yf + f * gf.nn + nd;
     *y = accumulate ? *y + v : v;
   }
 }
 
+// Restriction = transpose of the prolongation. Per direction, the fine nodes that see coarse node J
+// (J = P c + k, 0 <= k < P) lie at fine offsets o in [-2P, 2P] from the first fine node 2P c of coarse
+// cell c, with weight W[k][o + 2P]: E[o][k] for o >= 0 and, for a vertex (k = 0), E[o + 2P][P] from
+// the cell on the left for o < 0.
 template <int DIM, int P, typename Real>
 __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
                            const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine) {
+  constexpr int NW = 4 * P + 1;
+  __shared__ Real W[P][NW];
+  for (int i = threadIdx.x; i < P * NW; i += blockDim.x) {
+    const int k = i / NW, o = i % NW - 2 * P;
+    W[k][i % NW] = o >= 0 ? Real(xt.E[o][k]) : (k == 0 ? Real(xt.E[o + 2 * P][P]) : Real(0));
+  }
   pdl_wait();
+  __syncthreads();
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gc.nn) return;
-  constexpr int MAXL = 2 * (2 * P + 1);
-  int fi[3][MAXL];
-  Real fw[3][MAXL];
-  int cnt[3] = {0, 0, 0};
   long long rem = nd;
+  int b[3] = {0, 0, 0}, kk[3] = {0, 0, 0};
+#pragma unroll
   for (int t = 0; t < DIM; ++t) {
     const int J = int(rem % gc.n1);
     rem /= gc.n1;
-    int clo = (J % P == 0) ? J / P - 1 : J / P, chi = J / P;
-    if (clo < 0) clo = 0;
-    if (chi > gc.N - 1) chi = gc.N - 1;
-    for (int c = clo; c <= chi; ++c) {
-      const int k = J - c * P;
-      for (int o = 0; o <= 2 * P; ++o) {
-        if (o == 2 * P && c != gc.N - 1) continue;  // owned by the next coarse cell
-        const double w = xt.E[o][k];
-        if (w == 0.0) continue;
-        fi[t][cnt[t]] = 2 * P * c + o;
-        fw[t][cnt[t]] = Real(w);
-        ++cnt[t];
-      }
-    }
+    const int c = J / P;
+    kk[t] = J - P * c;
+    b[t] = 2 * P * c;
   }
   const unsigned char fc = flc[nd];
-  for (int f = 0; f <= DIM; ++f) {
-    Real v = Real(0);
-    if (!((fc >> f) & 1u)) {
-      if constexpr (DIM == 2) {
-        for (int b = 0; b < cnt[1]; ++b)
-          for (int a = 0; a < cnt[0]; ++a) {
-            const long long fn = fi[0][a] + (long long)gf.n1 * fi[1][b];
-            if (!mask_fine || !((flf[fn] >> f) & 1u)) v += fw[0][a] * fw[1][b] * xf[f * gf.nn + fn];
-          }
-      } else {
-        for (int c = 0; c < cnt[2]; ++c)
-          for (int b = 0; b < cnt[1]; ++b)
-            for (int a = 0; a < cnt[0]; ++a) {
-              const long long fn = fi[0][a] + (long long)gf.n1 * (fi[1][b] + (long long)gf.n1 * fi[2][c]);
-              if (!mask_fine || !((flf[fn] >> f) & 1u))
-                v += fw[0][a] * fw[1][b] * fw[2][c] * xf[f * gf.nn + fn];
-            }
+  Real acc[DIM + 1];
+#pragma unroll
+  for (int f = 0; f <= DIM; ++f) acc[f] = Real(0);
+#pragma unroll
+  for (int oz = 0; oz < (DIM == 3 ? NW : 1); ++oz) {
+    const int iz = DIM == 3 ? b[2] + oz - 2 * P : 0;
+    if (DIM == 3 && (iz < 0 || iz >= gf.n1)) continue;
+    const Real w3 = DIM == 3 ? W[kk[2]][oz] : Real(1);
+    if (w3 == Real(0)) continue;
+#pragma unroll
+    for (int oy = 0; oy < NW; ++oy) {
+      const int iy = b[1] + oy - 2 * P;
+      if (iy < 0 || iy >= gf.n1) continue;
+      const Real w2 = w3 * W[kk[1]][oy];
+      if (w2 == Real(0)) continue;
+      const long long rowb = (long long)gf.n1 * (iy + (DIM == 3 ? (long long)gf.n1 * iz : 0));
+#pragma unroll
+      for (int ox = 0; ox < NW; ++ox) {
+        const int ix = b[0] + ox - 2 * P;
+        if (ix < 0 || ix >= gf.n1) continue;
+        const Real w = w2 * W[kk[0]][ox];
+        if (w == Real(0)) continue;
+        const long long fn = rowb + ix;
+        const unsigned char ff = mask_fine ? flf[fn] : 0;
+#pragma unroll
+        for (int f = 0; f <= DIM; ++f)
+          if (!((ff >> f) & 1u)) acc[f] += w * xf[f * gf.nn + fn];
       }
     }
-    yc[f * gc.nn + nd] = v;
   }
+#pragma unroll
+  for (int f = 0; f <= DIM; ++f) yc[f * gc.nn + nd] = ((fc >> f) & 1u) ? Real(0) : acc[f];
 }
 
 template <typename Real>
@@ -1073,50 +1087,20 @@ cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, d
 template <typename Real>
 __global__ void k_cheb(int step, long long n, long long nu, const Real* __restrict__ f, const Real* __restrict__ Ax,
                        const Real* __restrict__ dinv, Real* __restrict__ d, Real* __restrict__ x,
-                       const double* __restrict__ lam_max, double lo, double hi, double c1, double rho_k) {
+                       const Real* __restrict__ inv_lam, double c0s, double c1, double c2s) {
   pdl_wait();
-  const double l0 = lam_max[0], l1 = lam_max[1];
+  // step 0: d = dinv f / theta_b, 1 / theta_b = c0s / lambda_b; step k: d = c1 d + (c2s / lambda_b) dinv (f - Ax)
+  const Real i0 = inv_lam[0], i1 = inv_lam[1];
+  const Real a0 = Real(step == 0 ? c0s : c2s) * i0, a1 = Real(step == 0 ? c0s : c2s) * i1;
+  const Real cc = Real(c1);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const double lm = e < nu ? l0 : l1;
-    const double a = lo * lm, b = hi * lm;
-    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
-    const bool ok = lm > 0.0 && lm < 1e300;
+    const Real a = e < nu ? a0 : a1;
     if (step == 0) {
-      const Real de = ok ? Real((double)dinv[e] * (double)f[e] / theta) : Real(0);
+      const Real de = a * (dinv[e] * f[e]);
       d[e] = de;
       x[e] = de;
     } else {
-      const double r = (double)dinv[e] * ((double)f[e] - (double)Ax[e]);
-      const Real de = ok ? Real(c1 * (double)d[e] + (2.0 * rho_k / delta) * r) : Real(0);
-      d[e] = de;
-      x[e] += de;
-    }
-  }
-}
-template <>
-__global__ void k_cheb<float>(int step, long long n, long long nu, const float* __restrict__ f,
-                              const float* __restrict__ Ax, const float* __restrict__ dinv, float* __restrict__ d,
-                              float* __restrict__ x, const double* __restrict__ lam_max, double lo, double hi,
-                              double c1, double rho_k) {
-  pdl_wait();
-  __shared__ float coef[2][3];
-  if (threadIdx.x < 2) {
-    const double lm = lam_max[threadIdx.x];
-    const double a = lo * lm, b = hi * lm;
-    const bool ok = lm > 0.0 && lm < 1e300;
-    coef[threadIdx.x][0] = ok ? float(2.0 / (b + a)) : 0.0f;                  // 1 / theta
-    coef[threadIdx.x][1] = ok ? float(2.0 * rho_k / (0.5 * (b - a))) : 0.0f;  // 2 rho_k / delta
-    coef[threadIdx.x][2] = ok ? float(c1) : 0.0f;
-  }
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int bk = e < nu ? 0 : 1;
-    if (step == 0) {
-      const float de = dinv[e] * f[e] * coef[bk][0];
-      d[e] = de;
-      x[e] = de;
-    } else {
-      const float de = coef[bk][2] * d[e] + coef[bk][1] * (dinv[e] * (f[e] - Ax[e]));
+      const Real de = cc * d[e] + a * (dinv[e] * (f[e] - Ax[e]));
       d[e] = de;
       x[e] += de;
     }
@@ -1125,19 +1109,17 @@ __global__ void k_cheb<float>(int step, long long n, long long nu, const float* 
 
 template <typename Real>
 cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, const Real* Ax, const Real* dinv, Real* d,
-                        Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
-                        cudaStream_t s) {
+                        Real* x, const Real* inv_lam, double c0s, double c1, double c2s, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  return launch_k(k_cheb<Real>, dim3((unsigned)g), dim3(BLK), 0, s, step, n, nu, f, Ax, dinv, d, x, lam_max, lo, hi, c1,
-                  rho_k);
+  return launch_k(k_cheb<Real>, dim3((unsigned)g), dim3(BLK), 0, s, step, n, nu, f, Ax, dinv, d, x, inv_lam, c0s, c1,
+                  c2s);
 }
 template cudaError_t launch_cheb<double>(int, long long, long long, const double*, const double*, const double*,
-                                         double*, double*, const double*, double, double, double, double,
-                                         cudaStream_t);
+                                         double*, double*, const double*, double, double, double, cudaStream_t);
 template cudaError_t launch_cheb<float>(int, long long, long long, const float*, const float*, const float*, float*,
-                                        float*, const double*, double, double, double, double, cudaStream_t);
+                                        float*, const float*, double, double, double, cudaStream_t);
 
 // ---- CG-Lanczos -------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
@@ -1374,6 +1356,8 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
     if (lane == 0) {
       lam[b] = 1.0;
       lam[2 + b] = 1.0;
+      lam[4 + b] = 1.0;
+      reinterpret_cast<float*>(lam + 6)[b] = 1.0f;
     }
     return;
   }
@@ -1406,8 +1390,13 @@ __global__ void k_tridiag_eig(int iters, const double* __restrict__ ah, const do
     h = nh;
   }
   if (lane == 0) {
-    lam[b] = h / sc;
+    const double lm = h / sc;
+    lam[b] = lm;
     lam[2 + b] = lo;  // Gershgorin lower bound
+    // 1 / lambda_max for the smoother kernels (FP64 and FP32 copies); 0 disables the block's update
+    const double il = (lm > 0.0 && lm < 1e300) ? 1.0 / lm : 0.0;
+    lam[4 + b] = il;
+    reinterpret_cast<float*>(lam + 6)[b] = (float)il;
   }
 }
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,

@@ -83,11 +83,11 @@ cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y,
 cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s);
 
 // ---- Chebyshev-Jacobi and eigenvalue estimation -----------------------------------------
-// step 0: x = d = dinv f / theta_b; step k: d = c1 d + (2 rho_k / delta_b) dinv (f - Ax), x += d.
+// step 0: x = d = dinv f / theta_b; step k: d = c1 d + (2 rho_k / delta_b) dinv (f - Ax), x += d,
+// with 1 / theta_b = c0s inv_lam[b] and 2 rho_k / delta_b = c2s inv_lam[b] (inv_lam = 1 / lambda_max).
 template <typename Real>
 cudaError_t launch_cheb(int step, long long n, long long nu, const Real* f, const Real* Ax, const Real* dinv,
-                        Real* d, Real* x, const double* lam_max, double lo, double hi, double c1, double rho_k,
-                        cudaStream_t s);
+                        Real* d, Real* x, const Real* inv_lam, double c0s, double c1, double c2s, cudaStream_t s);
 // CG-Lanczos on the two diagonal blocks (vectors in the multigrid precision, scalars in FP64).
 // scal holds 16 doubles: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1], then a
 // reduction counter that must be zero before the first call (every call leaves it zero); part holds
@@ -108,7 +108,9 @@ cudaError_t launch_cg_update(long long n, long long nu, Real* Ap, const Real* di
 template <typename Real>
 cudaError_t launch_cg_pupdate(long long n, long long nu, const Real* z, const double* scal, Real* pv,
                               cudaStream_t s);
-// lam_max[b] from the Lanczos tridiagonal of the first k_valid CG steps of each block.
+// lam_max[b] from the Lanczos tridiagonal of the first k_valid CG steps of each block; lam holds 8
+// doubles: lam_max[2], Gershgorin lower bounds[2], 1 / lam_max[2] (0 if unusable), and the two FP32
+// inverses packed into lam[6].
 cudaError_t launch_tridiag_eig(int iters, const double* alpha_hist, const double* beta_hist, double* lam,
                                cudaStream_t s);
 

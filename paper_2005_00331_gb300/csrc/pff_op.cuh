@@ -432,8 +432,22 @@ struct Stage2 {
   static constexpr int NSTAGE = 1;  // kept as a parameter: the kernel supports 2
 };
 
+// Register budget per thread that keeps the CTAs resident which fit in shared memory (FP32 Q2: five
+// per SM; double-word Q2: two): FP32 64 up to Q2 and 96 above (64 would spill there), double-word 80
+// for Q1 and 168 for Q2/Q3; native FP64 and double-word Q4 unconstrained.
+template <int P, typename Real>
+constexpr int jac2_reg_budget() {
+  return std::is_same<Real, float>::value ? (P <= 2 ? 64 : 96)
+         : std::is_same<Real, df64>::value ? (P == 1 ? 80 : (P <= 3 ? 168 : 0))
+                                           : 0;
+}
+template <int P, typename Real>
+constexpr int jac2_min_blocks() {
+  return jac2_reg_budget<P, Real>() ? 65536 / (Tile2<P>::NT * jac2_reg_budget<P, Real>()) : 1;
+}
+
 template <int P, typename Real, typename Store, int SPLIT>
-__global__ void __launch_bounds__(Tile2<P>::NT)
+__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real>())
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
               Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce) {
   pdl_wait();
@@ -463,25 +477,28 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   // Chebyshev coefficients per block (field < 2: u block), in the storage precision
   Store ch_c1 = Store(0), ch_c2[2] = {Store(0), Store(0)};
   if (ce.on) {
-    for (int b = 0; b < 2; ++b) {
-      const double lm = ce.lam_max[b];
-      const double a = ce.lo * lm, bb = ce.hi * lm;
-      const bool ok = lm > 0.0 && lm < 1e300;
-      ch_c2[b] = Store(ok ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0);
-    }
+    ch_c2[0] = Store(ce.c2s) * ce.inv_lam[0];
+    ch_c2[1] = Store(ce.c2s) * ce.inv_lam[1];
     ch_c1 = Store(ce.c1);
   }
   const long long ntiles = g.ntiles;
+  // node phases (copy, masking, store): this thread handles patch nodes tid + k NT, all fields
+  constexpr int NNODE = NPY * NPX, NIT = (NNODE + NT - 1) / NT;
   auto prefetch = [&](long long tile, int st) {
     const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
     const int x0 = tix * TX * P, y0 = tiy * TY * P;
     Store* xs = Xs + st * XS;
-    for (int i = tid; i < XS; i += NT) {
-      const int s = i % NPX, r = (i / NPX) % NPY, f = i / (NPX * NPY);
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+      const int rs = tid + k * NT;
+      if (rs >= NNODE) break;
+      const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
       const bool ok = gx < g.n1 && gy < g.n1;
-      const long long gi = ok ? f * g.nn + gx + (long long)g.n1 * gy : 0;
-      cp_async_bytes(xs + i, src + gi, ok, (int)sizeof(Store));
+      const Store* sp = src + (ok ? gx + (long long)g.n1 * gy : 0);
+      Store* dp = xs + rs;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) cp_async_bytes(dp + f * NNODE, sp + (ok ? f * g.nn : 0), ok, (int)sizeof(Store));
     }
     const char* qsrc = reinterpret_cast<const char*>(qpg + tile * (long long)NV * QPT);
     char* qdst = reinterpret_cast<char*>(QPs + st * NV * QPT);
@@ -507,8 +524,11 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
     const int x0 = tix * TX * P, y0 = tiy * TY * P;
     // masked compute-type node patch
     const Store* xs = Xs + st * XS;
-    for (int rs = tid; rs < NPY * NPX; rs += NT) {
-      const int s = rs % NPX, r = rs / NPX;
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+      const int rs = tid + k * NT;
+      if (rs >= NNODE) break;
+      const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
       unsigned char m = 0;
       if (oa.inmask != IN_RAW && gx < g.n1 && gy < g.n1) {
@@ -517,7 +537,7 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const int i = f * NPY * NPX + rs;
+        const int i = f * NNODE + rs;
         X[i] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(xs[i]);
       }
     }
@@ -619,8 +639,11 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       if (nxt < ntiles) prefetch(nxt, 0);
       cp_async_commit();
     }
-    for (int rs = tid; rs < NPY * NPX; rs += NT) {
-      const int s = rs % NPX, r = rs / NPX;
+#pragma unroll
+    for (int kk = 0; kk < NIT; ++kk) {
+      const int rs = tid + kk * NT;
+      if (rs >= NNODE) break;
+      const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
       if (gx >= g.n1 || gy >= g.n1) continue;
       const int ylo = r == 0 ? 0 : (r - 1) / P, yhi = r / P < TY - 1 ? r / P : TY - 1;
@@ -691,12 +714,7 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, Ch
     if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
   }
   const long long node = gx + (long long)g.n1 * gy;
-  Store c2[2];
-  for (int b = 0; b < 2; ++b) {
-    const double lm = ce.lam_max[b];
-    const double a = ce.lo * lm, bb = ce.hi * lm;
-    c2[b] = Store((lm > 0.0 && lm < 1e300) ? 2.0 * ce.rho_k / (0.5 * (bb - a)) : 0.0);
-  }
+  const Store c2[2] = {Store(ce.c2s) * ce.inv_lam[0], Store(ce.c2s) * ce.inv_lam[1]};
   const Store c1 = Store(ce.c1);
   for (int f = 0; f < 3; ++f) {
     const long long gi = f * g.nn + node;
