@@ -667,17 +667,36 @@ int coarse_solve<float>(pff_ctx* c, const float* r, float* z) {
 }
 
 // x = S f: block-diagonal Chebyshev-Jacobi of degree cheb_degree with zero initial guess.
+// started: the first step (x = d = dinv f / theta) was already done by the kernel that produced f.
+// acc: add S f to acc instead (x is then scratch).
 template <typename Real>
-int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
+ChebStart<Real> cheb_start(pff_ctx* c, int l, Real* x, Real* dv) {
+  LevelData& L = c->lv[l];
+  ChebStart<Real> cs{};
+  cs.d = dv;
+  cs.x = x;
+  cs.dinv = dinv_of<Real>(L);
+  cs.inv_lam = inv_lam_of<Real>(L);
+  cs.c0s = 2.0 / (c->prm.cheb_hi + c->prm.cheb_lo);
+  cs.nu = c->dim * L.nn;
+  cs.on = 1;
+  return cs;
+}
+
+template <typename Real>
+int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv, bool started = false,
+           Real* acc = nullptr) {
   LevelData& L = c->lv[l];
   const long long n = L.nd, nu = c->dim * L.nn;
   const double lo = c->prm.cheb_lo, hi = c->prm.cheb_hi;
   const double sigma = (hi + lo) / (hi - lo);
   double rho = 1.0 / sigma;
   const Real* il = inv_lam_of<Real>(L);
+  const int deg = c->prm.cheb_degree;
   // theta_b = (hi + lo) lambda_b / 2, delta_b = (hi - lo) lambda_b / 2
-  CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, il, 2.0 / (hi + lo), 0.0, 0.0, c->s));
-  for (int k = 1; k < c->prm.cheb_degree; ++k) {
+  if (!started) CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, il, 2.0 / (hi + lo), 0.0, 0.0, c->s));
+  bool added = false;
+  for (int k = 1; k < deg; ++k) {
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     if (c->dim == 2) {
       // the apply finishes the step on single-tile nodes; the seam nodes follow
@@ -689,7 +708,9 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
       ce.inv_lam = il;
       ce.c1 = rho_new * rho;
       ce.c2s = 4.0 * rho_new / (hi - lo);
+      ce.acc = (acc && k == deg - 1) ? acc : nullptr;
       ce.on = 1;
+      added = ce.acc != nullptr;
       // t is all zero on entry (work vectors start zeroed; every use below leaves it zeroed)
       CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce, true));
       CK(launch_cheb_seam<Real>(L.g, t, ce, c->s));
@@ -700,6 +721,7 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv) {
     }
     rho = rho_new;
   }
+  if (acc && !added) CK(launch_axpby<Real>(n, 1.0, x, 1.0, acc, c->s));
   return PFF_OK;
 }
 
@@ -715,17 +737,22 @@ int vcycle_level(pff_ctx* c, int l, const Real* r, Real* e) {
   Real** wc = work_of<Real>(Lc);
   Real *t = w[2], *res = w[3], *dv = w[4], *sx = w[5];
   const bool zt = c->dim == 2;  // in 2D the apply buffer t is kept zeroed between uses
-  CR(smooth<Real>(c, l, r, e, t, dv));
+  ChebStart<Real> off{};
+  off.on = 0;
+  // pre-smoothing; below the finest level its first step was done by the restriction
+  CR(smooth<Real>(c, l, r, e, t, dv, l > 0));
   CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY, nullptr, zt));
-  CK(launch_res_update<Real>(L.nd, r, t, res, c->s));
+  CK(launch_res_update<Real>(L.nd, r, t, res, off, c->s));
   // res is zero on masked fine rows (r is, and G has identity rows there with e = 0): no Z_f needed
-  CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s, false));
+  const bool coarsest = l + 1 == c->nlev - 1;
+  const ChebStart<Real> csc = coarsest ? off : cheb_start<Real>(c, l + 1, wc[1], wc[4]);
+  CK(launch_restrict<Real>(c->dim, c->p, res, wc[0], L.flags, Lc.flags, L.g, Lc.g, c->xt, c->s, false, &csc));
   CR(vcycle_level<Real>(c, l + 1, wc[0], wc[1]));
   CK(launch_prolong<Real>(c->dim, c->p, wc[1], e, L.flags, Lc.g, L.g, c->xt, true, c->s));
   CR(apply_level<Real>(c, l, e, t, JM_FULL, IN_ALL, OUT_IDENTITY, nullptr, zt));
-  CK(launch_res_update<Real>(L.nd, r, t, res, c->s));
-  CR(smooth<Real>(c, l, res, sx, t, dv));
-  CK(launch_axpby<Real>(L.nd, 1.0, sx, 1.0, e, c->s));
+  // post-smoothing on the new residual, started by the residual update and added into e
+  CK(launch_res_update<Real>(L.nd, r, t, res, cheb_start<Real>(c, l, sx, dv), c->s));
+  CR(smooth<Real>(c, l, res, sx, t, dv, true, e));
   return PFF_OK;
 }
 

@@ -88,6 +88,8 @@ struct Geom {
 // With delta_b = (hi - lo) lambda_b / 2 the coefficient is c2s / lambda_b, c2s = 4 rho_k / (hi - lo)
 // from the host and 1 / lambda_b from the device (inv_lam, 0 for an unusable estimate): no division
 // (and, for FP32, no FP64 arithmetic) in the kernels.
+// acc (last step of a post-smoothing): acc_i += x_i + d_i instead of x_i += d_i, so the correction is
+// added to the cycle's iterate without a separate kernel.
 template <typename Store>
 struct ChebEpi {
   const Store* f;
@@ -96,6 +98,20 @@ struct ChebEpi {
   Store* x;
   const Store* inv_lam;  // [2]: 1 / lambda_max of the u block and of the phi block
   double c1, c2s;
+  Store* acc;
+  int on;
+};
+
+// First Chebyshev step with zero initial guess, x = d = (c0s / lambda_b) dinv f, done by the kernel
+// that produces f (the restriction, the V-cycle's residual update). nu: first phase-field DoF.
+template <typename Real>
+struct ChebStart {
+  Real* d;
+  Real* x;
+  const Real* dinv;
+  const Real* inv_lam;
+  double c0s;
+  long long nu;
   int on;
 };
 

@@ -723,7 +723,8 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
 // the cell on the left for o < 0.
 template <int DIM, int P, typename Real>
 __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
-                           const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine) {
+                           const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine,
+                           ChebStart<Real> cs) {
   constexpr int NW = 4 * P + 1;
   __shared__ Real W[P][NW];
   for (int i = threadIdx.x; i < P * NW; i += blockDim.x) {
@@ -775,8 +776,22 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
       }
     }
   }
+  Real a0 = Real(0), a1 = Real(0);
+  if (cs.on) {
+    a0 = Real(cs.c0s) * cs.inv_lam[0];
+    a1 = Real(cs.c0s) * cs.inv_lam[1];
+  }
 #pragma unroll
-  for (int f = 0; f <= DIM; ++f) yc[f * gc.nn + nd] = ((fc >> f) & 1u) ? Real(0) : acc[f];
+  for (int f = 0; f <= DIM; ++f) {
+    const long long gi = f * gc.nn + nd;
+    const Real v = ((fc >> f) & 1u) ? Real(0) : acc[f];
+    yc[gi] = v;
+    if (cs.on) {
+      const Real de = (f < DIM ? a0 : a1) * (cs.dinv[gi] * v);
+      cs.d[gi] = de;
+      cs.x[gi] = de;
+    }
+  }
 }
 
 template <typename Real>
@@ -796,12 +811,15 @@ cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsig
 template <typename Real>
 cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
                             const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
-                            cudaStream_t s, bool mask_fine) {
+                            cudaStream_t s, bool mask_fine, const ChebStart<Real>* cs) {
   const unsigned gr = grid_for(gc.nn, 128);
+  ChebStart<Real> off{};
+  off.on = 0;
+  const ChebStart<Real>& st = cs ? *cs : off;
 #define PFF_CASE(DD, PP)                                                                                 \
   if (dim == DD && p == PP)                                                                              \
     return launch_k(k_restrict<DD, PP, Real>, dim3(gr), dim3(128), 0, s, xf, yc, flags_f, flags_c, gf, gc, \
-                    xt, mask_fine ? 1 : 0);
+                    xt, mask_fine ? 1 : 0, st);
   PFF_CASE(2, 1) PFF_CASE(2, 2) PFF_CASE(2, 3) PFF_CASE(2, 4)
   PFF_CASE(3, 1) PFF_CASE(3, 2) PFF_CASE(3, 3) PFF_CASE(3, 4)
 #undef PFF_CASE
@@ -814,10 +832,10 @@ template cudaError_t launch_prolong<float>(int, int, const float*, float*, const
                                            const Geom&, const XferTab&, bool, cudaStream_t);
 template cudaError_t launch_restrict<double>(int, int, const double*, double*, const unsigned char*,
                                              const unsigned char*, const Geom&, const Geom&, const XferTab&,
-                                             cudaStream_t, bool);
+                                             cudaStream_t, bool, const ChebStart<double>*);
 template cudaError_t launch_restrict<float>(int, int, const float*, float*, const unsigned char*,
                                             const unsigned char*, const Geom&, const Geom&, const XferTab&,
-                                            cudaStream_t, bool);
+                                            cudaStream_t, bool, const ChebStart<float>*);
 
 // Fine FE function evaluated at the coarse nodes (carries the state to coarse levels).
 __global__ void k_state_interp(int dim, int p, const double* __restrict__ xf, double* __restrict__ yc, int nfields,
@@ -917,24 +935,40 @@ cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y
 template cudaError_t launch_axpby<double>(long long, double, const double*, double, double*, cudaStream_t);
 template cudaError_t launch_axpby<float>(long long, double, const float*, double, float*, cudaStream_t);
 
-// res = r - t, then t = 0 (the V-cycle's residual; leaves the apply buffer zeroed for the next apply).
+// res = r - t, then t = 0 (the V-cycle's residual; leaves the apply buffer zeroed for the next apply);
+// with cs.on also the first smoothing step of res.
 template <typename Real>
-__global__ void k_res_update(long long n, const Real* __restrict__ r, Real* __restrict__ t, Real* __restrict__ res) {
+__global__ void k_res_update(long long n, const Real* __restrict__ r, Real* __restrict__ t, Real* __restrict__ res,
+                             ChebStart<Real> cs) {
   pdl_wait();
+  Real a0 = Real(0), a1 = Real(0);
+  if (cs.on) {
+    a0 = Real(cs.c0s) * cs.inv_lam[0];
+    a1 = Real(cs.c0s) * cs.inv_lam[1];
+  }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    res[e] = r[e] - t[e];
+    const Real v = r[e] - t[e];
+    res[e] = v;
     t[e] = Real(0);
+    if (cs.on) {
+      const Real de = (e < cs.nu ? a0 : a1) * (cs.dinv[e] * v);
+      cs.d[e] = de;
+      cs.x[e] = de;
+    }
   }
 }
 template <typename Real>
-cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, cudaStream_t s) {
+cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, const ChebStart<Real>& cs,
+                              cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  return launch_k(k_res_update<Real>, dim3((unsigned)g), dim3(BLK), 0, s, n, r, t, res);
+  return launch_k(k_res_update<Real>, dim3((unsigned)g), dim3(BLK), 0, s, n, r, t, res, cs);
 }
-template cudaError_t launch_res_update<double>(long long, const double*, double*, double*, cudaStream_t);
-template cudaError_t launch_res_update<float>(long long, const float*, float*, float*, cudaStream_t);
+template cudaError_t launch_res_update<double>(long long, const double*, double*, double*, const ChebStart<double>&,
+                                               cudaStream_t);
+template cudaError_t launch_res_update<float>(long long, const float*, float*, float*, const ChebStart<float>&,
+                                              cudaStream_t);
 
 template <typename Ti, typename To>
 __global__ void k_cast(long long n, const Ti* __restrict__ x, To* __restrict__ y) {

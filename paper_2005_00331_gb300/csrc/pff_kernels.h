@@ -48,11 +48,11 @@ template <typename Real>
 cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f,
                            const Geom& gc, const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s);
 // mask_fine = false skips Z_f (valid when x is already zero on masked fine rows, as the V-cycle's
-// residuals are).
+// residuals are). With cs, also the first smoothing step on the coarse level (x = d = c0 dinv yc).
 template <typename Real>
 cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsigned char* flags_f,
                             const unsigned char* flags_c, const Geom& gf, const Geom& gc, const XferTab& xt,
-                            cudaStream_t s, bool mask_fine = true);
+                            cudaStream_t s, bool mask_fine = true, const ChebStart<Real>* cs = nullptr);
 // Evaluates `nfields` fine nodal fields (each nn_f long, consecutive) at the coarse nodes.
 cudaError_t launch_state_interp(int dim, int p, const double* xf, double* yc, int nfields, const Geom& gf,
                                 const Geom& gc, const XferTab& xt, cudaStream_t s);
@@ -63,9 +63,10 @@ cudaError_t launch_coarse_active(int dim, int p, const unsigned char* flags_f, u
 // ---- vectors ---------------------------------------------------------------------------
 template <typename Real>
 cudaError_t launch_axpby(long long n, double a, const Real* x, double b, Real* y, cudaStream_t s);
-// res = r - t; t = 0.
+// res = r - t; t = 0; with cs.on also the first smoothing step of res (x = d = c0 dinv res).
 template <typename Real>
-cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, cudaStream_t s);
+cudaError_t launch_res_update(long long n, const Real* r, Real* t, Real* res, const ChebStart<Real>& cs,
+                              cudaStream_t s);
 template <typename Ti, typename To>
 cudaError_t launch_cast(long long n, const Ti* x, To* y, cudaStream_t s);
 // Two-block dot products of x and y over [0, nu) and [nu, n): result res[0], res[1] (device, FP64).

@@ -432,6 +432,35 @@ struct Stage2 {
   static constexpr int NSTAGE = 1;  // kept as a parameter: the kernel supports 2
 };
 
+// The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete; y is
+// reset to 0 there, so y is all zero again afterwards (the fused applies write no other entry).
+// Seam index t enumerates the vertical seam lines, then the horizontal ones (crossings once).
+template <typename Store>
+__device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, Store* y, const ChebEpi<Store>& ce,
+                                               long long t, Store c1, const Store c2[2]) {
+  const long long nv = (long long)(g.ntile[0] - 1) * g.n1;
+  int gx, gy;
+  if (t < nv) {
+    gx = int(t / g.n1 + 1) * tpx;
+    gy = int(t % g.n1);
+  } else {
+    const long long u = t - nv;
+    gy = int(u / g.n1 + 1) * tpy;
+    gx = int(u % g.n1);
+    if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
+  }
+  const long long node = gx + (long long)g.n1 * gy;
+  for (int f = 0; f < 3; ++f) {
+    const long long gi = f * g.nn + node;
+    const Store yv = y[gi];
+    const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - yv));
+    ce.d[gi] = dn;
+    if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
+    else ce.x[gi] = ce.x[gi] + dn;
+    y[gi] = Store(0);
+  }
+}
+
 // Register budget per thread that keeps the CTAs resident which fit in shared memory (FP32 Q2: five
 // per SM; double-word Q2: two): FP32 64 up to Q2 and 96 above (64 would spill there), double-word 80
 // for Q1 and 168 for Q2/Q3; native FP64 and double-word Q4 unconstrained.
@@ -681,7 +710,8 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
           const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
           const Store dn = ch_c1 * ce.d[gi] + ch_c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y));
           ce.d[gi] = dn;
-          ce.x[gi] = ce.x[gi] + dn;
+          if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
+          else ce.x[gi] = ce.x[gi] + dn;
         } else if (masked) {
           if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
         } else if (low || high) {
@@ -695,34 +725,14 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   cp_async_wait<0>();
 }
 
-// The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete; y is
-// reset to 0 there, so y is all zero again afterwards (the fused applies write no other entry).
 template <typename Store>
 __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, ChebEpi<Store> ce) {
   pdl_wait();
-  const long long nv = (long long)(g.ntile[0] - 1) * g.n1, nh = (long long)(g.ntile[1] - 1) * g.n1;
+  const long long nseam = (long long)(g.ntile[0] - 1 + g.ntile[1] - 1) * g.n1;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= nv + nh) return;
-  int gx, gy;
-  if (t < nv) {
-    gx = int(t / g.n1 + 1) * tpx;
-    gy = int(t % g.n1);
-  } else {
-    const long long u = t - nv;
-    gy = int(u / g.n1 + 1) * tpy;
-    gx = int(u % g.n1);
-    if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
-  }
-  const long long node = gx + (long long)g.n1 * gy;
+  if (t >= nseam) return;
   const Store c2[2] = {Store(ce.c2s) * ce.inv_lam[0], Store(ce.c2s) * ce.inv_lam[1]};
-  const Store c1 = Store(ce.c1);
-  for (int f = 0; f < 3; ++f) {
-    const long long gi = f * g.nn + node;
-    const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y[gi]));
-    ce.d[gi] = dn;
-    ce.x[gi] = ce.x[gi] + dn;
-    y[gi] = Store(0);
-  }
+  cheb_seam_node<Store>(g, tpx, tpy, y, ce, t, Store(ce.c1), c2);
 }
 
 template <int P, typename Real, typename Store, int SPLIT>
