@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps"], default="newton",
+    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps", "vcycle"], default="newton",
                     help="apply: time only the finest-level Jacobian apply (--precision) on the workload; "
                          "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid")
     ap.add_argument("--state", choices=["random", "tension"], default="random",
@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--newton-rtol", type=float, default=1e-8)
     ap.add_argument("--load-steps", type=int, default=10, help="--mode loadsteps: number of load steps")
     ap.add_argument("--load-inc", type=float, default=1e-4, help="--mode loadsteps: top displacement increment")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the last timed step (--mode vcycle: one extra cycle) by cudaProfilerStart/Stop, "
+                         "for `ncu --profile-from-start off`")
     ap.add_argument("--max-seconds", type=float, default=600.0,
                     help="--mode loadsteps: stop a precision's loading after this many seconds (partial result)")
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
@@ -257,9 +260,16 @@ def run_native(a, rank, world):
         t0 = time.perf_counter()
         for i in range(a.steps):
             flush.zero_()
+            last = a.profile_range and i == a.steps - 1
+            if last:
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStart()
             ev[i][0].record(stream)
             reps.append(step())
             ev[i][1].record(stream)
+            if last:
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStop()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
     n_launch = launch_count() - n_launch0
@@ -453,6 +463,39 @@ def run_pdas(a):
     return out
 
 
+def run_vcycle(a):
+    """The FP32 (or FP64, --mg-precision) V-cycle of the workload's first Newton step, replayed
+    --steps times after --warmup replays (CUDA events, warm caches)."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+    U_h, po_h = make_state(ctx, a, seed=0)
+    ctx.set_state(torch.from_numpy(U_h).to(dev), torch.from_numpy(po_h).to(dev),
+                  torch.from_numpy(po_h).to(dev), None)
+    ctx.solve_newton_step(check=False)
+    r = torch.randn(ctx.n_dofs, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(max(a.warmup, 1)):
+        ctx.vcycle(r, z)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        ctx.vcycle(r, z)
+    e1.record()
+    torch.cuda.synchronize()
+    if a.profile_range:
+        torch.cuda.cudart().cudaProfilerStart()
+        ctx.vcycle(r, z)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+    return {"mode": "vcycle", "workload": workload_name(a), "levels": ctx.n_levels,
+            "ms_per_cycle": e0.elapsed_time(e1) / a.steps, "replays": a.steps}
+
+
 def run_loadsteps(a):
     """Quasi-static loading from rest: --load-steps steps of --load-inc on the top face, each a full
     active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid."""
@@ -586,6 +629,10 @@ def main():
     if a.mode == "loadsteps":
         torch.cuda.set_device(local if world > 1 else 0)
         print(json.dumps(run_loadsteps(a)))
+        return
+    if a.mode == "vcycle":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_vcycle(a)))
         return
     if world > 1:
         torch.cuda.set_device(local)
