@@ -6,7 +6,8 @@ namespace pff {
 
 template <int DIM, int P, int SPLIT>
 static cudaError_t run_res(const double* U, double* r, const unsigned char* flags, const Geom& g,
-                           const Tab<double>& tb, const double* st, double eps, double kappa, cudaStream_t s) {
+                           const Tab<double>& tb, const double* st, const double* sp, double eps, double kappa,
+                           cudaStream_t s) {
   size_t smem;
   if constexpr (DIM == 2) smem = op2d_smem<P, double>();
   else smem = op3d_smem<P, double>();
@@ -21,6 +22,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   }
   PWRes<DIM, SPLIT> pw;
   pw.st = st;
+  pw.sp = SPLIT ? sp : nullptr;
   pw.qpt = g.qpt;
   pw.tstride = (long long)ST_NV * g.qpt;
   pw.qpx = g.qpx;
@@ -38,10 +40,10 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
 }
 
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
-                       const Geom& g, const Tab<double>& tb, const double* st, double eps, double kappa,
-                       cudaStream_t s) {
+                       const Geom& g, const Tab<double>& tb, const double* st, const double* sp, double eps,
+                       double kappa, cudaStream_t s) {
 #define PFF_CASE(DD, PP, SS) \
-  if (dim == DD && p == PP && split == SS) return run_res<DD, PP, SS>(U, r, flags, g, tb, st, eps, kappa, s);
+  if (dim == DD && p == PP && split == SS) return run_res<DD, PP, SS>(U, r, flags, g, tb, st, sp, eps, kappa, s);
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
   PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
   PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)

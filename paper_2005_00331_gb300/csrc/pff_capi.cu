@@ -102,6 +102,7 @@ struct LevelData {
   df64* qpdf = nullptr;     // per-point data as double-word pairs (float-float FP64 applies)
   Tab<df64> tdf{};
   double* st64 = nullptr;
+  double* sp64 = nullptr;   // finest level, Miehe split: sigma+ (Mandel) and E_s+ per point of the current u
   double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
   double* di64 = nullptr;   // its inverse (Jacobi scaling)
   float* d32 = nullptr;     // the diagonal computed in FP32 from the FP32 per-point data (FP32 multigrid)
@@ -126,6 +127,7 @@ struct pff_ctx {
   XferTab xt{};
   bool has_state = false, qp_valid = false, mg_ready = false, has_fields = false;
   bool st_valid = false;    // per-point residual state (depends on phi~ and the fields, not on U)
+  bool strain_valid = false;  // finest-level strain pass (eigen-decompositions) of the current u
   bool diag64_ok = false;   // FP64 diagonals present (always with the FP64 multigrid; on demand with FP32)
   double* phi_old = nullptr;
   double* hist1 = nullptr;  // phase field of the previous load step
@@ -423,14 +425,41 @@ int qp_setup_level(pff_ctx* c, int l) {
   return PFF_OK;
 }
 
+int ensure_st(pff_ctx* c);
+
+// Miehe split, finest level: the per-point work that depends on u only (eigen-decomposition,
+// tangent, sigma+ and E_s+ for the residual), once per u; the active-set projection changes phi only.
+int ensure_strain(pff_ctx* c) {
+  CR(ensure_st(c));
+  if (!c->strain_valid) {
+    LevelData& L = c->lv[0];
+    MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+    const double* F = L.fields;
+    CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
+                       c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
+                       L.qp64, L.qp32, L.qpdf, nullptr, c->s, L.sp64, QP_STRAIN));
+    c->strain_valid = true;
+  }
+  return PFF_OK;
+}
+
 // Tangent per-point data of the finest level (and the residual state with it).
 int ensure_qp(pff_ctx* c) {
   if (!c->has_state) return PFF_ERR_NO_STATE;
-  if (!c->qp_valid) {
+  if (c->qp_valid) return PFF_OK;
+  LevelData& L = c->lv[0];
+  if (L.sp64) {
+    CR(ensure_strain(c));
+    MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
+    const double* F = L.fields;
+    CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
+                       c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
+                       L.qp64, L.qp32, L.qpdf, nullptr, c->s, L.sp64, QP_PHASE));
+  } else {
     CR(qp_setup_level(c, 0));
-    c->qp_valid = true;
     c->st_valid = true;
   }
+  c->qp_valid = true;
   return PFF_OK;
 }
 
@@ -446,6 +475,8 @@ int ensure_st(pff_ctx* c) {
                        c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
                        nullptr, nullptr, nullptr, L.st64, c->s));
     c->st_valid = true;
+    c->strain_valid = false;  // the tangent depends on g(phi~) and the fields
+    c->qp_valid = false;
   }
   return PFF_OK;
 }
@@ -465,10 +496,12 @@ int ensure_diag64(pff_ctx* c) {
 int residual_into(pff_ctx* c, double* r) {
   CR(ensure_st(c));
   LevelData& L = c->lv[0];
+  if (L.sp64) CR(ensure_strain(c));
   CK(cudaMemsetAsync(r, 0, sizeof(double) * L.nd, c->s));
   const bool timed = prof_on(c, PFF_PROF_RESIDUAL);
   if (timed) CR(prof_mark(c));
-  CK(launch_res(c->dim, c->p, c->prm.split, L.U, r, L.flags, L.g, L.t64, L.st64, c->prm.eps, c->prm.kappa, c->s));
+  CK(launch_res(c->dim, c->p, c->prm.split, L.U, r, L.flags, L.g, L.t64, L.st64, L.sp64, c->prm.eps, c->prm.kappa,
+                c->s));
   if (timed) CR(prof_mark(c));
   return PFF_OK;
 }
@@ -1038,6 +1071,11 @@ static int setup_impl(pff_ctx* c) {
     if (l == 0) {
       CR(dalloc(c, &L.st64, ST_NV * nqp));
       CK(cudaMemsetAsync(L.st64, 0, sizeof(double) * ST_NV * nqp, c->s));
+      if (c->prm.split == 1) {
+        const int nm = c->dim == 2 ? 3 : 6;
+        CR(dalloc(c, &L.sp64, (nm + 1) * nqp));
+        CK(cudaMemsetAsync(L.sp64, 0, sizeof(double) * (nm + 1) * nqp, c->s));
+      }
     }
     CR(dalloc(c, &L.d64, L.nd));
     CR(dalloc(c, &L.di64, L.nd));
@@ -1179,6 +1217,7 @@ int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const doub
   c->has_state = true;
   c->qp_valid = false;
   c->st_valid = false;
+  c->strain_valid = false;
   c->mg_ready = false;
   c->nhist = 0;
   if (active) {
@@ -1361,6 +1400,7 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   if (r.status == PFF_OK || r.status == PFF_ERR_NOT_CONVERGED) {
     CK(launch_axpby<double>(L.nd, 1.0, c->dU, 1.0, L.U, c->s));
     c->qp_valid = false;
+    c->strain_valid = false;
     c->mg_ready = false;
     if (U_out) CK(cudaMemcpyAsync(U_out, L.U, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
   }
@@ -1414,6 +1454,7 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
                            c->phi_old, c->s));
   c->qp_valid = false;
   c->st_valid = false;
+  c->strain_valid = false;
   c->mg_ready = false;
   const int st = pff_solve_pdas(c, max_iters, newton_rtol, nullptr, reps, n_steps);
   if (st == PFF_OK) {

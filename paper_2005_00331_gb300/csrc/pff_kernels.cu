@@ -113,12 +113,15 @@ __device__ double eval_scalar(const CellQP<DIM, P>& cq, const double* f, const G
 // ===========================================================================================
 // Per-point data of the Jacobian: tangent of g(phi~) sigma^+ + sigma^- (Sec. 2.1, 3.5), the
 // coupling g'(phi) sigma^+ and the phase-field coefficients, times JxW (see qp_nv).
+// part QP_ALL: everything. Miehe split, in two passes: QP_STRAIN (what depends on u only: the
+// eigen-decomposition, the tangent, the phase-field coefficients, and sigma+ / E_s+ into sp64 for the
+// residual), then QP_PHASE (the coupling g'(phi) sigma+ from sp64 and phi, after each phi change).
 template <int DIM, int P, int SPLIT>
 __global__ void k_qp_setup(const double* __restrict__ U, const double* __restrict__ phit,
                            const double* __restrict__ gcf, const double* __restrict__ lamf,
                            const double* __restrict__ muf, Geom g, Tab<double> tb, MatConst mc,
                            double* __restrict__ qp64, float* __restrict__ qp32, df64* __restrict__ qpdf,
-                           double* __restrict__ st64) {
+                           double* __restrict__ st64, double* __restrict__ sp64, int part) {
   constexpr int NQ = ipow<DIM>(P + 1);
   constexpr int NM = Mandel<DIM>::NM;
   constexpr int NV = qp_nv(DIM, SPLIT);
@@ -140,9 +143,23 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
     st64[sb + 3 * g.qpt] = mu;
   }
   if (!qp64) return;  // residual state only (it does not depend on U)
+  const double jxw = cq.jxw(tb);
+  const long long base = cq.tile * NV * g.qpt + cq.qidx;
+  if (SPLIT == 1 && part == QP_PHASE) {
+    const double dgp = deg_dg(eval_scalar<DIM, P>(cq, U + DIM * g.nn, g, tb), mc.kappa);
+    const double* sp = sp64 + cq.tile * (NM + 1) * g.qpt + cq.qidx;
+    constexpr int OB = NM * (NM + 1) / 2;
+    for (int m = 0; m < NM; ++m) {
+      const double v = dgp * sp[m * g.qpt] * jxw;
+      const long long o = base + (OB + m) * g.qpt;
+      qp64[o] = v;
+      if (qp32) qp32[o] = (float)v;
+      if (qpdf) qpdf[o] = df_from(v);
+    }
+    return;
+  }
   double gu[DIM][DIM], ph, gph[DIM];
   eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
-  const double jxw = cq.jxw(tb);
   const double dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
 
   double e[DIM][DIM], tr = 0.0;
@@ -203,12 +220,19 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
         if (a < DIM && b < DIM) Cab += lam * aH;
         vals[o++] = Cab * jxw;
       }
-    for (int m = 0; m < NM; ++m) vals[o + m] = dgp * (2.0 * mu * epm[m] + (m < DIM ? lam * trp : 0.0)) * jxw;
+    for (int m = 0; m < NM; ++m) {
+      const double spm = 2.0 * mu * epm[m] + (m < DIM ? lam * trp : 0.0);
+      vals[o + m] = dgp * spm * jxw;
+      if (part == QP_STRAIN) sp64[cq.tile * (NM + 1) * g.qpt + m * g.qpt + cq.qidx] = spm;
+    }
     vals[o + NM] = (ddg * Esp + gc / mc.eps) * jxw;
     vals[o + NM + 1] = gc * mc.eps * jxw;
+    if (part == QP_STRAIN) sp64[cq.tile * (NM + 1) * g.qpt + NM * g.qpt + cq.qidx] = Esp;
   }
-  const long long base = cq.tile * NV * g.qpt + cq.qidx;
+  // QP_STRAIN leaves the coupling entries to the phase pass
+  constexpr int OB = SPLIT == 1 ? NM * (NM + 1) / 2 : 2;
   for (int v = 0; v < NV; ++v) {
+    if (SPLIT == 1 && part == QP_STRAIN && v >= OB && v < OB + NM) continue;
     qp64[base + v * g.qpt] = vals[v];
     if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
     if (qpdf) qpdf[base + v * g.qpt] = df_from(vals[v]);
@@ -217,13 +241,14 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
 
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
                             const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
-                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s) {
+                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s,
+                            double* sp64, int part) {
   const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
   const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
   const unsigned gr = grid_for(tot, 128);
 #define PFF_CASE(DD, PP, SS)                                                                          \
   if (dim == DD && p == PP && split == SS) {                                                          \
-    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, qpdf, st64); \
+    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, qpdf, st64, sp64, part); \
     return cudaGetLastError();                                                                        \
   }
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)

@@ -10,10 +10,15 @@ struct MatConst {
   double lambda, mu, gc, eps, kappa;
 };
 
-// Per-point data of the Jacobian (FP64 and optionally an FP32 copy) and of the residual.
+// Per-point data of the Jacobian (FP64, optional FP32 and double-word copies) and of the residual.
+// part: QP_ALL; or, with the Miehe split, QP_STRAIN (everything that depends on u only, plus
+// sigma+ and E_s+ into sp64 [tile][NM + 1][qpt]) followed by QP_PHASE (the coupling entries from
+// sp64 and phi).
+constexpr int QP_ALL = 0, QP_STRAIN = 1, QP_PHASE = 2;
 cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
                             const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
-                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s);
+                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s,
+                            double* sp64 = nullptr, int part = QP_ALL);
 // diag(G_uu, G_phiphi) of a level into d (zeroed here), masked rows set to 1, from the per-point
 // data of the same precision.
 template <typename Real>

@@ -65,9 +65,11 @@ cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y,
 cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                            const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
                            cudaStream_t s);
-// r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu.
+// r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu. With the
+// Miehe split and sp != null, sigma+ and E_s+ per point are read from sp ([tile][NM + 1][qpt], the
+// strain pass of the same u) instead of recomputing the eigen-decomposition.
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
-                       const Geom& g, const Tab<double>& tb, const double* st, double eps, double kappa,
-                       cudaStream_t s);
+                       const Geom& g, const Tab<double>& tb, const double* st, const double* sp, double eps,
+                       double kappa, cudaStream_t s);
 
 }  // namespace pff

@@ -107,6 +107,7 @@ struct PWJac {
 template <int DIM, int SPLIT>
 struct PWRes {
   const double* st;  // [tile][4][qpt]
+  const double* sp;  // Miehe split: [tile][NM + 1][qpt] sigma+ (Mandel) and E_s+ of the current u, or null
   long long tstride, qpt;
   int qpx, qpy, n;
   double W[MAXN], hd, eps, kappa;
@@ -133,6 +134,17 @@ struct PWRes {
           ee += e[i][j] * e[i][j];
         }
       Esp = 0.5 * lam * tr * tr + mu * ee;
+    } else if (this->sp) {
+      // sigma+ and E_s+ of this u, computed with the tangent (one eigen-decomposition per u)
+      constexpr int NM = Mandel<DIM>::NM;
+      const double* c = this->sp + tile * (long long)(NM + 1) * qpt + qi;
+      for (int m = 0; m < NM; ++m) {
+        const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
+        const double v = c[m * qpt];
+        if (i == j) sp[i][i] = v;
+        else sp[i][j] = sp[j][i] = v * 0.70710678118654752440;  // 1 / sqrt(2)
+      }
+      Esp = c[NM * qpt];
     } else {
       double l[DIM], V[DIM][DIM];
       eig_sym<DIM>(e, l, V);
