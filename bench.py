@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the last timed step (--mode vcycle: one extra cycle) by cudaProfilerStart/Stop, "
                          "for `ncu --profile-from-start off`")
+    ap.add_argument("--newton-max", type=int, default=30, help="--mode loadsteps: Newton iterations per load step")
+    ap.add_argument("--gmres-max", type=int, default=500, help="--mode loadsteps: FGMRES iterations per linear solve")
     ap.add_argument("--max-seconds", type=float, default=600.0,
                     help="--mode loadsteps: stop a precision's loading after this many seconds (partial result)")
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
@@ -510,7 +512,8 @@ def run_loadsteps(a):
     finals = {}
     for prec in (32, 64):
         ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
-                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode,
+                         gmres_max_iters=a.gmres_max)
         U_h, po_h = make_state(ctx, b, seed=0)
         U = torch.from_numpy(U_h).to(dev)
         po = torch.from_numpy(po_h).to(dev)
@@ -524,7 +527,8 @@ def run_loadsteps(a):
         steps, newton, iters, status = [], 0, 0, 0
         for k in range(1, a.load_steps + 1):
             t0 = time.perf_counter()
-            st, reps = ctx.solve_load_step(k * a.load_inc, check=False)
+            st, reps = ctx.solve_load_step(k * a.load_inc, max_iters=a.newton_max, newton_rtol=a.newton_rtol,
+                                           check=False)
             steps.append({"load": k * a.load_inc, "status": st, "newton_steps": len(reps),
                           "gmres_iters": [r["gmres_iters"] for r in reps], "seconds": time.perf_counter() - t0,
                           "n_active": reps[-1]["n_active"] if reps else None})
