@@ -78,6 +78,22 @@ def workload_name(a):
         "FP32 (mixed)" if a.mg_precision == 32 else "FP64")
 
 
+# ---- multi-rank aggregation (replicas: every rank solves its own copy, no data-path collective) ---
+def max_over_ranks(ms, world, device):
+    """The slowest rank's step time (ms); world == 1 returns ms unchanged."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n_dofs_per_rank, world, ms):
+    """Whole-job throughput: the DoFs all ranks processed per second of the slowest rank's step."""
+    return n_dofs_per_rank * world / (ms * 1e-3)
+
+
 # ---- measured DRAM traffic of the roofline kernel (from a committed ncu summary) --------------
 TRAFFIC_SOURCES = ("pff_op.cuh", "pff_common.cuh", "pff_df64.cuh", "op_jac2_f32.cu", "op_jac3_f32.cu")
 
@@ -93,14 +109,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(a, n_dofs):
+def measured_traffic(a, n_dofs, profiles_dir=None):
     """dram__bytes_read + dram__bytes_write per launch of the FP32 finest-level apply, from a
     'traffic-record:' line of a profiles/*.md summary with the same kernel sources and workload
     family (scaled by DoFs); None when no record matches the current kernel."""
     import glob
     want = {"dim": str(a.dim), "degree": str(a.degree), "split": str(a.split), "source": kernel_source_hash()}
-    here = os.path.dirname(os.path.abspath(__file__))
-    for fn in sorted(glob.glob(os.path.join(here, "profiles", "*.md"))):
+    here = profiles_dir or os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles")
+    for fn in sorted(glob.glob(os.path.join(here, "*.md"))):
         with open(fn) as fh:
             for ln in fh:
                 if not ln.strip().startswith("traffic-record:"):
@@ -644,12 +660,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     r = run_native(a, rank, world)
-    ms = r["step_ms"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = r["n_dofs"] * world / (ms * 1e-3)
+    ms = max_over_ranks(r["step_ms"], world, "cuda")
+    value = job_value(r["n_dofs"], world, ms)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return

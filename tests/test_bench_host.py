@@ -1,0 +1,64 @@
+"""Host logic of bench.py without a GPU: the whole-job aggregation of the multi-process launch
+(every rank solves its own replica; the step time is the slowest rank's, all ranks' DoFs count),
+run as two gloo ranks on CPU, and the lookup of the measured DRAM traffic record."""
+import os
+import socket
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")  # rank 1 is the slow one
+        out[rank] = (ms, bench.job_value(1000, world, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_step():
+    import torch.multiprocessing as mp
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[0] == res[1]
+    ms, value = res[0]
+    assert ms == 15.0
+    assert abs(value - 2 * 1000 / 15e-3) < 1e-6
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(12.5, 1, "cpu") == 12.5
+    assert bench.job_value(789507, 1, 10.0) == pytest.approx(78950700.0)
+
+
+def test_traffic_record_lookup(tmp_path):
+    import bench
+    a = types.SimpleNamespace(dim=2, degree=2, split=1)
+    h = bench.kernel_source_hash()
+    (tmp_path / "x.md").write_text("text\ntraffic-record: kernel=k dim=2 degree=2 split=1 dofs=100 bytes=5000 "
+                                   "source=%s\n" % h)
+    assert bench.measured_traffic(a, 200, str(tmp_path)) == pytest.approx(10000.0)
+    (tmp_path / "x.md").write_text("traffic-record: kernel=k dim=2 degree=2 split=1 dofs=100 bytes=5000 source=0\n")
+    assert bench.measured_traffic(a, 200, str(tmp_path)) is None
+    assert bench.measured_traffic(types.SimpleNamespace(dim=3, degree=2, split=1), 200, str(tmp_path)) is None
