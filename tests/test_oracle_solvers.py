@@ -193,3 +193,55 @@ def test_pdas_loop_converges_tension_test():
     assert norms[-1] <= 1e-8 * norms[0]
     # irreversibility: phi never exceeds phi_old
     assert np.all(U[2 * m.n_nodes:] <= phi_old + 1e-12)
+
+
+def _cheb_smoother_dense(A, d, degree, lam_max, lo=0.24, hi=1.2):
+    """x = S f of a Chebyshev-Jacobi smoother with zero initial guess, as a dense matrix from its
+    error polynomial (Saad, Sec. 12.3): A^{-1} f - x = T_s((theta - M)/delta) / T_s(theta/delta) A^{-1} f
+    with M = D^{-1} A, evaluated through the eigen-decomposition of D^{-1/2} A D^{-1/2} instead of the
+    three-term recurrence."""
+    a, b = lo * lam_max, hi * lam_max
+    theta, delta = 0.5 * (a + b), 0.5 * (b - a)
+    Ts = np.polynomial.chebyshev.Chebyshev.basis(degree)
+    sq = np.sqrt(d)
+    w, Q = np.linalg.eigh(A / np.outer(sq, sq))
+    R = (Q * (Ts((theta - w) / delta) / Ts(theta / delta))) @ Q.T
+    R = R / sq[:, None] * sq[None, :]  # D^{-1/2} R_sym D^{1/2}
+    return (np.eye(len(d)) - R) @ np.linalg.inv(A)
+
+
+@pytest.mark.parametrize("split", [mat.SPLIT_NONE, mat.SPLIT_MIEHE])
+def test_vcycle_equals_dense_two_grid(split):
+    """The V-cycle as a composition: on two levels it equals e = S r, e += P Gc^{-1} P^T (r - G e)
+    (masked as stated in the readings), e += S (r - G e), with the smoother built from its closed-form
+    error polynomial and the coarse operator inverted densely."""
+    dim, p, N = 2, 1, 8
+    m = M.Mesh(dim, p, N)
+    prm = fe.Params(LAM, MU, GC, 2.0 / N, KAPPA, split)
+    rng = np.random.default_rng(31)
+    U = m.dirichlet_values(1e-3)
+    U[:dim * m.n_nodes] += np.where(m.dirichlet_mask()[:dim * m.n_nodes], 0, rng.normal(0, 1e-4, dim * m.n_nodes))
+    U[dim * m.n_nodes:] = rng.uniform(0.9, 1, m.n_nodes)
+    act = rng.uniform(size=m.n_nodes) < 0.2
+    lv = S.build_levels(dim, p, N, prm, U, U[dim * m.n_nodes:], act, cheb_degree=4)
+    assert len(lv) == 2
+    L0, L1 = lv
+    r = np.where(L0.mask, 0.0, rng.normal(size=m.n_dofs))
+    e_oracle = S.vcycle(lv, r)
+
+    G = L0.G.toarray()
+    nu = L0.nu
+    Sm = np.zeros_like(G)
+    Sm[:nu, :nu] = _cheb_smoother_dense(L0.Guu.toarray(), L0.diag[:nu], 4, L0.lam_max[0])
+    Sm[nu:, nu:] = _cheb_smoother_dense(L0.Gpp.toarray(), L0.diag[nu:], 4, L0.lam_max[1])
+    P1 = L1.P.toarray()
+    P = np.kron(np.eye(dim + 1), P1)  # component-blocked vectors
+    Gc_inv = np.linalg.inv(L1.G.toarray())
+    e = Sm @ r
+    rc = P.T @ (r - G @ e)
+    rc[L1.mask] = 0.0
+    pe = P @ (Gc_inv @ rc)
+    pe[L0.mask] = 0.0
+    e = e + pe
+    e = e + Sm @ (r - G @ e)
+    assert np.linalg.norm(e - e_oracle) <= 1e-10 * np.linalg.norm(e_oracle)
