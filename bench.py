@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps", "vcycle"], default="newton",
+    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps", "vcycle", "adjoint"], default="newton",
                     help="apply: time only the finest-level Jacobian apply (--precision) on the workload; "
                          "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid")
     ap.add_argument("--state", choices=["random", "tension"], default="random",
@@ -481,6 +481,44 @@ def run_pdas(a):
     return out
 
 
+def run_adjoint(a):
+    """Residual under torch.autograd with the hand-written adjoint: forward R(U; G_c, lambda, mu) and
+    backward (transpose Jacobian apply + nodal parameter gradients) for a seeded lognormal G_c field,
+    --steps timed passes after --warmup (CUDA events)."""
+    import torch
+
+    from paper_2005_00331_gb300 import ResidualFunction, inputs, setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                     mg_precision=a.mg_precision, fp64_mode=a.fp64_mode)
+    U_h, po_h = make_state(ctx, a, seed=0)
+    nn = ctx.n_nodes
+    U = torch.from_numpy(U_h).to(dev).requires_grad_(True)
+    po = torch.from_numpy(po_h).to(dev)
+    gc = torch.from_numpy(inputs.lognormal_field(nn, 0)).to(dev).requires_grad_(True)
+    lam = torch.full((nn,), 121.15, dtype=torch.float64, device=dev, requires_grad=True)
+    mu = torch.full((nn,), 80.77, dtype=torch.float64, device=dev, requires_grad=True)
+    v = torch.from_numpy(inputs.normal_vector(ctx.n_dofs, 1)).to(dev)
+
+    def step():
+        R = ResidualFunction.apply(ctx, U, po, po, gc, lam, mu)
+        return torch.autograd.grad((R * v).sum(), (U, gc, lam, mu))
+
+    for _ in range(max(a.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    return {"mode": "adjoint", "workload": workload_name(a).split(", PDAS")[0] + ", FP64 residual + adjoint",
+            "n_dofs": ctx.n_dofs, "ms_per_forward_backward": ms, "dofs_per_s": ctx.n_dofs / (ms * 1e-3),
+            "passes": a.steps}
+
+
 def run_vcycle(a):
     """The FP32 (or FP64, --mg-precision) V-cycle of the workload's first Newton step, replayed
     --steps times after --warmup replays (CUDA events, warm caches)."""
@@ -653,6 +691,10 @@ def main():
     if a.mode == "vcycle":
         torch.cuda.set_device(local if world > 1 else 0)
         print(json.dumps(run_vcycle(a)))
+        return
+    if a.mode == "adjoint":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_adjoint(a)))
         return
     if world > 1:
         torch.cuda.set_device(local)
