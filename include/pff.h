@@ -151,7 +151,9 @@ int pff_apply_jacobian(pff_ctx* ctx, int level, const void* x, void* y, int prec
 int pff_residual(pff_ctx* ctx, double* r);
 
 /* Diagonal of the masked block-diagonal operator diag(G_uu, G_phiphi) on `level` (masked rows 1),
- * the Jacobi scaling of the smoother (Sec. 3.3). precision 64 or 32. */
+ * the Jacobi scaling of the smoother (Sec. 3.3). precision 64 or 32. With mg_precision 32 the
+ * multigrid's diagonal is computed in FP32 from the FP32 per-point data (what precision 32 returns);
+ * precision 64 computes the FP64 diagonals of all levels on first request. */
 int pff_diagonal(pff_ctx* ctx, int level, void* diag, int precision);
 
 /* lambda_max estimates of D^{-1} G_uu and D^{-1} G_phiphi on `level` (host double[2]). */
@@ -167,7 +169,8 @@ int pff_prolongate(pff_ctx* ctx, int level, const void* x_coarse, void* y_fine, 
 int pff_restrict(pff_ctx* ctx, int level, const void* x_fine, void* y_coarse, int precision);
 
 /* One application of the block-diagonal Chebyshev-Jacobi smoother on `level` with zero initial
- * guess: x = S(G_uu, G_phiphi) f (Sec. 3.3). */
+ * guess: x = S(G_uu, G_phiphi) f (Sec. 3.3), with the level's lambda_max estimate and the diagonal
+ * of the requested precision. */
 int pff_smooth(pff_ctx* ctx, int level, const void* f, void* x, int precision);
 
 /* Coarse-level solve: z = G_c^{-1} r by block forward substitution over the block lower triangular
