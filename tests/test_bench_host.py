@@ -62,3 +62,17 @@ def test_traffic_record_lookup(tmp_path):
     (tmp_path / "x.md").write_text("traffic-record: kernel=k dim=2 degree=2 split=1 dofs=100 bytes=5000 source=0\n")
     assert bench.measured_traffic(a, 200, str(tmp_path)) is None
     assert bench.measured_traffic(types.SimpleNamespace(dim=3, degree=2, split=1), 200, str(tmp_path)) is None
+
+
+def test_algorithmic_bytes_per_dof():
+    """Hand counts of the roofline's byte model: x and y once each, the per-point values of every
+    Gauss point of a cell spread over the cell's DoFs, one flag byte per node."""
+    import bench
+    assert [bench.qp_values(2, s) for s in (0, 1)] == [7, 11]
+    assert [bench.qp_values(3, s) for s in (0, 1)] == [10, 29]
+    # 2D Q2 Miehe FP32: 8 + 11 * 9 * 4 / 12 + 1/3
+    assert bench.apply_bytes_per_dof(2, 2, 1, 4) == pytest.approx(8 + 33 + 1 / 3)
+    # 3D Q2 Miehe FP32: 8 + 29 * 27 * 4 / 32 + 1/4
+    assert bench.apply_bytes_per_dof(3, 2, 1, 4) == pytest.approx(8 + 97.875 + 0.25)
+    # FP64: twice the vector and per-point bytes
+    assert bench.apply_bytes_per_dof(2, 2, 1, 8) == pytest.approx(16 + 66 + 1 / 3)
