@@ -22,6 +22,7 @@ finite element solvers for phase-field fracture problems"):
 
 Pins: every function is checked by ``tests/test_oracle_*.py`` against values the paper
 prints, closed forms, exact symbolic integration, finite differences or library routines.
-The V-cycle as a whole is "parity unpinned": each of its parts is pinned, and the cycle
-itself is only checked to contract.
+The V-cycle is pinned on two levels against the same cycle composed from dense matrices, with
+the smoother taken from its closed-form error polynomial; on more levels it is that composition
+applied recursively, and it is checked to contract.
 """
