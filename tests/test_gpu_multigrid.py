@@ -104,7 +104,7 @@ def test_eigen_smoother_coarse_vcycle_fp64(dim, p, N, split):
 
 @pytest.mark.parametrize("dim,p,N,split", [(2, 2, 8, 1), (3, 1, 8, 0)])
 def test_vcycle_fp32(dim, p, N, split):
-    """Mixed precision: FP32 levels, FP64 coarse solve; agrees with the FP64 cycle to FP32 accuracy."""
+    """Mixed precision: FP32 levels and FP32 coarse inverses; agrees with the FP64 cycle to FP32 accuracy."""
     pr = Problem(dim, p, N, split=split, seed=6, active_frac=0.2)
     lv = oracle_levels(pr)
     ctx = pr.context(mg_precision=32)
