@@ -4,10 +4,11 @@
 Default workload: the 2D notched specimen with Q2 elements on 256 x 256 cells (789,507 DoFs),
 seeded state u ~ N(0, (1e-3)^2), phi ~ U(0.9, 1) with phi = 0 on the slit, phi_old slightly above
 phi (about half of the phase-field DoFs end up in the active set). One step is one pass of the
-whole hot path: set_state (per-point tangent data), residual, active set (Alg. 1), multigrid
-setup (state transfer, diagonals, eigenvalue estimates, dense coarse inverse), flexible GMRES
-with the monolithic GMG preconditioner to 1e-6, and the Newton update. The multigrid runs in
-FP32 (mixed precision) unless --mg-precision 64.
+whole hot path: set_state with the active set of Alg. 1, then one Newton step: residual, active
+set, residual of the projected state, per-point tangent data, multigrid setup (state transfer,
+diagonals, eigenvalue estimates, dense coarse inverses), flexible GMRES with the monolithic GMG
+preconditioner to 1e-6, and the Newton update. The multigrid runs in FP32 (mixed precision)
+unless --mg-precision 64; the outer FP64 operator in double-word arithmetic unless --fp64-mode 0.
 
 value = DoFs processed per second of full Newton steps (n_dofs * steps / time, summed over
 ranks). Extra keys: the Jacobian-apply sweep (p = 1..4, FP64 and FP32), the Newton step with the
