@@ -162,6 +162,13 @@ class Context:
         except Exception:
             pass
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
+
     def level_sizes(self, level):
         nn, N = _LL(), _I()
         _check(self._lib.pff_level_sizes(self._h, level, ctypes.byref(nn), ctypes.byref(N)), "pff_level_sizes")
