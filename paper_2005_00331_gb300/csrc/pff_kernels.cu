@@ -1,11 +1,13 @@
-// pff_kernels.cu -- per-point setup, diagonal, parameter gradient, coarse assembly, transfers,
-// vector, Chebyshev, CG-Lanczos and Newton-step kernels of libpff.
+// pff_kernels.cu -- launch counter, dense coarse inverses, transfers, vector, Chebyshev,
+// CG-Lanczos and Newton-step kernels of libpff (per-point setup, diagonal, parameter gradient and
+// coarse assembly live in pff_qp.cu, pff_diag.cu and pff_pgrad.cu).
 #include <cstdint>
 #include <atomic>
 
 #include "pff_kernels.h"
 #include "pff_launch.h"
 #include "pff_op.cuh"
+#include "pff_point.cuh"
 
 namespace pff {
 
@@ -14,554 +16,6 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
-namespace {
-
-constexpr int BLK = 256;
-constexpr double RS2 = 0.70710678118654752440;
-
-inline unsigned grid_for(long long n, int blk = BLK) {
-  long long g = (n + blk - 1) / blk;
-  return (unsigned)(g < 1 ? 1 : g);
-}
-
-template <int DIM>
-__host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
-
-// Cell, quadrature-point and tile bookkeeping shared by the direct (one thread per point) kernels.
-template <int DIM, int P>
-struct CellQP {
-  int c[3], q[3];
-  long long tile, qidx;
-  __device__ void set(long long cell, int qq, const Geom& g) {
-    constexpr int n = P + 1;
-    c[0] = int(cell % g.N);
-    c[1] = int((cell / g.N) % g.N);
-    c[2] = DIM == 3 ? int(cell / ((long long)g.N * g.N)) : 0;
-    q[0] = qq % n;
-    q[1] = (qq / n) % n;
-    q[2] = DIM == 3 ? qq / (n * n) : 0;
-    const int TX = TileCfg<DIM, P>::TX, TY = TileCfg<DIM, P>::TY, TZ = TileCfg<DIM, P>::TZ;
-    const int tx = c[0] / TX, ty = c[1] / TY, tz = c[2] / TZ;
-    const int lx = c[0] % TX, ly = c[1] % TY, lz = c[2] % TZ;
-    tile = tx + (long long)g.ntile[0] * (ty + (long long)g.ntile[1] * tz);
-    qidx = ((long long)(lz * n + q[2]) * g.qpy + (ly * n + q[1])) * g.qpx + (lx * n + q[0]);
-  }
-  __device__ long long node(int a, const Geom& g) const {
-    constexpr int n = P + 1;
-    const int ax = a % n, ay = (a / n) % n, az = DIM == 3 ? a / (n * n) : 0;
-    long long nd = (c[0] * P + ax) + (long long)g.n1 * (c[1] * P + ay);
-    if (DIM == 3) nd += (long long)g.n1 * g.n1 * (c[2] * P + az);
-    return nd;
-  }
-  // N_a and grad N_a at this point
-  template <typename Real>
-  __device__ void shape(int a, const Tab<Real>& tb, Real& N, Real dN[DIM]) const {
-    constexpr int n = P + 1;
-    const int aa[3] = {a % n, (a / n) % n, DIM == 3 ? a / (n * n) : 0};
-    N = Real(1);
-    for (int t = 0; t < DIM; ++t) dN[t] = Real(1);
-    for (int s = 0; s < DIM; ++s) {
-      const Real Sv = tb.S[q[s]][aa[s]], Dv = tb.D[q[s]][aa[s]];
-      N *= Sv;
-      for (int t = 0; t < DIM; ++t) dN[t] *= (t == s ? Dv : Sv);
-    }
-  }
-  __device__ double jxw(const Tab<double>& tb) const {
-    double w = tb.hd;
-    for (int s = 0; s < DIM; ++s) w *= tb.W[q[s]];
-    return w;
-  }
-};
-
-// Evaluates a DoF vector (u, phi) at the point: grad u, phi, grad phi.
-template <int DIM, int P>
-__device__ void eval_state(const CellQP<DIM, P>& cq, const double* U, const Geom& g, const Tab<double>& tb,
-                           double gu[DIM][DIM], double& ph, double gph[DIM]) {
-  constexpr int NA = ipow<DIM>(P + 1);
-  for (int k = 0; k < DIM; ++k)
-    for (int j = 0; j < DIM; ++j) gu[k][j] = 0.0;
-  ph = 0.0;
-  for (int j = 0; j < DIM; ++j) gph[j] = 0.0;
-  for (int a = 0; a < NA; ++a) {
-    double N, dN[DIM];
-    cq.shape(a, tb, N, dN);
-    const long long nd = cq.node(a, g);
-    for (int k = 0; k < DIM; ++k) {
-      const double uk = U[k * g.nn + nd];
-      for (int j = 0; j < DIM; ++j) gu[k][j] += uk * dN[j];
-    }
-    const double pv = U[DIM * g.nn + nd];
-    ph += pv * N;
-    for (int j = 0; j < DIM; ++j) gph[j] += pv * dN[j];
-  }
-}
-
-template <int DIM, int P>
-__device__ double eval_scalar(const CellQP<DIM, P>& cq, const double* f, const Geom& g, const Tab<double>& tb) {
-  constexpr int NA = ipow<DIM>(P + 1);
-  double v = 0.0;
-  for (int a = 0; a < NA; ++a) {
-    double N, dN[DIM];
-    cq.shape(a, tb, N, dN);
-    v += f[cq.node(a, g)] * N;
-  }
-  return v;
-}
-
-}  // namespace
-
-// ===========================================================================================
-// Per-point data of the Jacobian: tangent of g(phi~) sigma^+ + sigma^- (Sec. 2.1, 3.5), the
-// coupling g'(phi) sigma^+ and the phase-field coefficients, times JxW (see qp_nv).
-// part QP_ALL: everything. Miehe split, in two passes: QP_STRAIN (what depends on u only: the
-// eigen-decomposition, the tangent, the phase-field coefficients, and sigma+ / E_s+ into sp64 for the
-// residual), then QP_PHASE (the coupling g'(phi) sigma+ from sp64 and phi, after each phi change).
-template <int DIM, int P, int SPLIT>
-__global__ void k_qp_setup(const double* __restrict__ U, const double* __restrict__ phit,
-                           const double* __restrict__ gcf, const double* __restrict__ lamf,
-                           const double* __restrict__ muf, Geom g, Tab<double> tb, MatConst mc,
-                           double* __restrict__ qp64, float* __restrict__ qp32, df64* __restrict__ qpdf,
-                           double* __restrict__ st64, double* __restrict__ sp64, int part) {
-  constexpr int NQ = ipow<DIM>(P + 1);
-  constexpr int NM = Mandel<DIM>::NM;
-  constexpr int NV = qp_nv(DIM, SPLIT);
-  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell * NQ) return;
-  CellQP<DIM, P> cq;
-  cq.set(t / NQ, int(t % NQ), g);
-  const double pt = eval_scalar<DIM, P>(cq, phit, g, tb);
-  const double gc = gcf ? eval_scalar<DIM, P>(cq, gcf, g, tb) : mc.gc;
-  const double lam = lamf ? eval_scalar<DIM, P>(cq, lamf, g, tb) : mc.lambda;
-  const double mu = muf ? eval_scalar<DIM, P>(cq, muf, g, tb) : mc.mu;
-  const double gt = deg_g(pt, mc.kappa);
-  if (st64) {
-    const long long sb = cq.tile * ST_NV * g.qpt + cq.qidx;
-    st64[sb] = gt;
-    st64[sb + g.qpt] = gc;
-    st64[sb + 2 * g.qpt] = lam;
-    st64[sb + 3 * g.qpt] = mu;
-  }
-  if (!qp64) return;  // residual state only (it does not depend on U)
-  const double jxw = cq.jxw(tb);
-  const long long base = cq.tile * NV * g.qpt + cq.qidx;
-  if (SPLIT == 1 && part == QP_PHASE) {
-    const double dgp = deg_dg(eval_scalar<DIM, P>(cq, U + DIM * g.nn, g, tb), mc.kappa);
-    const double* sp = sp64 + cq.tile * (NM + 1) * g.qpt + cq.qidx;
-    constexpr int OB = NM * (NM + 1) / 2;
-    for (int m = 0; m < NM; ++m) {
-      const double v = dgp * sp[m * g.qpt] * jxw;
-      const long long o = base + (OB + m) * g.qpt;
-      qp64[o] = v;
-      if (qp32) qp32[o] = (float)v;
-      if (qpdf) qpdf[o] = df_from(v);
-    }
-    return;
-  }
-  double gu[DIM][DIM], ph, gph[DIM];
-  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
-  const double dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
-
-  double e[DIM][DIM], tr = 0.0;
-  for (int i = 0; i < DIM; ++i) {
-    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
-    tr += e[i][i];
-  }
-  double em[NM];
-  for (int m = 0; m < NM; ++m) {
-    const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
-    em[m] = (i == j) ? e[i][i] : e[i][j] / RS2;
-  }
-  double vals[NV];
-  if constexpr (SPLIT == 0) {
-    double ee = 0.0;
-    for (int m = 0; m < NM; ++m) ee += em[m] * em[m];
-    const double Es = 0.5 * lam * tr * tr + mu * ee;
-    vals[0] = gt * lam * jxw;
-    vals[1] = gt * mu * jxw;
-    for (int m = 0; m < NM; ++m) vals[2 + m] = dgp * (2.0 * mu * em[m] + (m < DIM ? lam * tr : 0.0)) * jxw;
-    vals[2 + NM] = (ddg * Es + gc / mc.eps) * jxw;
-    vals[3 + NM] = gc * mc.eps * jxw;
-  } else {
-    double l[DIM], V[DIM][DIM];
-    eig_sym<DIM>(e, l, V);
-    double trs = tr;
-    snap_zero<DIM>(l, trs);
-    const double H = heav(trs), trp = pos(trs);
-    double sl2 = 0.0;
-    for (int t2 = 0; t2 < DIM; ++t2) sl2 += pos(l[t2]) * pos(l[t2]);
-    const double Esp = 0.5 * lam * trp * trp + mu * sl2;
-    // P+ = sum_i H(l_i) E_ii E_ii^T + sum_{i<j} theta_ij E_ij E_ij^T (orthonormal Mandel basis)
-    double Pp[NM][NM];
-    for (int a = 0; a < NM; ++a)
-      for (int b = 0; b < NM; ++b) Pp[a][b] = 0.0;
-    double epm[NM];
-    for (int m = 0; m < NM; ++m) epm[m] = 0.0;
-    for (int i = 0; i < DIM; ++i) {
-      for (int j = i; j < DIM; ++j) {
-        double vi[DIM], vj[DIM], Em[NM];
-        for (int k = 0; k < DIM; ++k) {
-          vi[k] = V[k][i];
-          vj[k] = V[k][j];
-        }
-        mandel_dyad<DIM>(vi, vj, i == j, Em);
-        const double th = (i == j) ? heav(l[i]) : theta_dd(l[i], l[j]);
-        for (int a = 0; a < NM; ++a)
-          for (int b = 0; b < NM; ++b) Pp[a][b] += th * Em[a] * Em[b];
-        if (i == j)
-          for (int m = 0; m < NM; ++m) epm[m] += pos(l[i]) * Em[m];
-      }
-    }
-    const double aH = gt * H + 1.0 - H;
-    int o = 0;
-    for (int a = 0; a < NM; ++a)
-      for (int b = a; b < NM; ++b) {
-        double Cab = 2.0 * mu * ((a == b ? 1.0 : 0.0) + (gt - 1.0) * Pp[a][b]);
-        if (a < DIM && b < DIM) Cab += lam * aH;
-        vals[o++] = Cab * jxw;
-      }
-    for (int m = 0; m < NM; ++m) {
-      const double spm = 2.0 * mu * epm[m] + (m < DIM ? lam * trp : 0.0);
-      vals[o + m] = dgp * spm * jxw;
-      if (part == QP_STRAIN) sp64[cq.tile * (NM + 1) * g.qpt + m * g.qpt + cq.qidx] = spm;
-    }
-    vals[o + NM] = (ddg * Esp + gc / mc.eps) * jxw;
-    vals[o + NM + 1] = gc * mc.eps * jxw;
-    if (part == QP_STRAIN) sp64[cq.tile * (NM + 1) * g.qpt + NM * g.qpt + cq.qidx] = Esp;
-  }
-  // QP_STRAIN leaves the coupling entries to the phase pass
-  constexpr int OB = SPLIT == 1 ? NM * (NM + 1) / 2 : 2;
-  for (int v = 0; v < NV; ++v) {
-    if (SPLIT == 1 && part == QP_STRAIN && v >= OB && v < OB + NM) continue;
-    qp64[base + v * g.qpt] = vals[v];
-    if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
-    if (qpdf) qpdf[base + v * g.qpt] = df_from(vals[v]);
-  }
-}
-
-cudaError_t launch_qp_setup(int dim, int p, int split, const double* U, const double* phit, const double* gcf,
-                            const double* lamf, const double* muf, const Geom& g, const Tab<double>& tb,
-                            const MatConst& mc, double* qp64, float* qp32, df64* qpdf, double* st64, cudaStream_t s,
-                            double* sp64, int part) {
-  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
-  const unsigned gr = grid_for(tot, 128);
-#define PFF_CASE(DD, PP, SS)                                                                          \
-  if (dim == DD && p == PP && split == SS) {                                                          \
-    count_launch(); k_qp_setup<DD, PP, SS><<<gr, 128, 0, s>>>(U, phit, gcf, lamf, muf, g, tb, mc, qp64, qp32, qpdf, st64, sp64, part); \
-    return cudaGetLastError();                                                                        \
-  }
-  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
-  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
-  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
-  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
-#undef PFF_CASE
-  return cudaErrorInvalidValue;
-}
-
-// ===========================================================================================
-// Diagonal of diag(G_uu, G_phiphi): for a basis function N_a e_k the quadratic form
-// e(N_a e_k) : C_eff : e(N_a e_k), and c N_a^2 + k |grad N_a|^2 for the phase field.
-template <int DIM, int P, int SPLIT, typename Real>
-__global__ void k_diagonal(const Real* __restrict__ qp, Geom g, Tab<Real> tb, Real* __restrict__ d) {
-  constexpr int NA = ipow<DIM>(P + 1), NQ = NA;
-  constexpr int NM = Mandel<DIM>::NM;
-  constexpr int NV = qp_nv(DIM, SPLIT);
-  constexpr int OFFB = SPLIT == 0 ? 2 : NM * (NM + 1) / 2;
-  constexpr Real R2 = Real(RS2);
-  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell * NA) return;
-  const long long cell = t / NA;
-  const int a = int(t % NA);
-  Real acc[DIM + 1];
-  for (int f = 0; f <= DIM; ++f) acc[f] = Real(0);
-  CellQP<DIM, P> cq;
-  long long nd = 0;
-  for (int q = 0; q < NQ; ++q) {
-    cq.set(cell, q, g);
-    if (q == 0) nd = cq.node(a, g);
-    Real N, dN[DIM];
-    cq.shape(a, tb, N, dN);
-    const Real* v = qp + cq.tile * NV * g.qpt + cq.qidx;
-    for (int k = 0; k < DIM; ++k) {
-      Real em[NM];
-      for (int m = 0; m < NM; ++m) {
-        const int i = Mandel<DIM>::ia(m), j = Mandel<DIM>::ib(m);
-        if (i == j) em[m] = (i == k) ? dN[k] : Real(0);
-        else em[m] = (i == k ? dN[j] : (j == k ? dN[i] : Real(0))) * R2;
-      }
-      Real val = Real(0);
-      if constexpr (SPLIT == 0) {
-        Real ee = Real(0);
-        for (int m = 0; m < NM; ++m) ee += em[m] * em[m];
-        val = v[0] * dN[k] * dN[k] + Real(2) * v[g.qpt] * ee;
-      } else {
-        for (int i = 0; i < NM; ++i)
-          for (int j = i; j < NM; ++j) {
-            const Real cij = v[sym_index(NM, i, j) * g.qpt];
-            val += (i == j ? Real(1) : Real(2)) * cij * em[i] * em[j];
-          }
-      }
-      acc[k] += val;
-    }
-    Real gg = Real(0);
-    for (int j = 0; j < DIM; ++j) gg += dN[j] * dN[j];
-    acc[DIM] += v[(OFFB + NM) * g.qpt] * N * N + v[(OFFB + NM + 1) * g.qpt] * gg;
-  }
-  for (int f = 0; f <= DIM; ++f) atomicAdd(d + f * g.nn + nd, acc[f]);
-}
-
-template <typename Real>
-__global__ void k_diag_finish(long long n, long long nn, const unsigned char* __restrict__ flags, Real* __restrict__ d) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int f = int(e / nn);
-  if ((flags[e % nn] >> f) & 1u) d[e] = Real(1);
-}
-
-template <typename Real>
-cudaError_t launch_diagonal(int dim, int p, int split, const Real* qp, const unsigned char* flags, const Geom& g,
-                            const Tab<Real>& tb, Real* d, cudaStream_t s) {
-  const long long n = (dim + 1) * g.nn;
-  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(Real) * n, s);
-  if (e != cudaSuccess) return e;
-  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
-  const unsigned gr = grid_for(tot, 128);
-  bool done = false;
-#define PFF_CASE(DD, PP, SS)                                                         \
-  if (!done && dim == DD && p == PP && split == SS) {                               \
-    count_launch(); k_diagonal<DD, PP, SS, Real><<<gr, 128, 0, s>>>(qp, g, tb, d);  \
-    done = true;                                                                     \
-  }
-  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
-  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
-  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
-  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
-#undef PFF_CASE
-  if (!done) return cudaErrorInvalidValue;
-  count_launch(); k_diag_finish<Real><<<grid_for(n), BLK, 0, s>>>(n, g.nn, flags, d);
-  return cudaGetLastError();
-}
-template cudaError_t launch_diagonal<double>(int, int, int, const double*, const unsigned char*, const Geom&,
-                                             const Tab<double>&, double*, cudaStream_t);
-template cudaError_t launch_diagonal<float>(int, int, int, const float*, const unsigned char*, const Geom&,
-                                            const Tab<float>&, float*, cudaStream_t);
-
-// ===========================================================================================
-// Parameter gradients: per point the partial derivatives of the residual's pointwise terms with
-// respect to G_c, lambda, mu, contracted with the test function v; then integrated against N_a.
-template <int DIM, int P, int SPLIT>
-__global__ void k_pgrad_qp(const double* __restrict__ U, const double* __restrict__ v,
-                           const double* __restrict__ st64, Geom g, Tab<double> tb, MatConst mc,
-                           double* __restrict__ tmp) {
-  constexpr int NQ = ipow<DIM>(P + 1);
-  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell * NQ) return;
-  CellQP<DIM, P> cq;
-  cq.set(t / NQ, int(t % NQ), g);
-  double gu[DIM][DIM], ph, gph[DIM], gv[DIM][DIM], vph, gvph[DIM];
-  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
-  eval_state<DIM, P>(cq, v, g, tb, gv, vph, gvph);
-  const double gt = st64[cq.tile * ST_NV * g.qpt + cq.qidx];
-  const double jxw = cq.jxw(tb);
-  const double dgp = deg_dg(ph, mc.kappa);
-  double e[DIM][DIM], tr = 0.0, divv = 0.0;
-  for (int i = 0; i < DIM; ++i) {
-    for (int j = 0; j < DIM; ++j) e[i][j] = 0.5 * (gu[i][j] + gu[j][i]);
-    tr += e[i][i];
-    divv += gv[i][i];
-  }
-  double gpgv = 0.0;
-  for (int j = 0; j < DIM; ++j) gpgv += gph[j] * gvph[j];
-  const double s_gc = -(1.0 - ph) / mc.eps * vph + mc.eps * gpgv;
-  double ep[DIM][DIM];
-  double trp;
-  if constexpr (SPLIT == 0) {
-    trp = tr;
-    for (int i = 0; i < DIM; ++i)
-      for (int j = 0; j < DIM; ++j) ep[i][j] = e[i][j];
-  } else {
-    double l[DIM], V[DIM][DIM];
-    eig_sym<DIM>(e, l, V);
-    double trs = tr;
-    snap_zero<DIM>(l, trs);
-    trp = pos(trs);
-    for (int i = 0; i < DIM; ++i)
-      for (int j = 0; j < DIM; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < DIM; ++k) s += pos(l[k]) * V[i][k] * V[j][k];
-        ep[i][j] = s;
-      }
-  }
-  // lambda: sigma+ = trp I, sigma- = (tr - trp) I, E+ = trp^2/2
-  const double s_lam = (gt * trp + (tr - trp)) * divv + dgp * 0.5 * trp * trp * vph;
-  // mu: sigma+ = 2 e+, sigma- = 2 (e - e+), E+ = e+ : e+
-  double s_mu = 0.0, epep = 0.0;
-  for (int i = 0; i < DIM; ++i)
-    for (int j = 0; j < DIM; ++j) {
-      s_mu += (gt * 2.0 * ep[i][j] + 2.0 * (e[i][j] - ep[i][j])) * gv[i][j];
-      epep += ep[i][j] * ep[i][j];
-    }
-  s_mu += dgp * epep * vph;
-  tmp[t] = s_gc * jxw;
-  tmp[ncell * NQ + t] = s_lam * jxw;
-  tmp[2 * ncell * NQ + t] = s_mu * jxw;
-}
-
-template <int DIM, int P>
-__global__ void k_pgrad_int(const double* __restrict__ tmp, Geom g, Tab<double> tb, double* __restrict__ o0,
-                            double* __restrict__ o1, double* __restrict__ o2) {
-  constexpr int NA = ipow<DIM>(P + 1), NQ = NA;
-  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell * NA) return;
-  const long long cell = t / NA;
-  const int a = int(t % NA);
-  double acc[3] = {0.0, 0.0, 0.0};
-  CellQP<DIM, P> cq;
-  long long nd = 0;
-  for (int q = 0; q < NQ; ++q) {
-    cq.set(cell, q, g);
-    if (q == 0) nd = cq.node(a, g);
-    double N, dN[DIM];
-    cq.shape(a, tb, N, dN);
-    for (int k = 0; k < 3; ++k) acc[k] += N * tmp[k * ncell * NQ + cell * NQ + q];
-  }
-  if (o0) atomicAdd(o0 + nd, acc[0]);
-  if (o1) atomicAdd(o1 + nd, acc[1]);
-  if (o2) atomicAdd(o2 + nd, acc[2]);
-}
-
-cudaError_t launch_param_grad(int dim, int p, int split, const double* U, const double* v, const double* st64,
-                              const Geom& g, const Tab<double>& tb, const MatConst& mc, double* tmp,
-                              double* out_gc, double* out_lam, double* out_mu, cudaStream_t s) {
-  for (double* o : {out_gc, out_lam, out_mu}) {
-    if (o) {
-      cudaError_t e = cudaMemsetAsync(o, 0, sizeof(double) * g.nn, s);
-      if (e != cudaSuccess) return e;
-    }
-  }
-  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long tot = ncell * (dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1));
-  const unsigned gr = grid_for(tot, 128);
-  bool done = false;
-#define PFF_CASE(DD, PP, SS)                                                                  \
-  if (!done && dim == DD && p == PP && split == SS) {                                        \
-    count_launch(); k_pgrad_qp<DD, PP, SS><<<gr, 128, 0, s>>>(U, v, st64, g, tb, mc, tmp);                   \
-    count_launch(); k_pgrad_int<DD, PP><<<gr, 128, 0, s>>>(tmp, g, tb, out_gc, out_lam, out_mu);             \
-    done = true;                                                                              \
-  }
-  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
-  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
-  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
-  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
-#undef PFF_CASE
-  return done ? cudaGetLastError() : cudaErrorInvalidValue;
-}
-
-// ===========================================================================================
-// Dense coarse operator: element matrices from the stored per-point data, one thread per
-// (cell, test DoF, trial DoF), accumulated into the u-u, phi-phi and phi-u blocks.
-template <int DIM, int P, int SPLIT>
-__global__ void k_coarse_asm(const double* __restrict__ qp64, Geom g, Tab<double> tb, double* __restrict__ Au,
-                             double* __restrict__ Ap, double* __restrict__ B) {
-  constexpr int NA = ipow<DIM>(P + 1), NQ = NA, NL = (DIM + 1) * NA;
-  const long long ncell = DIM == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncell * NL * NL) return;
-  const long long cell = t / (NL * NL);
-  const int i = int((t / NL) % NL), j = int(t % NL);
-  const int fi = i / NA, a = i % NA, fj = j / NA, b = j % NA;
-  if (fi < DIM && fj == DIM) return;  // G_uphi = 0
-  PWJac<DIM, double, SPLIT> pw;
-  pw.qp = qp64;
-  pw.qpt = g.qpt;
-  pw.tstride = (long long)qp_nv(DIM, SPLIT) * g.qpt;
-  pw.mode = JM_FULL;
-  CellQP<DIM, P> cq;
-  double val = 0.0;
-  long long na_ = 0, nb_ = 0;
-  for (int q = 0; q < NQ; ++q) {
-    cq.set(cell, q, g);
-    if (q == 0) {
-      na_ = cq.node(a, g);
-      nb_ = cq.node(b, g);
-    }
-    double Na, dNa[DIM], Nb, dNb[DIM];
-    cq.shape(a, tb, Na, dNa);
-    cq.shape(b, tb, Nb, dNb);
-    QPIn<DIM, double> in;
-    for (int k = 0; k < DIM; ++k)
-      for (int m = 0; m < DIM; ++m) in.gu[k][m] = (k == fj) ? dNb[m] : 0.0;
-    in.ph = (fj == DIM) ? Nb : 0.0;
-    for (int m = 0; m < DIM; ++m) in.gph[m] = (fj == DIM) ? dNb[m] : 0.0;
-    QPOut<DIM, double> o;
-    pw(cq.tile, cq.qidx, in, o);
-    if (fi < DIM) {
-      for (int m = 0; m < DIM; ++m) val += o.cu[fi][m] * dNa[m];
-    } else {
-      val += o.cv * Na;
-      for (int m = 0; m < DIM; ++m) val += o.cg[m] * dNa[m];
-    }
-  }
-  const long long nn = g.nn, nu = DIM * nn;
-  if (fi < DIM && fj < DIM) atomicAdd(Au + (fi * nn + na_) * nu + (fj * nn + nb_), val);
-  else if (fi == DIM && fj == DIM) atomicAdd(Ap + na_ * nn + nb_, val);
-  else atomicAdd(B + na_ * nu + (fj * nn + nb_), val);
-}
-
-__global__ void k_coarse_mask(int dim, long long nn, const unsigned char* __restrict__ flags, double* Au, double* Ap,
-                              double* B) {
-  const long long nu = dim * nn;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  // rows/cols of Au
-  if (t < nu * nu) {
-    const long long r = t / nu, c = t % nu;
-    const bool mr = (flags[r % nn] >> (r / nn)) & 1u, mc = (flags[c % nn] >> (c / nn)) & 1u;
-    if (mr || mc) Au[t] = (r == c) ? 1.0 : 0.0;
-  }
-  if (t < nn * nn) {
-    const long long r = t / nn, c = t % nn;
-    const bool mr = (flags[r] >> dim) & 1u, mc = (flags[c] >> dim) & 1u;
-    if (mr || mc) Ap[t] = (r == c) ? 1.0 : 0.0;
-  }
-  if (t < nn * nu) {
-    const long long r = t / nu, c = t % nu;
-    const bool mr = (flags[r] >> dim) & 1u, mc = (flags[c % nn] >> (c / nn)) & 1u;
-    if (mr || mc) B[t] = 0.0;
-  }
-}
-
-cudaError_t launch_coarse_assemble(int dim, int p, int split, const double* qp64, const unsigned char* flags,
-                                   const Geom& g, const Tab<double>& tb, double* Au, double* Ap, double* B,
-                                   cudaStream_t s) {
-  const long long nn = g.nn, nu = dim * nn;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(Au, 0, sizeof(double) * nu * nu, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(Ap, 0, sizeof(double) * nn * nn, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(B, 0, sizeof(double) * nn * nu, s)) != cudaSuccess) return e;
-  const long long ncell = dim == 2 ? (long long)g.N * g.N : (long long)g.N * g.N * g.N;
-  const int na = dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
-  const long long nl = (dim + 1) * na;
-  const unsigned gr = grid_for(ncell * nl * nl, 128);
-  bool done = false;
-#define PFF_CASE(DD, PP, SS)                                             \
-  if (!done && dim == DD && p == PP && split == SS) {                   \
-    count_launch(); k_coarse_asm<DD, PP, SS><<<gr, 128, 0, s>>>(qp64, g, tb, Au, Ap, B); \
-    done = true;                                                         \
-  }
-  PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
-  PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
-  PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)
-  PFF_CASE(3, 1, 1) PFF_CASE(3, 2, 1) PFF_CASE(3, 3, 1) PFF_CASE(3, 4, 1)
-#undef PFF_CASE
-  if (!done) return cudaErrorInvalidValue;
-  count_launch(); k_coarse_mask<<<grid_for(nu * nu), BLK, 0, s>>>(dim, nn, flags, Au, Ap, B);
-  return cudaGetLastError();
-}
 
 // In-place Gauss-Jordan inversion without pivoting, blocked by GJB pivots. One block step with
 // pivot block K (rows/columns k0 .. k0+bk-1) and P = A_KK^{-1} performs
@@ -774,13 +228,15 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
   Real acc[DIM + 1];
 #pragma unroll
   for (int f = 0; f <= DIM; ++f) acc[f] = Real(0);
-#pragma unroll
+  // in 3D only the innermost direction is unrolled: the (4p+1)^3 stencil unrolled whole made this
+  // file take minutes to compile (2D unrolls the whole (4p+1)^2 stencil as before)
+#pragma unroll 1
   for (int oz = 0; oz < (DIM == 3 ? NW : 1); ++oz) {
     const int iz = DIM == 3 ? b[2] + oz - 2 * P : 0;
     if (DIM == 3 && (iz < 0 || iz >= gf.n1)) continue;
     const Real w3 = DIM == 3 ? W[kk[2]][oz] : Real(1);
     if (w3 == Real(0)) continue;
-#pragma unroll
+#pragma unroll(DIM == 2 ? NW : 1)
     for (int oy = 0; oy < NW; ++oy) {
       const int iy = b[1] + oy - 2 * P;
       if (iy < 0 || iy >= gf.n1) continue;

@@ -1,0 +1,106 @@
+// pff_point.cuh -- bookkeeping shared by the one-thread-per-point kernels of libpff (internal):
+// launch shape helpers, the cell / Gauss point / tile index of a point, shape functions and the
+// evaluation of nodal fields at a point.
+#pragma once
+#include "pff_common.cuh"
+#include "pff_kernels.h"
+
+namespace pff {
+
+namespace {
+
+constexpr int BLK = 256;
+constexpr double RS2 = 0.70710678118654752440;
+
+inline unsigned grid_for(long long n, int blk = BLK) {
+  long long g = (n + blk - 1) / blk;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <int DIM>
+__host__ __device__ constexpr int ipow(int b) { return DIM == 2 ? b * b : b * b * b; }
+
+// Cell, quadrature-point and tile bookkeeping shared by the direct (one thread per point) kernels.
+template <int DIM, int P>
+struct CellQP {
+  int c[3], q[3];
+  long long tile, qidx;
+  __device__ void set(long long cell, int qq, const Geom& g) {
+    constexpr int n = P + 1;
+    c[0] = int(cell % g.N);
+    c[1] = int((cell / g.N) % g.N);
+    c[2] = DIM == 3 ? int(cell / ((long long)g.N * g.N)) : 0;
+    q[0] = qq % n;
+    q[1] = (qq / n) % n;
+    q[2] = DIM == 3 ? qq / (n * n) : 0;
+    const int TX = TileCfg<DIM, P>::TX, TY = TileCfg<DIM, P>::TY, TZ = TileCfg<DIM, P>::TZ;
+    const int tx = c[0] / TX, ty = c[1] / TY, tz = c[2] / TZ;
+    const int lx = c[0] % TX, ly = c[1] % TY, lz = c[2] % TZ;
+    tile = tx + (long long)g.ntile[0] * (ty + (long long)g.ntile[1] * tz);
+    qidx = ((long long)(lz * n + q[2]) * g.qpy + (ly * n + q[1])) * g.qpx + (lx * n + q[0]);
+  }
+  __device__ long long node(int a, const Geom& g) const {
+    constexpr int n = P + 1;
+    const int ax = a % n, ay = (a / n) % n, az = DIM == 3 ? a / (n * n) : 0;
+    long long nd = (c[0] * P + ax) + (long long)g.n1 * (c[1] * P + ay);
+    if (DIM == 3) nd += (long long)g.n1 * g.n1 * (c[2] * P + az);
+    return nd;
+  }
+  // N_a and grad N_a at this point
+  template <typename Real>
+  __device__ void shape(int a, const Tab<Real>& tb, Real& N, Real dN[DIM]) const {
+    constexpr int n = P + 1;
+    const int aa[3] = {a % n, (a / n) % n, DIM == 3 ? a / (n * n) : 0};
+    N = Real(1);
+    for (int t = 0; t < DIM; ++t) dN[t] = Real(1);
+    for (int s = 0; s < DIM; ++s) {
+      const Real Sv = tb.S[q[s]][aa[s]], Dv = tb.D[q[s]][aa[s]];
+      N *= Sv;
+      for (int t = 0; t < DIM; ++t) dN[t] *= (t == s ? Dv : Sv);
+    }
+  }
+  __device__ double jxw(const Tab<double>& tb) const {
+    double w = tb.hd;
+    for (int s = 0; s < DIM; ++s) w *= tb.W[q[s]];
+    return w;
+  }
+};
+
+// Evaluates a DoF vector (u, phi) at the point: grad u, phi, grad phi.
+template <int DIM, int P>
+__device__ void eval_state(const CellQP<DIM, P>& cq, const double* U, const Geom& g, const Tab<double>& tb,
+                           double gu[DIM][DIM], double& ph, double gph[DIM]) {
+  constexpr int NA = ipow<DIM>(P + 1);
+  for (int k = 0; k < DIM; ++k)
+    for (int j = 0; j < DIM; ++j) gu[k][j] = 0.0;
+  ph = 0.0;
+  for (int j = 0; j < DIM; ++j) gph[j] = 0.0;
+  for (int a = 0; a < NA; ++a) {
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    const long long nd = cq.node(a, g);
+    for (int k = 0; k < DIM; ++k) {
+      const double uk = U[k * g.nn + nd];
+      for (int j = 0; j < DIM; ++j) gu[k][j] += uk * dN[j];
+    }
+    const double pv = U[DIM * g.nn + nd];
+    ph += pv * N;
+    for (int j = 0; j < DIM; ++j) gph[j] += pv * dN[j];
+  }
+}
+
+template <int DIM, int P>
+__device__ double eval_scalar(const CellQP<DIM, P>& cq, const double* f, const Geom& g, const Tab<double>& tb) {
+  constexpr int NA = ipow<DIM>(P + 1);
+  double v = 0.0;
+  for (int a = 0; a < NA; ++a) {
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    v += f[cq.node(a, g)] * N;
+  }
+  return v;
+}
+
+}  // namespace
+
+}  // namespace pff
