@@ -555,7 +555,8 @@ def run_vcycle(a):
 
 def run_loadsteps(a):
     """Quasi-static loading from rest: --load-steps steps of --load-inc on the top face, each a full
-    active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid."""
+    active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid. Each step
+    also records the force on the top face (the load-displacement curve of Sec. 5.1)."""
     import torch
 
     from paper_2005_00331_gb300 import setup_mesh
@@ -584,9 +585,11 @@ def run_loadsteps(a):
             t0 = time.perf_counter()
             st, reps = ctx.solve_load_step(k * a.load_inc, max_iters=a.newton_max, newton_rtol=a.newton_rtol,
                                            check=False)
+            sec = time.perf_counter() - t0
             steps.append({"load": k * a.load_inc, "status": st, "newton_steps": len(reps),
-                          "gmres_iters": [r["gmres_iters"] for r in reps], "seconds": time.perf_counter() - t0,
-                          "n_active": reps[-1]["n_active"] if reps else None})
+                          "gmres_iters": [r["gmres_iters"] for r in reps], "seconds": sec,
+                          "n_active": reps[-1]["n_active"] if reps else None,
+                          "reaction_force": ctx.reaction_force()})  # the load-displacement curve
             print("fp%d load step %d: %s" % (prec, k, json.dumps(steps[-1])), file=sys.stderr, flush=True)
             newton += len(reps)
             status = status or st

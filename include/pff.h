@@ -150,6 +150,13 @@ int pff_apply_jacobian(pff_ctx* ctx, int level, const void* x, void* y, int prec
 /* r = R(U) of Eq. (residual) at the current state, FP64, rows of Dirichlet DoFs set to 0. */
 int pff_residual(pff_ctx* ctx, double* r);
 
+/* Force on the loaded top face of the tension test (Sec. 5.1), the ordinate of its load-displacement
+ * curve, at the current state: the u_dim rows of R(U) (Dirichlet rows kept) summed over the nodes of
+ * the top face, i.e. the residual's u-equation tested with the unit displacement of that face in the
+ * loading direction (the consistent nodal reaction; for a uniform stress it is the face integral of
+ * sigma_dd). *force is a host double. Synchronous. Errors: INVALID_ARG, NO_STATE. */
+int pff_reaction_force(pff_ctx* ctx, double* force);
+
 /* Diagonal of the masked block-diagonal operator diag(G_uu, G_phiphi) on `level` (masked rows 1),
  * the Jacobi scaling of the smoother (Sec. 3.3). precision 64 or 32. With mg_precision 32 the
  * multigrid's diagonal is computed in FP32 from the FP32 per-point data (what precision 32 returns);
@@ -208,6 +215,17 @@ int pff_solve_pdas(pff_ctx* ctx, int max_iters, double newton_rtol, double* U_ou
  * advances only when the step converges. Same outputs and errors as pff_solve_pdas. */
 int pff_solve_load_step(pff_ctx* ctx, double load, int max_iters, double newton_rtol, pff_report* reps,
                         int* n_steps);
+
+/* Phase-field history of the load-step loop, for checkpoint and resume: phi1 = phase field after the
+ * last converged load step, phi2 = the one before (device arrays of n_nodes doubles); n_hist (host
+ * int) = how many are known (0, 1 or 2). pff_get_history copies the known ones (outputs may be NULL;
+ * unknown ones are left untouched). pff_set_history installs a history after pff_set_state (which
+ * clears it): with the state U and the history of a checkpoint taken after a converged load step, the
+ * next pff_solve_load_step continues that run (same iterates up to the order of the floating-point
+ * sums of shared nodes). Synchronous. Errors: INVALID_ARG (n_hist outside 0..2, or a needed array
+ * NULL), NO_STATE (pff_set_history before pff_set_state). */
+int pff_get_history(pff_ctx* ctx, double* phi1, double* phi2, int* n_hist);
+int pff_set_history(pff_ctx* ctx, const double* phi1, const double* phi2, int n_hist);
 
 /* Parameter gradients of the residual (not in the paper; needed for adjoints): for a test vector v
  * (DoF layout), g_gc = (dR/dG_c)^T v, g_lambda = (dR/dlambda)^T v, g_mu = (dR/dmu)^T v with the

@@ -15,7 +15,7 @@ finite element solvers for phase-field fracture problems"):
                   (lin_lambda), (lin_v) and Alg. 2, and the tangent of the split stress (Sec. 2.1, 3.5).
 * ``fe``       -- the residual of Eq. (residual) and the Jacobian of Eq. (G), both assembled cell by
                   cell from full tensor-product tables (no sum factorisation), the energy of Sec. 2.1,
-                  lumped mass, parameter gradients of the residual.
+                  lumped mass, parameter gradients of the residual, the force on the loaded face.
 * ``solvers``  -- Alg. 1 (active set, one primal-dual active-set step), transfers between nested
                   meshes, Chebyshev-Jacobi smoothing and eigenvalue estimation (Sec. 3.3), the
                   monolithic V-cycle with block-diagonal smoother, flexible GMRES.

@@ -123,6 +123,17 @@ def residual(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=No
     return R
 
 
+def reaction_force(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=None):
+    """Force on the loaded (top) face of the tension test of Sec. 5.1, the ordinate of its
+    load-displacement curve: the u_d-rows of the residual, Dirichlet rows kept, summed over the
+    top-face nodes. That sum is the u-equation tested with w = e_d times the sum of the top-face basis
+    functions, i.e. the work of the stress g(phi~) sigma^+ + sigma^- on the field that moves the top
+    face by a unit amount in the loading direction (the consistent nodal reaction; for a homogeneous
+    stress it equals the face integral of sigma_dd)."""
+    R = residual(mesh, prm, U, phi_tilde, gc_field, lam_field, mu_field, zero_dirichlet=False)
+    return float(R[mesh.dof(mesh.dim - 1, mesh.top_nodes())].sum())
+
+
 def energy(mesh, prm, U, gc_field=None, lam_field=None, mu_field=None):
     """Discrete energy of Sec. 2.1 with the split, evaluated by the same Gauss rule:
     int g(phi) E_s^+ + E_s^- + G_c/2 ((1 - phi)^2/eps + eps |grad phi|^2)."""

@@ -7,7 +7,7 @@ namespace pff {
 template <int DIM, int P, int SPLIT>
 static cudaError_t run_res(const double* U, double* r, const unsigned char* flags, const Geom& g,
                            const Tab<double>& tb, const double* st, const double* sp, double eps, double kappa,
-                           cudaStream_t s) {
+                           int outmask, cudaStream_t s) {
   size_t smem;
   if constexpr (DIM == 2) smem = op2d_smem<P, double>();
   else smem = op3d_smem<P, double>();
@@ -32,7 +32,7 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
   pw.hd = tb.hd;
   pw.eps = eps;
   pw.kappa = kappa;
-  OpArgs oa{IN_RAW, OUT_ZERO_DIRICHLET};
+  OpArgs oa{IN_RAW, outmask};
   dim3 blk(Tile3<P>::QPX, Tile3<P>::QPY, Tile3<P>::TZ);
   if constexpr (DIM == 2) blk = dim3(Tile2<P>::QPX, Tile2<P>::TY);
   if (g.ntiles > 0) { count_launch(); kern<<<(unsigned)g.ntiles, blk, smem, s>>>(U, r, flags, g, tb, pw, oa); }
@@ -41,9 +41,11 @@ static cudaError_t run_res(const double* U, double* r, const unsigned char* flag
 
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* st, const double* sp, double eps,
-                       double kappa, cudaStream_t s) {
-#define PFF_CASE(DD, PP, SS) \
-  if (dim == DD && p == PP && split == SS) return run_res<DD, PP, SS>(U, r, flags, g, tb, st, sp, eps, kappa, s);
+                       double kappa, cudaStream_t s, int outmask) {
+  if (outmask != OUT_ZERO_DIRICHLET && outmask != OUT_RAW) return cudaErrorInvalidValue;
+#define PFF_CASE(DD, PP, SS)                    \
+  if (dim == DD && p == PP && split == SS)      \
+    return run_res<DD, PP, SS>(U, r, flags, g, tb, st, sp, eps, kappa, outmask, s);
   PFF_CASE(2, 1, 0) PFF_CASE(2, 2, 0) PFF_CASE(2, 3, 0) PFF_CASE(2, 4, 0)
   PFF_CASE(2, 1, 1) PFF_CASE(2, 2, 1) PFF_CASE(2, 3, 1) PFF_CASE(2, 4, 1)
   PFF_CASE(3, 1, 0) PFF_CASE(3, 2, 0) PFF_CASE(3, 3, 0) PFF_CASE(3, 4, 0)

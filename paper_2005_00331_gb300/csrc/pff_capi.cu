@@ -493,7 +493,7 @@ int ensure_diag64(pff_ctx* c) {
   return PFF_OK;
 }
 
-int residual_into(pff_ctx* c, double* r) {
+int residual_into(pff_ctx* c, double* r, int outmask = OUT_ZERO_DIRICHLET) {
   CR(ensure_st(c));
   LevelData& L = c->lv[0];
   if (L.sp64) CR(ensure_strain(c));
@@ -501,7 +501,7 @@ int residual_into(pff_ctx* c, double* r) {
   const bool timed = prof_on(c, PFF_PROF_RESIDUAL);
   if (timed) CR(prof_mark(c));
   CK(launch_res(c->dim, c->p, c->prm.split, L.U, r, L.flags, L.g, L.t64, L.st64, L.sp64, c->prm.eps, c->prm.kappa,
-                c->s));
+                c->s, outmask));
   if (timed) CR(prof_mark(c));
   return PFF_OK;
 }
@@ -1270,6 +1270,48 @@ int pff_apply_jacobian(pff_ctx* c, int level, const void* x, void* y, int precis
 int pff_residual(pff_ctx* c, double* r) {
   if (!c || !r) return PFF_ERR_INVALID_ARG;
   return residual_into(c, r);
+}
+
+int pff_reaction_force(pff_ctx* c, double* force) {
+  if (!c || !force) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  LevelData& L = c->lv[0];
+  double* r = c->scratch;  // the full residual, Dirichlet rows kept
+  CR(residual_into(c, r, OUT_RAW));
+  // the top face (last coordinate index n1 - 1) is the last n1^(dim-1) nodes of the lexicographic order
+  const long long nface = c->dim == 2 ? (long long)L.g.n1 : (long long)L.g.n1 * L.g.n1;
+  std::vector<double> h((size_t)nface);
+  CK(cudaMemcpyAsync(h.data(), r + (long long)(c->dim - 1) * L.nn + (L.nn - nface), sizeof(double) * nface,
+                     cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  double f = 0.0;
+  for (double v : h) f += v;
+  *force = f;
+  return PFF_OK;
+}
+
+int pff_get_history(pff_ctx* c, double* phi1, double* phi2, int* n_hist) {
+  if (!c || !n_hist) return PFF_ERR_INVALID_ARG;
+  const long long nn = c->lv[0].nn;
+  if (phi1 && c->nhist >= 1)
+    CK(cudaMemcpyAsync(phi1, c->hist1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+  if (phi2 && c->nhist >= 2)
+    CK(cudaMemcpyAsync(phi2, c->hist2, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  *n_hist = c->nhist;
+  return PFF_OK;
+}
+
+int pff_set_history(pff_ctx* c, const double* phi1, const double* phi2, int n_hist) {
+  if (!c || n_hist < 0 || n_hist > 2 || (n_hist >= 1 && !phi1) || (n_hist == 2 && !phi2))
+    return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  const long long nn = c->lv[0].nn;
+  if (n_hist >= 1) CK(cudaMemcpyAsync(c->hist1, phi1, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+  if (n_hist == 2) CK(cudaMemcpyAsync(c->hist2, phi2, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  c->nhist = n_hist;
+  return PFF_OK;
 }
 
 int pff_diagonal(pff_ctx* c, int level, void* diag, int precision) {

@@ -67,9 +67,10 @@ cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y
                            cudaStream_t s);
 // r = R(U) (FP64) from the per-point state st: [tile][4][qpt] = g(phi~), G_c, lambda, mu. With the
 // Miehe split and sp != null, sigma+ and E_s+ per point are read from sp ([tile][NM + 1][qpt], the
-// strain pass of the same u) instead of recomputing the eigen-decomposition.
+// strain pass of the same u) instead of recomputing the eigen-decomposition. r must be zeroed by the
+// caller. outmask: OUT_ZERO_DIRICHLET (Dirichlet rows 0) or OUT_RAW (every row, for reactions).
 cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* st, const double* sp, double eps,
-                       double kappa, cudaStream_t s);
+                       double kappa, cudaStream_t s, int outmask = OUT_ZERO_DIRICHLET);
 
 }  // namespace pff

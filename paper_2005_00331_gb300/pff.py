@@ -61,6 +61,9 @@ _SIGS = {
     "pff_get_active": (_I, [_P, _P]),
     "pff_apply_jacobian": (_I, [_P, _I, _P, _P, _I, _I]),
     "pff_residual": (_I, [_P, _P]),
+    "pff_reaction_force": (_I, [_P, ctypes.POINTER(_D)]),
+    "pff_get_history": (_I, [_P, _P, _P, ctypes.POINTER(_I)]),
+    "pff_set_history": (_I, [_P, _P, _P, _I]),
     "pff_diagonal": (_I, [_P, _I, _P, _I]),
     "pff_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
     "pff_level_state": (_I, [_P, _I, _P]),
@@ -318,6 +321,53 @@ class Context:
         if check:
             _check(st, "pff_solve_load_step")
         return st, [reps[i].as_dict() for i in range(n.value)]
+
+    def reaction_force(self):
+        """Force on the loaded top face at the current state (pff_reaction_force), a Python float."""
+        f = _D()
+        _check(self._lib.pff_reaction_force(self._h, ctypes.byref(f)), "pff_reaction_force")
+        return f.value
+
+    def get_history(self):
+        """(n_hist, phi1, phi2): the phase fields of the last two converged load steps (None where unknown)."""
+        nn = self.n_nodes
+        phi1 = torch.empty(nn, dtype=torch.float64, device=self._dev())
+        phi2 = torch.empty(nn, dtype=torch.float64, device=self._dev())
+        n = _I()
+        _check(self._lib.pff_get_history(self._h, _ptr(phi1), _ptr(phi2), ctypes.byref(n)), "pff_get_history")
+        return n.value, (phi1 if n.value >= 1 else None), (phi2 if n.value >= 2 else None)
+
+    def set_history(self, phi1=None, phi2=None):
+        """Installs the load-step history after set_state (phi2 only together with phi1)."""
+        if phi2 is not None and phi1 is None:
+            raise ValueError("phi2 needs phi1")
+        n = 0 if phi1 is None else (1 if phi2 is None else 2)
+        nn = self.n_nodes
+        _check(self._lib.pff_set_history(self._h, _ptr(phi1, numel=nn), _ptr(phi2, numel=nn), n),
+               "pff_set_history")
+
+    def checkpoint(self, load=float("nan")):
+        """Host copy of what the next load step reads (state and phase-field history), as a
+        ``checkpoint.Checkpoint``; ``load`` records the last converged top displacement."""
+        from . import checkpoint as ck
+        n, phi1, phi2 = self.get_history()
+        host = (lambda t: t.cpu().numpy() if t is not None else None)
+        return ck.Checkpoint(self.params.dim, self.params.degree, self.params.n_cells_1d, float(load),
+                             self.get_state().cpu().numpy(), n, host(phi1), host(phi2))
+
+    def resume(self, ckpt, gc_field=None, lambda_field=None, mu_field=None):
+        """Restores a checkpoint into this context (same mesh): set_state with phi_old = the last
+        converged phase field (the state's own phase field when no step has converged), then the
+        history. The next solve_load_step continues the checkpointed run."""
+        ckpt.check_mesh(self.params.dim, self.params.degree, self.params.n_cells_1d)
+        dev = self._dev()
+        dvec = (lambda a: torch.from_numpy(a).to(device=dev, dtype=torch.float64).contiguous())
+        U = dvec(ckpt.U)
+        phi1 = dvec(ckpt.phi1) if ckpt.n_hist >= 1 else None
+        phi2 = dvec(ckpt.phi2) if ckpt.n_hist >= 2 else None
+        phi_old = phi1 if phi1 is not None else U[self.params.dim * self.n_nodes:].contiguous()
+        self.set_state(U, phi_old, None, None, gc_field, lambda_field, mu_field)
+        self.set_history(phi1, phi2)
 
     def param_grad(self, v):
         outs = [torch.empty(self.n_nodes, dtype=torch.float64, device=v.device) for _ in range(3)]

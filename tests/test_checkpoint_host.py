@@ -1,0 +1,77 @@
+"""Host logic of the load-step checkpoint file (no GPU): round trip, and the checks that reject a
+file of another kind, sizes that do not fit the mesh, a bad history count and a foreign mesh."""
+import numpy as np
+import pytest
+
+from paper_2005_00331_gb300 import checkpoint as ck
+
+
+def make(n_hist, dim=2, degree=2, cells=4, seed=0):
+    rng = np.random.default_rng(seed)
+    nn = (degree * cells + 1) ** dim
+    return ck.Checkpoint(dim, degree, cells, 3e-3, rng.normal(size=(dim + 1) * nn), n_hist,
+                         rng.uniform(size=nn) if n_hist >= 1 else None,
+                         rng.uniform(size=nn) if n_hist >= 2 else None)
+
+
+@pytest.mark.parametrize("n_hist", [0, 1, 2])
+@pytest.mark.parametrize("dim,degree,cells", [(2, 2, 4), (3, 1, 3)])
+def test_round_trip(tmp_path, n_hist, dim, degree, cells):
+    a = make(n_hist, dim, degree, cells)
+    path = str(tmp_path / "c.npz")
+    ck.save(path, a)
+    b = ck.load(path)
+    assert (b.dim, b.degree, b.n_cells_1d, b.n_hist, b.load) == (dim, degree, cells, n_hist, 3e-3)
+    assert np.array_equal(a.U, b.U)
+    for k, (x, y) in enumerate(((a.phi1, b.phi1), (a.phi2, b.phi2)), start=1):
+        if n_hist >= k:
+            assert np.array_equal(x, y)
+        else:
+            assert y is None
+    b.check_mesh(dim, degree, cells)
+
+
+def test_rejects_other_files(tmp_path):
+    path = str(tmp_path / "other.npz")
+    np.savez(path, format=np.array("something-else"), U=np.zeros(3))
+    with pytest.raises(ValueError):
+        ck.load(path)
+    np.savez(path, U=np.zeros(3))
+    with pytest.raises(ValueError):
+        ck.load(path)
+
+
+def test_rejects_bad_contents(tmp_path):
+    a = make(2)
+    a.U = a.U[:-1]
+    with pytest.raises(ValueError):
+        ck.save(str(tmp_path / "x.npz"), a)
+    a = make(2)
+    a.phi2 = None
+    with pytest.raises(ValueError):
+        a.validate()
+    a = make(1)
+    a.n_hist = 3
+    with pytest.raises(ValueError):
+        a.validate()
+    a = make(0)
+    a.U[5] = np.nan
+    with pytest.raises(ValueError):
+        a.validate()
+    with pytest.raises(ValueError):
+        make(1).check_mesh(2, 2, 8)
+    with pytest.raises(ValueError):
+        make(1).check_mesh(3, 2, 4)
+
+
+def test_truncated_history_on_disk(tmp_path):
+    """A file whose phi arrays do not match its declared history count is rejected on load."""
+    a = make(2)
+    path = str(tmp_path / "t.npz")
+    ck.save(path, a)
+    with np.load(path) as z:
+        parts = {k: z[k] for k in z.files}
+    parts["phi2"] = parts["phi2"][:-1]
+    np.savez(path, **parts)
+    with pytest.raises(ValueError):
+        ck.load(path)

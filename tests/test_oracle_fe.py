@@ -235,3 +235,46 @@ def test_param_grad_finite_differences(split):
         fm[key] = fields[key] - h * dirv
         fd = (fe.residual(m, prm, U, pt, **fp) - fe.residual(m, prm, U, pt, **fm)) @ v / (2 * h)
         assert abs(fd - grads[gi] @ dirv) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("dim,p,N", [(2, 1, 4), (2, 3, 3), (3, 2, 2)])
+@pytest.mark.parametrize("split", [mat.SPLIT_NONE, mat.SPLIT_MIEHE])
+@pytest.mark.parametrize("load", [2e-3, -2e-3])
+def test_reaction_force_uniaxial_strain(dim, p, N, split, load):
+    """Load-displacement ordinate in closed form: u_d = load x_d (top face moved by `load`, bottom
+    fixed, no lateral motion) and phi = phi~ = c give a uniform stress with sigma_dd = (lambda + 2 mu)
+    load on the unit top face. Without a split all of it is degraded by g(c); with the Miehe split a
+    stretched specimen (load > 0) is degraded and a compressed one is not."""
+    c = 0.7
+    m = M.Mesh(dim, p, N)
+    U = np.zeros(m.n_dofs)
+    U[(dim - 1) * m.n_nodes:dim * m.n_nodes] = load * m.coords[:, dim - 1]
+    U[dim * m.n_nodes:] = c
+    F = fe.reaction_force(m, fe.Params(LAM, MU, GC, 0.2, KAPPA, split), U, np.full(m.n_nodes, c))
+    degraded = split == mat.SPLIT_NONE or load > 0
+    expect = (LAM + 2 * MU) * load * (mat.g(c, KAPPA) if degraded else 1.0)
+    assert abs(F - expect) <= 1e-13 * abs(expect)
+
+
+def test_reaction_force_balance():
+    """The basis functions sum to one and a rigid translation has no strain, so every u-component of
+    the residual (Dirichlet rows kept) sums to zero over all nodes for any state; at a converged load
+    step the interior u-rows vanish as well, and the top reaction equals minus the bottom one."""
+    from oracle import solvers as S
+    m = M.Mesh(2, 1, 8)
+    prm = fe.Params(LAM, MU, GC, 2.0 / 8, KAPPA, mat.SPLIT_MIEHE)
+    rng = np.random.default_rng(12)
+    U, phit = random_state(m, rng)
+    R = fe.residual(m, prm, U, phit, zero_dirichlet=False)
+    for k in range(2):
+        assert abs(R[k * m.n_nodes:(k + 1) * m.n_nodes].sum()) <= 1e-14 * np.abs(R).sum()
+    U = m.dirichlet_values(0.0)
+    phi = np.ones(m.n_nodes)
+    phi[m.slit_nodes()] = 0.0
+    U[2 * m.n_nodes:] = phi
+    for Uk in S.load_steps(m, prm, U, [4e-3, 8e-3]):
+        phik = Uk[2 * m.n_nodes:]
+        top = fe.reaction_force(m, prm, Uk, phik)
+        R = fe.residual(m, prm, Uk, phik, zero_dirichlet=False)
+        bottom = R[m.dof(1, m.bottom_nodes())].sum()
+        assert top > 0 and abs(top + bottom) <= 1e-10 * top
