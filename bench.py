@@ -49,9 +49,11 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the apply sweep and the FP64-MG comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
-    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps", "vcycle", "adjoint"], default="newton",
+    ap.add_argument("--mode", choices=["newton", "apply", "pdas", "loadsteps", "vcycle", "adjoint", "spmv"],
+                    default="newton",
                     help="apply: time only the finest-level Jacobian apply (--precision) on the workload; "
-                         "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid")
+                         "pdas: full active-set Newton solve to --newton-rtol, FP64 vs FP32 multigrid; "
+                         "spmv: assembled-matrix (cuSPARSE) product against the matrix-free one, p = 1..4")
     ap.add_argument("--state", choices=["random", "tension"], default="random",
                     help="random: seeded u, phi (the apply-sweep workload); tension: u = 0 with the top load "
                          "lifted, phi = 1 except 0 on the slit (a load step from rest)")
@@ -446,6 +448,76 @@ def run_apply_only(a):
             "launches": launch_count() - n0}
 
 
+def _event_times(fn, steps, warmup, flush, stream):
+    """CUDA-event durations (ms) of `steps` calls of fn after `warmup` untimed ones, L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def run_spmv(a):
+    """The paper's SpMV-vs-MFMV comparison over the polynomial degree (Sec. 6.3, fig. compare:vmult):
+    for p = 1..4 on the --dim/--cells specimen, the masked Jacobian of the workload state assembled
+    into CSR (pff_csr_assemble; assembly time reported, not part of the product) and multiplied by
+    cuSPARSE, against the matrix-free FP64 apply (--fp64-mode) and the FP32 one; best and median of
+    --steps event-timed products after --warmup, the L2 flushed before each."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    hbm, hbm_kind = peaks()
+    out = {"mode": "spmv", "dim": a.dim, "cells_per_dir": a.cells, "split": a.split, "fp64_mode": a.fp64_mode,
+           "steps": a.steps, "warmup": a.warmup, "hbm_peak_GB_per_s": hbm, "hbm_peak_kind": hbm_kind, "degrees": {}}
+    for p in (1, 2, 3, 4):
+        b = argparse.Namespace(**vars(a))
+        b.degree = p
+        ctx = setup_mesh(dim=a.dim, degree=p, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                         mg_precision=32, fp64_mode=a.fp64_mode)
+        U_h, po_h = make_state(ctx, b, seed=0)
+        U = torch.from_numpy(U_h).to(dev)
+        po = torch.from_numpy(po_h).to(dev)
+        act = (po - U[a.dim * ctx.n_nodes:] < 1e-8).to(torch.uint8).contiguous()
+        ctx.set_state(U, po, po, act)
+        t0 = time.perf_counter()
+        nnz = ctx.csr_assemble()
+        t_asm = time.perf_counter() - t0
+        nd = ctx.n_dofs
+        x = torch.randn(nd, dtype=torch.float64, device=dev)
+        y = torch.empty_like(x)
+        x32, y32 = x.float(), torch.empty(nd, dtype=torch.float32, device=dev)
+        t_sp = _event_times(lambda: ctx.csr_spmv(x, y), a.steps, a.warmup, flush, stream)
+        y_sp = y.clone()
+        t_mf = _event_times(lambda: ctx.apply_jacobian(x, y), a.steps, a.warmup, flush, stream)
+        t_mf32 = _event_times(lambda: ctx.apply_jacobian(x32, y32, precision=32), a.steps, a.warmup, flush, stream)
+        diff = float((y_sp - y).norm() / max(float(y.norm()), 1e-300))
+        sp_bytes = nnz * 12 + (nd + 1) * 4 + 2 * nd * 8  # values + column indices, row offsets, x and y once
+        best = min(t_sp)
+        out["degrees"][str(p)] = {
+            "n_dofs": nd, "nnz": nnz, "nnz_per_row": nnz / nd, "csr_MB": (nnz * 12 + (nd + 1) * 4) / 1e6,
+            "assemble_s": t_asm, "spmv_best_ms": best, "spmv_median_ms": statistics.median(t_sp),
+            "mf64_best_ms": min(t_mf), "mf64_median_ms": statistics.median(t_mf),
+            "mf32_best_ms": min(t_mf32), "mf32_median_ms": statistics.median(t_mf32),
+            "spmv_GB_per_s": sp_bytes / (best * 1e-3) / 1e9,
+            "spmv_frac_of_hbm": sp_bytes / (best * 1e-3) / 1e9 / hbm if hbm else None,
+            "mf64_speedup_vs_spmv": best / min(t_mf), "rel_diff_spmv_vs_mf64": diff}
+        print("p=%d: %s" % (p, json.dumps(out["degrees"][str(p)])), file=sys.stderr, flush=True)
+        ctx.close()
+    return out
+
+
 def run_pdas(a):
     """Full active-set Newton solve (Alg. 1 to --newton-rtol) from the workload state, with the FP32
     (mixed) and with the FP64 multigrid; both inside FP64 FGMRES with the FP64 residual."""
@@ -701,6 +773,10 @@ def main():
     if a.mode == "adjoint":
         torch.cuda.set_device(local if world > 1 else 0)
         print(json.dumps(run_adjoint(a)))
+        return
+    if a.mode == "spmv":
+        torch.cuda.set_device(local if world > 1 else 0)
+        print(json.dumps(run_spmv(a)))
         return
     if world > 1:
         torch.cuda.set_device(local)

@@ -39,7 +39,9 @@ extern "C" {
 #define PFF_ERR_NOT_CONVERGED (-5) /* FGMRES reached its iteration cap */
 #define PFF_ERR_BREAKDOWN (-6)     /* Krylov breakdown (zero norm before convergence) */
 #define PFF_ERR_NO_STATE (-7)      /* pff_set_state has not been called */
-#define PFF_ERR_TOO_LARGE (-8)     /* problem exceeds the fixed scratch of pff_param_grad_noalloc */
+#define PFF_ERR_TOO_LARGE (-8)     /* problem exceeds the fixed scratch of pff_param_grad_noalloc, or
+                                      the 32-bit indices of the assembled comparator matrix */
+#define PFF_ERR_UNAVAILABLE (-9)   /* an optional library (cuSPARSE, for pff_csr_spmv) cannot be loaded */
 
 /* Splits of the elastic energy (Sec. 2.1): none = isotropic model, miehe = spectral split. */
 #define PFF_SPLIT_NONE 0
@@ -250,6 +252,45 @@ int pff_param_grad(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda
  * pff_param_grad otherwise (the state must have been set; outputs are overwritten). */
 #define PFF_NOALLOC_SCRATCH_DOUBLES (2LL * 1024 * 1024)
 int pff_param_grad_noalloc(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda, double* g_mu);
+
+/* ---- Assembled-matrix comparator (Sec. 6.3, fig. compare:vmult) ------------------------------
+ * The paper times the matrix-free product against a sparse-matrix product with the assembled
+ * Jacobian. pff_csr_assemble assembles the finest level's operator of the linear solve,
+ * Z G Z + (I - Z) (Eq. (G) at the current state; Dirichlet and active DoFs masked as by
+ * pff_apply_jacobian's default mask), into a context-owned device CSR matrix (32-bit indices, FP64
+ * values, columns ascending, rows and columns in the DoF layout): the pattern comes from the mesh
+ * and the masks (pff_csr_pattern), the values from (d+1)(2p+1)^d products of the native FP64
+ * matrix-free operator with coloured probe vectors (two nodes of one colour never share a row).
+ * The matrix is a snapshot of the state: later state changes do not update it; assembling again
+ * replaces it. *nnz (host, may be NULL) receives the number of entries. Synchronous.
+ * Errors: NO_STATE, TOO_LARGE (n_dofs + 1 or nnz above 2^31 - 1), OOM, CUDA. */
+int pff_csr_assemble(pff_ctx* ctx, long long* nnz);
+
+/* y = A x with the assembled matrix, by cuSPARSE SpMV (FP64, default algorithm; the library is
+ * loaded on first use) on the context's stream. x, y: device arrays of n_dofs doubles, not aliased.
+ * Errors: INVALID_ARG, NO_STATE (nothing assembled), UNAVAILABLE (cuSPARSE not found), CUDA. */
+int pff_csr_spmv(pff_ctx* ctx, const double* x, double* y);
+
+/* Copies the assembled matrix into device arrays: rowptr (n_dofs + 1 ints), col (nnz ints), val
+ * (nnz doubles); each may be NULL. Synchronous. Errors: INVALID_ARG, NO_STATE (nothing assembled). */
+int pff_csr_export(pff_ctx* ctx, int* rowptr, int* col, double* val);
+
+/* Host only (no GPU work): the pattern that pff_csr_assemble uses, for a mesh of n_cells_1d^dim Q_p
+ * cells and host node flags (one byte per node; bit f set = DoF of component f masked). A masked row
+ * holds its diagonal; an unmasked row of node i holds the unmasked DoFs of every node sharing a cell
+ * with i, of the displacement components for a displacement row (G_uphi = 0) and of all components
+ * for a phase-field row, columns ascending. *nnz (required) receives the number of entries; rowptr
+ * (n_dofs + 1 ints) and col (nnz ints) are host arrays filled when not NULL, so a first call with
+ * both NULL sizes them. Errors: INVALID_ARG, TOO_LARGE. */
+int pff_csr_pattern(int dim, int degree, int n_cells_1d, const unsigned char* flags, int* rowptr, int* col,
+                    long long* nnz);
+
+/* Host only: the probing plan of pff_csr_assemble. For component f and colour `color` (0 <=
+ * color < (2p+1)^dim; a node's colour is sum_t (i_t mod (2p+1)) (2p+1)^t over its indices i_t),
+ * targets[r] (host, n_dofs entries) receives, for every row r, the one column of component f and that
+ * colour among the nodes sharing a cell with r's node, or -1 when there is none; the assembly stores
+ * the probe's y[r] there when the pattern holds that column. Errors: INVALID_ARG. */
+int pff_csr_probe_targets(int dim, int degree, int n_cells_1d, int f, int color, long long* targets);
 
 /* Device timing of one kernel family with CUDA events recorded on the context's stream around
  * each launch of that family (for throughput and roofline figures; off by default):

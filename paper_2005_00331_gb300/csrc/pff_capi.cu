@@ -13,6 +13,7 @@
 
 #include "../../include/pff.h"
 #include "pff_kernels.h"
+#include "pff_csr.h"
 #include "pff_launch.h"
 
 using namespace pff;
@@ -144,6 +145,7 @@ struct pff_ctx {
   int* cnt = nullptr;
   double* pinned = nullptr;    // host pinned scalars
   double* pgrad_tmp = nullptr;
+  pff::CsrMat* csr = nullptr;  // assembled comparator matrix (pff_csr_assemble)
   // coarse dense blocks
   double *Au = nullptr, *Ap = nullptr, *Bc = nullptr, *gjbuf = nullptr, *cr = nullptr, *ce = nullptr, *ct = nullptr;
   // FP32 copies of the coarse blocks and their inverses (multigrid in FP32)
@@ -1009,7 +1011,8 @@ const char* pff_strerror(int st) {
     case PFF_ERR_NOT_CONVERGED: return "linear solver did not converge";
     case PFF_ERR_BREAKDOWN: return "Krylov breakdown";
     case PFF_ERR_NO_STATE: return "no state set";
-    case PFF_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of the allocation-free entry point";
+    case PFF_ERR_TOO_LARGE: return "problem too large for this entry point (allocation-free scratch or 32-bit CSR indices)";
+    case PFF_ERR_UNAVAILABLE: return "an optional library (cuSPARSE) could not be loaded";
     default: return "unknown status";
   }
 }
@@ -1031,6 +1034,7 @@ void pff_destroy(pff_ctx* c) {
     if (L.aux) cudaStreamDestroy(L.aux);
     if (L.join) cudaEventDestroy(L.join);
   }
+  csr_destroy(c->csr);
   for (void* q : c->allocs) cudaFree(q);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
@@ -1287,6 +1291,78 @@ int pff_reaction_force(pff_ctx* c, double* force) {
   double f = 0.0;
   for (double v : h) f += v;
   *force = f;
+  return PFF_OK;
+}
+
+int pff_csr_pattern(int dim, int degree, int n_cells_1d, const unsigned char* flags, int* rowptr, int* col,
+                    long long* nnz) {
+  if ((dim != 2 && dim != 3) || degree < 1 || degree > 4 || n_cells_1d < 1 || !flags || !nnz)
+    return PFF_ERR_INVALID_ARG;
+  std::vector<int> rp, cl;
+  if (!csr_pattern(dim, degree, n_cells_1d, flags, rp, cl)) return PFF_ERR_TOO_LARGE;
+  *nnz = (long long)cl.size();
+  if (rowptr) std::memcpy(rowptr, rp.data(), sizeof(int) * rp.size());
+  if (col) std::memcpy(col, cl.data(), sizeof(int) * cl.size());
+  return PFF_OK;
+}
+
+int pff_csr_probe_targets(int dim, int degree, int n_cells_1d, int f, int color, long long* targets) {
+  const int m = 2 * degree + 1;
+  if ((dim != 2 && dim != 3) || degree < 1 || degree > 4 || n_cells_1d < 1 || f < 0 || f > dim || !targets ||
+      color < 0 || color >= (dim == 2 ? m * m : m * m * m))
+    return PFF_ERR_INVALID_ARG;
+  const int n1 = degree * n_cells_1d + 1;
+  const long long nn = dim == 2 ? (long long)n1 * n1 : (long long)n1 * n1 * n1;
+  for (long long r = 0; r < (dim + 1) * nn; ++r) targets[r] = probe_target(r, nn, n1, dim, degree, f, color);
+  return PFF_OK;
+}
+
+int pff_csr_assemble(pff_ctx* c, long long* nnz) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  if (!c->has_state) return PFF_ERR_NO_STATE;
+  CR(ensure_qp(c));
+  LevelData& L = c->lv[0];
+  std::vector<unsigned char> fl((size_t)L.nn);
+  CK(cudaMemcpyAsync(fl.data(), L.flags, (size_t)L.nn, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  std::vector<int> rowptr, col;
+  if (!csr_pattern(c->dim, c->p, L.N, fl.data(), rowptr, col)) return PFF_ERR_TOO_LARGE;
+  csr_destroy(c->csr);
+  c->csr = nullptr;
+  CR(csr_create(&c->csr, L.nd, rowptr, col, c->s));
+  // probe the native-FP64 operator of the linear solve with one coloured vector per (component, colour)
+  double* x = c->scratch;
+  double* y = c->scratch + L.nd;
+  const int m = 2 * c->p + 1, ncolor = c->dim == 2 ? m * m : m * m * m;
+  for (int f = 0; f <= c->dim; ++f) {
+    for (int color = 0; color < ncolor; ++color) {
+      CK(launch_probe_set(c->dim, c->p, L.nn, L.g.n1, f, color, x, c->s));
+      CK(cudaMemsetAsync(y, 0, sizeof(double) * L.nd, c->s));
+      CK(launch_jac(c->dim, c->p, c->prm.split, static_cast<const double*>(x), y, L.flags, L.g, L.t64, L.qp64,
+                    JM_FULL, IN_ALL, OUT_IDENTITY, c->s));
+      CK(launch_probe_gather(c->csr, c->dim, c->p, L.nn, L.g.n1, f, color, y, c->s));
+    }
+  }
+  CK(cudaStreamSynchronize(c->s));
+  if (nnz) *nnz = csr_nnz(c->csr);
+  return PFF_OK;
+}
+
+int pff_csr_spmv(pff_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y || x == y) return PFF_ERR_INVALID_ARG;
+  if (!c->csr) return PFF_ERR_NO_STATE;
+  return csr_spmv(c->csr, x, y, c->s);
+}
+
+int pff_csr_export(pff_ctx* c, int* rowptr, int* col, double* val) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  if (!c->csr) return PFF_ERR_NO_STATE;
+  const long long nr = c->lv[0].nd + 1, nz = csr_nnz(c->csr);
+  if (rowptr)
+    CK(cudaMemcpyAsync(rowptr, csr_rowptr(c->csr), sizeof(int) * nr, cudaMemcpyDeviceToDevice, c->s));
+  if (col) CK(cudaMemcpyAsync(col, csr_col(c->csr), sizeof(int) * nz, cudaMemcpyDeviceToDevice, c->s));
+  if (val) CK(cudaMemcpyAsync(val, csr_val(c->csr), sizeof(double) * nz, cudaMemcpyDeviceToDevice, c->s));
+  CK(cudaStreamSynchronize(c->s));
   return PFF_OK;
 }
 

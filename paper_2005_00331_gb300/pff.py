@@ -16,7 +16,7 @@ PFF_MASK_RAW, PFF_MASK_ADJOINT = 4, 8
 PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT = 0x10, 0x20, 0x40
 PFF_PROF_OFF, PFF_PROF_JAC64_L0, PFF_PROF_JAC32_L0, PFF_PROF_JAC64, PFF_PROF_JAC32, PFF_PROF_RESIDUAL = range(6)
 
-PFF_ERR_TOO_LARGE = -8
+PFF_ERR_TOO_LARGE, PFF_ERR_UNAVAILABLE = -8, -9
 
 
 class PFFError(RuntimeError):
@@ -63,6 +63,11 @@ _SIGS = {
     "pff_residual": (_I, [_P, _P]),
     "pff_reaction_force": (_I, [_P, ctypes.POINTER(_D)]),
     "pff_get_history": (_I, [_P, _P, _P, ctypes.POINTER(_I)]),
+    "pff_csr_assemble": (_I, [_P, ctypes.POINTER(_LL)]),
+    "pff_csr_spmv": (_I, [_P, _P, _P]),
+    "pff_csr_export": (_I, [_P, _P, _P, _P]),
+    "pff_csr_pattern": (_I, [_I, _I, _I, _P, _P, _P, ctypes.POINTER(_LL)]),
+    "pff_csr_probe_targets": (_I, [_I, _I, _I, _I, _I, _P]),
     "pff_set_history": (_I, [_P, _P, _P, _I]),
     "pff_diagonal": (_I, [_P, _I, _P, _I]),
     "pff_lambda_max": (_I, [_P, _I, ctypes.POINTER(_D)]),
@@ -153,6 +158,7 @@ class Context:
         _check(lib.pff_sizes(h, ctypes.byref(nd), ctypes.byref(nn), ctypes.byref(nl)), "pff_sizes")
         self.n_dofs, self.n_nodes, self.n_levels = nd.value, nn.value, nl.value
         self.dim = params.dim
+        self.csr_nnz = 0
 
     def close(self):
         if getattr(self, "_h", None):
@@ -369,11 +375,64 @@ class Context:
         self.set_state(U, phi_old, None, None, gc_field, lambda_field, mu_field)
         self.set_history(phi1, phi2)
 
+    def csr_assemble(self):
+        """Assembles the masked finest-level Jacobian into the context's CSR matrix; returns nnz."""
+        nnz = _LL()
+        _check(self._lib.pff_csr_assemble(self._h, ctypes.byref(nnz)), "pff_csr_assemble")
+        self.csr_nnz = nnz.value
+        return nnz.value
+
+    def csr_spmv(self, x, y=None):
+        """y = A x with the assembled matrix (cuSPARSE)."""
+        if y is None:
+            y = torch.empty(self.n_dofs, dtype=torch.float64, device=x.device)
+        _check(self._lib.pff_csr_spmv(self._h, _ptr(x, numel=self.n_dofs), _ptr(y, numel=self.n_dofs)),
+               "pff_csr_spmv")
+        return y
+
+    def csr_export(self):
+        """(rowptr, col, val) of the assembled matrix as device tensors (int32, int32, float64)."""
+        dev = self._dev()
+        rowptr = torch.empty(self.n_dofs + 1, dtype=torch.int32, device=dev)
+        col = torch.empty(self.csr_nnz, dtype=torch.int32, device=dev)
+        val = torch.empty(self.csr_nnz, dtype=torch.float64, device=dev)
+        _check(self._lib.pff_csr_export(self._h, _ptr(rowptr, torch.int32), _ptr(col, torch.int32), _ptr(val)),
+               "pff_csr_export")
+        return rowptr, col, val
+
     def param_grad(self, v):
         outs = [torch.empty(self.n_nodes, dtype=torch.float64, device=v.device) for _ in range(3)]
         _check(self._lib.pff_param_grad(self._h, _ptr(v, numel=self.n_dofs), *[_ptr(o) for o in outs]),
                "pff_param_grad")
         return outs
+
+
+def csr_pattern(dim, degree, n_cells_1d, flags):
+    """Host-only pattern of the assembled comparator matrix (pff_csr_pattern) for host node flags
+    (a uint8 numpy array, one byte per node): returns (rowptr, col) as int32 numpy arrays."""
+    import numpy as np
+    lib = load_library()
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    if fl.size != (degree * n_cells_1d + 1) ** dim:
+        raise ValueError("expected %d node flags, got %d" % ((degree * n_cells_1d + 1) ** dim, fl.size))
+    fp = fl.ctypes.data_as(ctypes.c_void_p)
+    nnz = _LL()
+    _check(lib.pff_csr_pattern(dim, degree, n_cells_1d, fp, None, None, ctypes.byref(nnz)), "pff_csr_pattern")
+    rowptr = np.empty((dim + 1) * fl.size + 1, dtype=np.int32)
+    col = np.empty(nnz.value, dtype=np.int32)
+    _check(lib.pff_csr_pattern(dim, degree, n_cells_1d, fp, rowptr.ctypes.data_as(ctypes.c_void_p),
+                               col.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nnz)), "pff_csr_pattern")
+    return rowptr, col
+
+
+def csr_probe_targets(dim, degree, n_cells_1d, f, color):
+    """Host-only probing plan of the comparator assembly (pff_csr_probe_targets): for each row, the
+    column that the probe (component f, colour) fills, or -1; an int64 numpy array."""
+    import numpy as np
+    out = np.empty((dim + 1) * (degree * n_cells_1d + 1) ** dim, dtype=np.int64)
+    _check(load_library().pff_csr_probe_targets(dim, degree, n_cells_1d, f, color,
+                                                out.ctypes.data_as(ctypes.c_void_p)), "pff_csr_probe_targets")
+    return out
 
 
 def setup_mesh(dim=2, degree=1, n_cells_1d=32, stream=None, **kw):
