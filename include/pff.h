@@ -271,6 +271,10 @@ int pff_csr_assemble(pff_ctx* ctx, long long* nnz);
  * Errors: INVALID_ARG, NO_STATE (nothing assembled), UNAVAILABLE (cuSPARSE not found), CUDA. */
 int pff_csr_spmv(pff_ctx* ctx, const double* x, double* y);
 
+/* Host only: 1 when cuSPARSE can be loaded and every entry point pff_csr_spmv uses resolves, else 0
+ * (loads the library on the first call; no GPU work). */
+int pff_csr_spmv_available(void);
+
 /* Copies the assembled matrix into device arrays: rowptr (n_dofs + 1 ints), col (nnz ints), val
  * (nnz doubles); each may be NULL. Synchronous. Errors: INVALID_ARG, NO_STATE (nothing assembled). */
 int pff_csr_export(pff_ctx* ctx, int* rowptr, int* col, double* val);

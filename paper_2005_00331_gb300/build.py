@@ -26,6 +26,13 @@ def _nvcc():
     return path
 
 
+def _defines():
+    """The library directory of the toolkit, where libpff looks for cuSPARSE when the loader does not
+    find it by name (it is loaded only by the assembled-matrix comparator)."""
+    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(_nvcc()))), "lib64")
+    return ['-DPFF_CUDA_LIBDIR="%s"' % libdir]
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -36,7 +43,7 @@ def _digest():
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + _defines()).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -49,11 +56,12 @@ def build(force=False, jobs=None, verbose=False):
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
     nvcc = _nvcc()
+    defines = _defines()
     srcs = _sources()
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + defines + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, r.stdout, r.stderr))

@@ -1348,6 +1348,8 @@ int pff_csr_assemble(pff_ctx* c, long long* nnz) {
   return PFF_OK;
 }
 
+int pff_csr_spmv_available(void) { return csr_spmv_available() ? 1 : 0; }
+
 int pff_csr_spmv(pff_ctx* c, const double* x, double* y) {
   if (!c || !x || !y || x == y) return PFF_ERR_INVALID_ARG;
   if (!c->csr) return PFF_ERR_NO_STATE;

@@ -48,10 +48,14 @@ SparseLib& sparse_lib() {
   static std::once_flag once;
   std::call_once(once, [] {
     void* h = nullptr;
-    for (const char* name : {"libcusparse.so.12", "libcusparse.so"}) {
-      h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
-      if (h) break;
-    }
+    // by soname (the loader's paths, or a copy the process has loaded already), then in the
+    // library directory of the toolkit that built libpff
+    const char* names[] = {"libcusparse.so.12", "libcusparse.so",
+#ifdef PFF_CUDA_LIBDIR
+                           PFF_CUDA_LIBDIR "/libcusparse.so.12",
+#endif
+                           nullptr};
+    for (int k = 0; names[k] && !h; ++k) h = dlopen(names[k], RTLD_NOW | RTLD_LOCAL);
     if (!h) return;
     L.ok = sym(h, "cusparseCreate", L.create) && sym(h, "cusparseDestroy", L.destroy) &&
            sym(h, "cusparseSetStream", L.set_stream) && sym(h, "cusparseCreateCsr", L.create_csr) &&
@@ -87,7 +91,7 @@ __global__ void k_probe_gather(long long nrows, const int* __restrict__ rowptr, 
   const int target = (int)tl;
   int a = rowptr[r], b = rowptr[r + 1];  // bisection over the row's ascending columns, [a, b)
   while (a < b) {
-    const int mid = (a + b) >> 1;
+    const int mid = a + ((b - a) >> 1);
     if (col[mid] < target) a = mid + 1;
     else b = mid;
   }
@@ -214,6 +218,8 @@ void csr_destroy(CsrMat* m) {
   if (m->rowptr) cudaFree(m->rowptr);
   delete m;
 }
+
+bool csr_spmv_available() { return sparse_lib().ok; }
 
 long long csr_nnz(const CsrMat* m) { return m ? m->nnz : 0; }
 const int* csr_rowptr(const CsrMat* m) { return m->rowptr; }

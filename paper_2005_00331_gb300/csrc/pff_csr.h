@@ -42,5 +42,7 @@ cudaError_t launch_probe_gather(CsrMat* m, int dim, int p, long long nn, int n1,
 // y = A x by cuSPARSE SpMV (FP64, default algorithm) on stream s. Returns PFF_OK, PFF_ERR_UNAVAILABLE
 // when cuSPARSE cannot be loaded, or PFF_ERR_CUDA.
 int csr_spmv(CsrMat* m, const double* x, double* y, cudaStream_t s);
+// Whether cuSPARSE was found and all its entry points resolved (loads it on first call; no GPU work).
+bool csr_spmv_available();
 
 }  // namespace pff

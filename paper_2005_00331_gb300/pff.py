@@ -65,6 +65,7 @@ _SIGS = {
     "pff_get_history": (_I, [_P, _P, _P, ctypes.POINTER(_I)]),
     "pff_csr_assemble": (_I, [_P, ctypes.POINTER(_LL)]),
     "pff_csr_spmv": (_I, [_P, _P, _P]),
+    "pff_csr_spmv_available": (_I, []),
     "pff_csr_export": (_I, [_P, _P, _P, _P]),
     "pff_csr_pattern": (_I, [_I, _I, _I, _P, _P, _P, ctypes.POINTER(_LL)]),
     "pff_csr_probe_targets": (_I, [_I, _I, _I, _I, _I, _P]),

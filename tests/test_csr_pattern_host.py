@@ -122,3 +122,9 @@ def test_probing_fills_every_entry_once(dim, p, N):
     assert np.all(hits == 1)
     B = sp.csr_matrix((val, col, rowptr), shape=(n, n))
     assert abs(B - A).max() == 0.0
+
+
+def test_cusparse_entry_points_resolve():
+    """The comparator's SpMV library loads and every entry point it calls resolves (no GPU work)."""
+    from paper_2005_00331_gb300 import load_library
+    assert load_library().pff_csr_spmv_available() == 1
