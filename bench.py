@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--newton-rtol", type=float, default=1e-8)
     ap.add_argument("--load-steps", type=int, default=10, help="--mode loadsteps: number of load steps")
     ap.add_argument("--load-inc", type=float, default=1e-4, help="--mode loadsteps: top displacement increment")
+    ap.add_argument("--specimen", choices=["tension", "shear"], default="tension",
+                    help="--mode loadsteps: top face pulled up (Sec. 5.1) or moved to the right (Sec. 5.2)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the last timed step (--mode vcycle: one extra cycle) by cudaProfilerStart/Stop, "
                          "for `ncu --profile-from-start off`")
@@ -627,16 +629,17 @@ def run_vcycle(a):
 
 def run_loadsteps(a):
     """Quasi-static loading from rest: --load-steps steps of --load-inc on the top face, each a full
-    active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid. Each step
-    also records the force on the top face (the load-displacement curve of Sec. 5.1)."""
+    active-set Newton solve with the extrapolated phase field; FP32 (mixed) vs FP64 multigrid; the top
+    face pulled up (--specimen tension, Sec. 5.1) or moved to the right (shear, Sec. 5.2). Each step
+    also records the force on the top face in the loading direction (the load-displacement curve)."""
     import torch
 
     from paper_2005_00331_gb300 import setup_mesh
     dev = torch.device("cuda", torch.cuda.current_device())
     b = argparse.Namespace(**vars(a))
     b.state = "tension"
-    out = {"mode": "loadsteps", "workload": workload_name(a), "load_steps": a.load_steps, "load_inc": a.load_inc,
-           "newton_rtol": a.newton_rtol}
+    out = {"mode": "loadsteps", "workload": workload_name(a), "specimen": a.specimen, "load_steps": a.load_steps,
+           "load_inc": a.load_inc, "newton_rtol": a.newton_rtol}
     finals = {}
     for prec in (32, 64):
         ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
@@ -646,6 +649,8 @@ def run_loadsteps(a):
         U = torch.from_numpy(U_h).to(dev)
         po = torch.from_numpy(po_h).to(dev)
         U[(a.dim - 1) * ctx.n_nodes:a.dim * ctx.n_nodes] = 0.0  # start from rest: no load yet
+        if a.specimen == "shear":
+            ctx.set_load_component(0)
         # warm-up: one load step (graph capture, kernel attributes), then restart from rest
         ctx.set_state(U, po, po, None)
         ctx.solve_load_step(a.load_inc, check=False)

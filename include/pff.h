@@ -152,11 +152,12 @@ int pff_apply_jacobian(pff_ctx* ctx, int level, const void* x, void* y, int prec
 /* r = R(U) of Eq. (residual) at the current state, FP64, rows of Dirichlet DoFs set to 0. */
 int pff_residual(pff_ctx* ctx, double* r);
 
-/* Force on the loaded top face of the tension test (Sec. 5.1), the ordinate of its load-displacement
- * curve, at the current state: the u_dim rows of R(U) (Dirichlet rows kept) summed over the nodes of
- * the top face, i.e. the residual's u-equation tested with the unit displacement of that face in the
- * loading direction (the consistent nodal reaction; for a uniform stress it is the face integral of
- * sigma_dd). *force is a host double. Synchronous. Errors: INVALID_ARG, NO_STATE. */
+/* Force on the loaded top face (tension test, Sec. 5.1; shear test, Sec. 5.2), the ordinate of the
+ * load-displacement curve, at the current state: the rows of R(U) (Dirichlet rows kept) of the loaded
+ * component (pff_set_load_component; u_dim by default) summed over the nodes of the top face, i.e.
+ * the residual's u-equation tested with the unit displacement of that face in the loading direction
+ * (the consistent nodal reaction; for a uniform stress it is the face integral of sigma_{comp,dim}).
+ * *force is a host double. Synchronous. Errors: INVALID_ARG, NO_STATE. */
 int pff_reaction_force(pff_ctx* ctx, double* force);
 
 /* Diagonal of the masked block-diagonal operator diag(G_uu, G_phiphi) on `level` (masked rows 1),
@@ -209,8 +210,16 @@ int pff_solve_newton_step(pff_ctx* ctx, double* U_out, pff_report* rep);
  * The final state is the context's state (and is copied to U_out when non-NULL). Synchronous. */
 int pff_solve_pdas(pff_ctx* ctx, int max_iters, double newton_rtol, double* U_out, pff_report* reps, int* n_steps);
 
-/* One quasi-static load step of the tension test (Sec. 5.1) from the current state: the displacement
- * component u_dim on the top face is set to `load` (all other Dirichlet values kept), phi_old becomes
+/* Displacement component that the load steps prescribe on the top face and in which
+ * pff_reaction_force measures: dim - 1 (the default; the tension test of Sec. 5.1, top face pulled)
+ * or 0 (the shear test of Sec. 5.2, top face moved to the right; the other components stay as the
+ * state has them, 0 for that test). Both tests fix every displacement component on the top and bottom
+ * faces, so the masks do not change. Errors: INVALID_ARG (comp outside 0..dim-1). */
+int pff_set_load_component(pff_ctx* ctx, int comp);
+
+/* One quasi-static load step of the tension test (Sec. 5.1; of the shear test with
+ * pff_set_load_component) from the current state: the loaded displacement component (u_dim by
+ * default) on the top face is set to `load` (all other Dirichlet values kept), phi_old becomes
  * the phase field of the previous load step and phi~ its linear extrapolation from the last two
  * steps, clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2; phi^{n-1} while only one is known); then
  * pff_solve_pdas. The phase-field history starts from the state of the last pff_set_state and

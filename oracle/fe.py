@@ -123,15 +123,16 @@ def residual(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=No
     return R
 
 
-def reaction_force(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=None):
-    """Force on the loaded (top) face of the tension test of Sec. 5.1, the ordinate of its
-    load-displacement curve: the u_d-rows of the residual, Dirichlet rows kept, summed over the
-    top-face nodes. That sum is the u-equation tested with w = e_d times the sum of the top-face basis
-    functions, i.e. the work of the stress g(phi~) sigma^+ + sigma^- on the field that moves the top
-    face by a unit amount in the loading direction (the consistent nodal reaction; for a homogeneous
-    stress it equals the face integral of sigma_dd)."""
+def reaction_force(mesh, prm, U, phi_tilde, gc_field=None, lam_field=None, mu_field=None, comp=None):
+    """Force on the loaded (top) face in the loading direction e_comp (comp = d-1, the default: the
+    tension test of Sec. 5.1; comp = 0: the shear test of Sec. 5.2), the ordinate of the
+    load-displacement curve: the u_comp-rows of the residual, Dirichlet rows kept, summed over the
+    top-face nodes. That sum is the u-equation tested with w = e_comp times the sum of the top-face
+    basis functions, i.e. the work of the stress g(phi~) sigma^+ + sigma^- on the field that moves the
+    top face by a unit amount in the loading direction (the consistent nodal reaction; for a
+    homogeneous stress it equals the face integral of sigma_{comp,d})."""
     R = residual(mesh, prm, U, phi_tilde, gc_field, lam_field, mu_field, zero_dirichlet=False)
-    return float(R[mesh.dof(mesh.dim - 1, mesh.top_nodes())].sum())
+    return float(R[mesh.dof(mesh.dim - 1 if comp is None else comp, mesh.top_nodes())].sum())
 
 
 def energy(mesh, prm, U, gc_field=None, lam_field=None, mu_field=None):

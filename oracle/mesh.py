@@ -75,10 +75,12 @@ class Mesh:
                 m[self.dof(c, nodes)] = True
         return m
 
-    def dirichlet_values(self, load):
-        """Lifted boundary values: 0 everywhere except u_d = load on the top face."""
+    def dirichlet_values(self, load, comp=None):
+        """Lifted boundary values: 0 everywhere except u_comp = load on the top face; comp = d-1 (the
+        default) pulls the top face (tension test, Sec. 5.1), comp = 0 moves it to the right (shear
+        test, Sec. 5.2)."""
         v = np.zeros(self.n_dofs)
-        v[self.dof(self.dim - 1, self.top_nodes())] = load
+        v[self.dof(self.dim - 1 if comp is None else comp, self.top_nodes())] = load
         return v
 
     def slit_nodes(self):

@@ -344,17 +344,19 @@ def pdas_step(mesh, prm, U, phi_old, phi_tilde, c=1.0, solve="direct", levels_kw
     return U + dU, act, float(np.linalg.norm(rhs)), info
 
 
-def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, **fields):
-    """Quasi-static loading of the tension test (Sec. 5.1): for each load, u_d := load on the top face,
+def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, comp=None, return_phit=False, **fields):
+    """Quasi-static loading of the tension test (Sec. 5.1; comp = 0: of the shear test, Sec. 5.2, whose
+    top face moves to the right): for each load, u_comp := load on the top face (comp = d-1 by default),
     phi_old := the previous step's phase field, phi~ := clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2:
     linear extrapolation from the last two steps, dt = 1; phi^{n-1} for the first step), then Alg. 1
-    repeated until the active set is unchanged and ||R~|| <= rtol ||R~_0||. Returns the states."""
+    repeated until the active set is unchanged and ||R~|| <= rtol ||R~_0||. Returns the states (and,
+    with return_phit, the phi~ each step solved with, which the u-equation of its residual uses)."""
     d, nn = mesh.dim, mesh.n_nodes
     U = U.copy()
     h1, h2 = U[d * nn:].copy(), None
-    out = []
+    out, phits = [], []
     for load in loads:
-        U[mesh.dof(d - 1, mesh.top_nodes())] = load
+        U[mesh.dof(d - 1 if comp is None else comp, mesh.top_nodes())] = load
         phi_old = h1.copy()
         phit = h1.copy() if h2 is None else np.clip(2.0 * h1 - h2, 0.0, 1.0)
         norms, prev = [], None
@@ -366,4 +368,5 @@ def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, **fields):
             prev = act
         h2, h1 = h1, U[d * nn:].copy()
         out.append(U.copy())
-    return out
+        phits.append(phit)
+    return (out, phits) if return_phit else out

@@ -134,6 +134,7 @@ struct pff_ctx {
   double* hist1 = nullptr;  // phase field of the previous load step
   double* hist2 = nullptr;  // ... and of the one before
   int nhist = 0;
+  int load_comp = -1;       // displacement component of the top-face load (-1: dim - 1, tension)
   double* mass = nullptr;
   double* R = nullptr;
   double* rhs = nullptr;
@@ -494,6 +495,8 @@ int ensure_diag64(pff_ctx* c) {
   c->diag64_ok = true;
   return PFF_OK;
 }
+
+int load_comp(const pff_ctx* c) { return c->load_comp < 0 ? c->dim - 1 : c->load_comp; }
 
 int residual_into(pff_ctx* c, double* r, int outmask = OUT_ZERO_DIRICHLET) {
   CR(ensure_st(c));
@@ -1285,7 +1288,7 @@ int pff_reaction_force(pff_ctx* c, double* force) {
   // the top face (last coordinate index n1 - 1) is the last n1^(dim-1) nodes of the lexicographic order
   const long long nface = c->dim == 2 ? (long long)L.g.n1 : (long long)L.g.n1 * L.g.n1;
   std::vector<double> h((size_t)nface);
-  CK(cudaMemcpyAsync(h.data(), r + (long long)(c->dim - 1) * L.nn + (L.nn - nface), sizeof(double) * nface,
+  CK(cudaMemcpyAsync(h.data(), r + (long long)load_comp(c) * L.nn + (L.nn - nface), sizeof(double) * nface,
                      cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
   double f = 0.0;
@@ -1365,6 +1368,12 @@ int pff_csr_export(pff_ctx* c, int* rowptr, int* col, double* val) {
   if (col) CK(cudaMemcpyAsync(col, csr_col(c->csr), sizeof(int) * nz, cudaMemcpyDeviceToDevice, c->s));
   if (val) CK(cudaMemcpyAsync(val, csr_val(c->csr), sizeof(double) * nz, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
+  return PFF_OK;
+}
+
+int pff_set_load_component(pff_ctx* c, int comp) {
+  if (!c || comp < 0 || comp >= c->dim) return PFF_ERR_INVALID_ARG;
+  c->load_comp = comp;
   return PFF_OK;
 }
 
@@ -1570,8 +1579,8 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
     CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
     c->nhist = 1;
   }
-  CK(launch_load_step_prep(c->dim, nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr, L.phit,
-                           c->phi_old, c->s));
+  CK(launch_load_step_prep(load_comp(c), nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr,
+                           L.phit, c->phi_old, c->s));
   c->qp_valid = false;
   c->st_valid = false;
   c->strain_valid = false;

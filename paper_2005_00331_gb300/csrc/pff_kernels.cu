@@ -1033,11 +1033,11 @@ cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags,
 }
 
 // Load stepping: u_dim := load on top-face nodes.
-__global__ void k_lift_top(int dim, long long nn, const unsigned char* __restrict__ flags, double load,
+__global__ void k_lift_top(int comp, long long nn, const unsigned char* __restrict__ flags, double load,
                            double* __restrict__ U) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= nn) return;
-  if (flags[i] & 0x10u) U[(dim - 1) * nn + i] = load;
+  if (flags[i] & 0x10u) U[comp * nn + i] = load;
 }
 // phi~ = clamp(2 h1 - h2, 0, 1) (or h1 when h2 is null); phi_old = h1.
 __global__ void k_extrapolate(long long nn, const double* __restrict__ h1, const double* __restrict__ h2,
@@ -1050,9 +1050,9 @@ __global__ void k_extrapolate(long long nn, const double* __restrict__ h1, const
   phit[i] = t;
   phi_old[i] = a;
 }
-cudaError_t launch_load_step_prep(int dim, long long nn, const unsigned char* flags, double load, double* U,
+cudaError_t launch_load_step_prep(int comp, long long nn, const unsigned char* flags, double load, double* U,
                                   const double* h1, const double* h2, double* phit, double* phi_old, cudaStream_t s) {
-  count_launch(); k_lift_top<<<grid_for(nn), BLK, 0, s>>>(dim, nn, flags, load, U);
+  count_launch(); k_lift_top<<<grid_for(nn), BLK, 0, s>>>(comp, nn, flags, load, U);
   count_launch(); k_extrapolate<<<grid_for(nn), BLK, 0, s>>>(nn, h1, h2, phit, phi_old);
   return cudaGetLastError();
 }

@@ -141,8 +141,8 @@ cudaError_t launch_set_active(int dim, long long nn, const unsigned char* active
                               cudaStream_t s);
 cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags, unsigned char* active,
                               cudaStream_t s);
-// Load step: u_dim := load on the top face; phi~ = clamp(2 h1 - h2, 0, 1) (h1 if h2 is null), phi_old = h1.
-cudaError_t launch_load_step_prep(int dim, long long nn, const unsigned char* flags, double load, double* U,
+// Load step: u_comp := load on the top face; phi~ = clamp(2 h1 - h2, 0, 1) (h1 if h2 is null), phi_old = h1.
+cudaError_t launch_load_step_prep(int comp, long long nn, const unsigned char* flags, double load, double* U,
                                   const double* h1, const double* h2, double* phit, double* phi_old, cudaStream_t s);
 // Lumped phase-field mass: int psi_i over the mesh (tensor product of 1D GLL weight sums).
 cudaError_t launch_lumped_mass(int dim, long long nn, int n1, const double* w1, double* mass, cudaStream_t s);

@@ -62,6 +62,7 @@ _SIGS = {
     "pff_apply_jacobian": (_I, [_P, _I, _P, _P, _I, _I]),
     "pff_residual": (_I, [_P, _P]),
     "pff_reaction_force": (_I, [_P, ctypes.POINTER(_D)]),
+    "pff_set_load_component": (_I, [_P, _I]),
     "pff_get_history": (_I, [_P, _P, _P, ctypes.POINTER(_I)]),
     "pff_csr_assemble": (_I, [_P, ctypes.POINTER(_LL)]),
     "pff_csr_spmv": (_I, [_P, _P, _P]),
@@ -328,6 +329,11 @@ class Context:
         if check:
             _check(st, "pff_solve_load_step")
         return st, [reps[i].as_dict() for i in range(n.value)]
+
+    def set_load_component(self, comp):
+        """Loaded displacement component of the load steps and the reaction force: dim - 1 (tension,
+        the default) or 0 (shear test)."""
+        _check(self._lib.pff_set_load_component(self._h, comp), "pff_set_load_component")
 
     def reaction_force(self):
         """Force on the loaded top face at the current state (pff_reaction_force), a Python float."""

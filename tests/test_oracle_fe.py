@@ -259,7 +259,8 @@ def test_reaction_force_uniaxial_strain(dim, p, N, split, load):
 def test_reaction_force_balance():
     """The basis functions sum to one and a rigid translation has no strain, so every u-component of
     the residual (Dirichlet rows kept) sums to zero over all nodes for any state; at a converged load
-    step the interior u-rows vanish as well, and the top reaction equals minus the bottom one."""
+    step (residual with the phi~ the step solved with) the interior u-rows vanish as well, and the top
+    reaction equals minus the bottom one."""
     from oracle import solvers as S
     m = M.Mesh(2, 1, 8)
     prm = fe.Params(LAM, MU, GC, 2.0 / 8, KAPPA, mat.SPLIT_MIEHE)
@@ -272,9 +273,47 @@ def test_reaction_force_balance():
     phi = np.ones(m.n_nodes)
     phi[m.slit_nodes()] = 0.0
     U[2 * m.n_nodes:] = phi
-    for Uk in S.load_steps(m, prm, U, [4e-3, 8e-3]):
-        phik = Uk[2 * m.n_nodes:]
-        top = fe.reaction_force(m, prm, Uk, phik)
-        R = fe.residual(m, prm, Uk, phik, zero_dirichlet=False)
+    for Uk, phit in zip(*S.load_steps(m, prm, U, [4e-3, 8e-3], return_phit=True)):
+        top = fe.reaction_force(m, prm, Uk, phit)
+        R = fe.residual(m, prm, Uk, phit, zero_dirichlet=False)
         bottom = R[m.dof(1, m.bottom_nodes())].sum()
+        assert top > 0 and abs(top + bottom) <= 1e-10 * top
+
+
+@pytest.mark.parametrize("dim,p,N", [(2, 1, 4), (2, 2, 3), (3, 2, 2)])
+@pytest.mark.parametrize("split", [mat.SPLIT_NONE, mat.SPLIT_MIEHE])
+@pytest.mark.parametrize("gamma", [2e-3, -2e-3])
+def test_reaction_force_simple_shear(dim, p, N, split, gamma):
+    """Shear test (Sec. 5.2) in closed form: u_x = gamma x_d (top face moved sideways by gamma), phi =
+    phi~ = c: the strain has eigenvalues +-gamma/2 (and 0 in 3D) and no trace, so sigma_xd = mu gamma;
+    without a split it is degraded by g(c), with the Miehe split only its tensile half is, which
+    leaves (1 + g(c)) mu gamma / 2 on the unit top face in the x direction."""
+    c = 0.7
+    m = M.Mesh(dim, p, N)
+    U = np.zeros(m.n_dofs)
+    U[:m.n_nodes] = gamma * m.coords[:, dim - 1]
+    U[dim * m.n_nodes:] = c
+    F = fe.reaction_force(m, fe.Params(LAM, MU, GC, 0.2, KAPPA, split), U, np.full(m.n_nodes, c), comp=0)
+    g = mat.g(c, KAPPA)
+    expect = MU * gamma * (g if split == mat.SPLIT_NONE else 0.5 * (1.0 + g))
+    assert abs(F - expect) <= 1e-13 * abs(expect)
+
+
+@pytest.mark.parametrize("split", [mat.SPLIT_NONE, mat.SPLIT_MIEHE])
+def test_shear_load_steps_balance(split):
+    """Shear load steps of the notched specimen converge to states whose x reaction on the top face
+    equals minus that on the bottom face and is positive for a rightward load."""
+    from oracle import solvers as S
+    m = M.Mesh(2, 1, 8)
+    prm = fe.Params(LAM, MU, GC, 2.0 / 8, KAPPA, split)
+    U = m.dirichlet_values(0.0, comp=0)
+    phi = np.ones(m.n_nodes)
+    phi[m.slit_nodes()] = 0.0
+    U[2 * m.n_nodes:] = phi
+    for Uk, phit in zip(*S.load_steps(m, prm, U, [4e-3, 8e-3], comp=0, return_phit=True)):
+        assert np.all(Uk[m.dof(0, m.top_nodes())] == Uk[m.dof(0, m.top_nodes())][0])
+        assert np.all(Uk[m.dof(1, m.top_nodes())] == 0.0)
+        top = fe.reaction_force(m, prm, Uk, phit, comp=0)
+        R = fe.residual(m, prm, Uk, phit, zero_dirichlet=False)
+        bottom = R[m.dof(0, m.bottom_nodes())].sum()
         assert top > 0 and abs(top + bottom) <= 1e-10 * top
