@@ -80,3 +80,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(pff, "library_path", lambda: str(tmp_path / "libpff.so"))
     with pytest.raises(RuntimeError):
         pff.load_library(build_if_missing=False)
+
+
+def test_plain_c_consumer(lib, tmp_path):
+    """include/pff.h compiles as strict C99, and a C program linked against libpff
+    (tests/abi_consumer.c) runs the host-only entry points and gets the documented results."""
+    import shutil
+    import subprocess
+    from paper_2005_00331_gb300 import build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    libdir = os.path.dirname(build.build())
+    exe = str(tmp_path / "abi_consumer")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "abi_consumer.c"), "-o", exe, "-L", libdir, "-lpff",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
