@@ -10,7 +10,8 @@ finite element solvers for phase-field fracture problems"):
 
 * ``basis``    -- 1D Gauss-Legendre points, Gauss-Lobatto-Legendre nodes, Lagrange bases (Sec. 3.1).
 * ``mesh``     -- uniform Q_p meshes of the unit square / cube, DoF numbering, Dirichlet data of the
-                  tension test, the slit, DoF counts of Table tab:slit:dofs:p (Sec. 5.1).
+                  tension and shear tests, the slit (phi = 0 on its nodes, or cut into the mesh with
+                  duplicated nodes), DoF counts of Table tab:slit:dofs:p (Sec. 5.1, 5.2).
 * ``material`` -- degradation g, strain, Miehe spectral split, the eigen-derivative of Eqs.
                   (lin_lambda), (lin_v) and Alg. 2, and the tangent of the split stress (Sec. 2.1, 3.5).
 * ``fe``       -- the residual of Eq. (residual) and the Jacobian of Eq. (G), both assembled cell by

@@ -18,11 +18,23 @@ SLIT_TOL = 1e-12
 
 
 class Mesh:
-    """Structured mesh of N^d cells of edge h = 1/N with Q_p nodes at GLL points."""
+    """Structured mesh of N^d cells of edge h = 1/N with Q_p nodes at GLL points.
 
-    def __init__(self, dim, p, N):
+    slit = "phase" (the default): one node per grid point; the slit enters as phi = 0 on its nodes.
+    slit = "duplicate": the slit is cut into the mesh as in Sec. 5.1: every node on the slit except the
+    tip (last coordinate 1/2, x < 1/2) gets a second copy, appended after the grid nodes, which the
+    cells below the slit use (N even); the grid-point node stays with the cells above. Only the
+    residual, the Jacobian and direct solves are defined on such a mesh (the multigrid transfers
+    assume one node per grid point)."""
+
+    def __init__(self, dim, p, N, slit="phase"):
         if dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
+        if slit not in ("phase", "duplicate"):
+            raise ValueError("slit must be 'phase' or 'duplicate'")
+        if slit == "duplicate" and N % 2:
+            raise ValueError("a slit cut into the mesh needs an even number of cells per direction")
+        self.slit = slit
         self.dim, self.p, self.N = dim, p, N
         self.h = 1.0 / N
         self.n1 = p * N + 1
@@ -52,6 +64,21 @@ class Mesh:
         strides = self.n1 ** np.arange(dim)
         self.cell_nodes = (ijk * strides).sum(axis=2)
         self.cell_origin = cidx * self.h
+        self.n_grid_nodes = self.n_nodes
+        self.dup_of = np.zeros(0, dtype=np.int64)  # grid node of each duplicate
+        if slit == "duplicate":
+            on_mid = self.node_ijk[:, dim - 1] == p * N // 2
+            open_side = self.node_ijk[:, 0] < p * N // 2  # x < 1/2: the tip stays shared
+            self.dup_of = np.nonzero(on_mid & open_side)[0]
+            dup_index = np.full(self.n_nodes, -1, dtype=np.int64)
+            dup_index[self.dup_of] = self.n_nodes + np.arange(len(self.dup_of))
+            below = (cidx[:, dim - 1] == N // 2 - 1) & (cidx[:, 0] < N // 2)
+            cn = self.cell_nodes[below]
+            self.cell_nodes[below] = np.where(dup_index[cn] >= 0, dup_index[cn], cn)
+            self.node_ijk = np.concatenate([self.node_ijk, self.node_ijk[self.dup_of]])
+            self.coords = np.concatenate([self.coords, self.coords[self.dup_of]])
+            self.n_nodes += len(self.dup_of)
+            self.n_dofs = self.n_comp * self.n_nodes
 
     def dof(self, comp, node):
         return comp * self.n_nodes + node
@@ -95,7 +122,16 @@ class Mesh:
         tip carries a second copy of all d+1 fields."""
         if self.dim != 2:
             raise ValueError("the paper counts duplicated slit DoFs in 2D only")
+        if self.slit == "duplicate":
+            return self.n_dofs
         return self.n_comp * (self.n_nodes + len(self.slit_nodes()) - 1)
+
+    def expand(self, grid_vec, comps=None):
+        """A vector of the one-node-per-grid-point layout (n_comp blocks of n_grid_nodes, or one
+        block when comps == 1) in this mesh's layout, duplicates taking their grid node's values."""
+        comps = self.n_comp if comps is None else comps
+        g = np.asarray(grid_vec).reshape(comps, self.n_grid_nodes)
+        return np.concatenate([g, g[:, self.dup_of]], axis=1).reshape(-1)
 
 
 def level_sizes(N, coarse_min=3):
