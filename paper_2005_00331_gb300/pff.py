@@ -152,6 +152,7 @@ class Context:
         self._lib = lib
         self.params = params
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = self.stream.device
         h = ctypes.c_void_p()
         _check(lib.pff_setup_mesh(ctypes.byref(h), ctypes.byref(params), ctypes.c_void_p(self.stream.cuda_stream)),
                "pff_setup_mesh")
@@ -186,7 +187,8 @@ class Context:
         return nn.value, N.value
 
     def _dev(self):
-        return torch.device("cuda", torch.cuda.current_device())
+        """The device of the context's stream (where the library allocated everything)."""
+        return self.device
 
     def node_flags(self, level=0):
         nn, _ = self.level_sizes(level)
