@@ -686,12 +686,17 @@ def run_loadsteps(a):
 
 
 # ---- CPU oracle baseline ----------------------------------------------------------------------
+# Cells per direction of the oracle's timed step: the reference arm times one step per benchmark step
+# (32^2: ~1-1.5 s each, so that --steps 50 ends within minutes); the cpu_baseline of the GPU line is
+# one larger sample (96^2, 112 k DoFs: ~10-15 s of CPU work). The oracle's DoF/s hardly depends on
+# the size (32^2, 64^2, 96^2 within 3 % of each other).
 CPU_SAMPLE_CELLS = 32
+CPU_BASELINE_CELLS = 96
 
 
-def cpu_oracle_sample(a, seconds_cap=30.0):
+def cpu_oracle_sample(a, cells=CPU_SAMPLE_CELLS):
     """Times the oracle's PDAS Newton step (FGMRES + V-cycle, sparse direct coarse solve) on the
-    same specimen family with CPU_SAMPLE_CELLS cells per direction, in one single-threaded process."""
+    same specimen family with `cells` cells per direction, in one single-threaded process."""
     code = r'''
 import json, sys, time
 sys.path.insert(0, %r)
@@ -712,7 +717,7 @@ t = time.perf_counter()
 S.pdas_step(m, prm, U, po, po, solve="gmg", levels_kw=dict(cheb_degree=%d))
 dt = time.perf_counter() - t
 print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt}))
-''' % (ROOT, a.dim, a.degree, CPU_SAMPLE_CELLS, a.split, a.cheb_degree)
+''' % (ROOT, a.dim, a.degree, cells, a.split, a.cheb_degree)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
@@ -721,7 +726,7 @@ print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt}))
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": d["n_dofs"] / d["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
             "sample": "one oracle PDAS Newton step (FGMRES + GMG) on the %dD Q%d notched specimen with %d^%d "
-                      "cells (%d DoFs), %.1f s" % (a.dim, a.degree, CPU_SAMPLE_CELLS, a.dim, d["n_dofs"],
+                      "cells (%d DoFs), %.1f s" % (a.dim, a.degree, cells, a.dim, d["n_dofs"],
                                                    d["seconds"])}
 
 
@@ -838,7 +843,7 @@ def main():
                 "achieved": ff["GB_per_s"], "peak": hbm, "unit": "GB/s", "frac": ff["GB_per_s"] / hbm,
                 "peak_kind": hbm_kind}
     if not a.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_sample(a)
+        line["cpu_baseline"] = cpu_oracle_sample(a, CPU_BASELINE_CELLS)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
