@@ -164,6 +164,7 @@ class Context:
         self.csr_nnz = 0
 
     def close(self):
+        """Destroys the library context (pff_destroy); the object is unusable afterwards."""
         if getattr(self, "_h", None):
             self._lib.pff_destroy(self._h)
             self._h = None
@@ -182,6 +183,7 @@ class Context:
         return False
 
     def level_sizes(self, level):
+        """(n_nodes, n_cells_1d) of multigrid level `level` (0 = finest)."""
         nn, N = _LL(), _I()
         _check(self._lib.pff_level_sizes(self._h, level, ctypes.byref(nn), ctypes.byref(N)), "pff_level_sizes")
         return nn.value, N.value
@@ -191,12 +193,15 @@ class Context:
         return self.device
 
     def node_flags(self, level=0):
+        """Node flags of a level (pff_node_flags): bit f = DoF of component f masked, plus PFF_FLAG_*."""
         nn, _ = self.level_sizes(level)
         out = torch.empty(nn, dtype=torch.uint8, device=self._dev())
         _check(self._lib.pff_node_flags(self._h, level, _ptr(out, torch.uint8)), "pff_node_flags")
         return out
 
     def set_state(self, U, phi_old, phi_tilde=None, active=None, gc_field=None, lambda_field=None, mu_field=None):
+        """Sets the Newton state (pff_set_state): U in the DoF layout, phi_old, phi~ (default phi_old),
+        the active set (uint8 per node; None = computed by the rule of Alg. 1) and optional nodal fields."""
         nn = self.n_nodes
         _check(self._lib.pff_set_state(self._h, _ptr(U, numel=self.n_dofs), _ptr(phi_old, numel=nn),
                                        _ptr(phi_tilde, numel=nn), _ptr(active, torch.uint8, nn),
@@ -204,11 +209,13 @@ class Context:
                                        _ptr(mu_field, numel=nn)), "pff_set_state")
 
     def get_state(self):
+        """Current state U (a new device tensor)."""
         out = torch.empty(self.n_dofs, dtype=torch.float64, device=self._dev())
         _check(self._lib.pff_get_state(self._h, _ptr(out)), "pff_get_state")
         return out
 
     def get_active(self):
+        """Current active set, one byte per node (1 = active)."""
         out = torch.empty(self.n_nodes, dtype=torch.uint8, device=self._dev())
         _check(self._lib.pff_get_active(self._h, _ptr(out, torch.uint8)), "pff_get_active")
         return out
@@ -217,6 +224,8 @@ class Context:
         return (self.dim + 1) * self.level_sizes(level)[0]
 
     def apply_jacobian(self, x, y=None, level=0, mode=PFF_MODE_FULL, precision=None):
+        """y = G x on `level` (pff_apply_jacobian); precision from x's dtype unless given, mode =
+        PFF_MODE_* | PFF_MASK_*."""
         prec = precision or (32 if x.dtype == torch.float32 else 64)
         dt = torch.float32 if prec == 32 else torch.float64
         nd = self._level_nd(level)
@@ -227,28 +236,33 @@ class Context:
         return y
 
     def residual(self, r=None):
+        """r = R(U) of Eq. (residual), FP64, Dirichlet rows 0 (pff_residual)."""
         if r is None:
             r = torch.empty(self.n_dofs, dtype=torch.float64, device=self._dev())
         _check(self._lib.pff_residual(self._h, _ptr(r, numel=self.n_dofs)), "pff_residual")
         return r
 
     def diagonal(self, level=0, precision=64):
+        """Jacobi diagonal diag(G_uu, G_phiphi) of a level, masked rows 1 (pff_diagonal)."""
         dt = torch.float32 if precision == 32 else torch.float64
         out = torch.empty(self._level_nd(level), dtype=dt, device=self._dev())
         _check(self._lib.pff_diagonal(self._h, level, _ptr(out, dt), precision), "pff_diagonal")
         return out
 
     def lambda_max(self, level=0):
+        """[lambda_max(D^-1 G_uu), lambda_max(D^-1 G_phiphi)] of a level (CG-Lanczos estimate)."""
         arr = (_D * 2)()
         _check(self._lib.pff_lambda_max(self._h, level, arr), "pff_lambda_max")
         return [arr[0], arr[1]]
 
     def level_state(self, level):
+        """The state carried to a coarse level (pff_level_state)."""
         out = torch.empty(self._level_nd(level), dtype=torch.float64, device=self._dev())
         _check(self._lib.pff_level_state(self._h, level, _ptr(out)), "pff_level_state")
         return out
 
     def prolongate(self, level, xc, precision=64):
+        """Prolongation from level + 1 to `level` (pff_prolongate)."""
         dt = torch.float32 if precision == 32 else torch.float64
         y = torch.empty(self._level_nd(level), dtype=dt, device=xc.device)
         _check(self._lib.pff_prolongate(self._h, level, _ptr(xc, dt, self._level_nd(level + 1)), _ptr(y, dt),
@@ -256,6 +270,7 @@ class Context:
         return y
 
     def restrict(self, level, xf, precision=64):
+        """Restriction from `level` to level + 1, the transpose of the prolongation (pff_restrict)."""
         dt = torch.float32 if precision == 32 else torch.float64
         y = torch.empty(self._level_nd(level + 1), dtype=dt, device=xf.device)
         _check(self._lib.pff_restrict(self._h, level, _ptr(xf, dt, self._level_nd(level)), _ptr(y, dt), precision),
@@ -263,6 +278,7 @@ class Context:
         return y
 
     def smooth(self, level, f, precision=64):
+        """One block-diagonal Chebyshev-Jacobi smoothing of f from zero on a level (pff_smooth)."""
         dt = torch.float32 if precision == 32 else torch.float64
         x = torch.empty(self._level_nd(level), dtype=dt, device=f.device)
         _check(self._lib.pff_smooth(self._h, level, _ptr(f, dt, self._level_nd(level)), _ptr(x, dt), precision),
@@ -270,17 +286,20 @@ class Context:
         return x
 
     def coarse_solve(self, r):
+        """Exact block forward substitution on the coarsest level (pff_coarse_solve)."""
         z = torch.empty_like(r)
         _check(self._lib.pff_coarse_solve(self._h, _ptr(r, numel=self._level_nd(self.n_levels - 1)), _ptr(z)),
                "pff_coarse_solve")
         return z
 
     def vcycle(self, r, z=None):
+        """z = V-cycle applied to r (pff_vcycle), the preconditioner of the linear solve."""
         z = torch.empty_like(r) if z is None else z
         _check(self._lib.pff_vcycle(self._h, _ptr(r, numel=self.n_dofs), _ptr(z, numel=self.n_dofs)), "pff_vcycle")
         return z
 
     def solve_linear(self, b, x=None, check=True):
+        """FGMRES with the V-cycle on G x = b (pff_solve_linear); returns (x, iterations, relative residual)."""
         x = torch.empty_like(b) if x is None else x
         its, rel = _I(), _D()
         st = self._lib.pff_solve_linear(self._h, _ptr(b, numel=self.n_dofs), _ptr(x, numel=self.n_dofs),
@@ -290,6 +309,7 @@ class Context:
         return x, its.value, rel.value
 
     def solve_newton_step(self, U_out=None, check=True):
+        """One step of Alg. 1 (pff_solve_newton_step); returns its report as a dict."""
         rep = Report()
         st = self._lib.pff_solve_newton_step(self._h, _ptr(U_out, numel=self.n_dofs), ctypes.byref(rep))
         if check:
@@ -309,6 +329,7 @@ class Context:
         _check(self._lib.pff_profile(self._h, family), "pff_profile")
 
     def profile_result(self):
+        """(launches, total ms) of the timed kernel family since pff_profile (synchronises)."""
         n, ms = _I(), _D()
         _check(self._lib.pff_profile_result(self._h, ctypes.byref(n), ctypes.byref(ms)), "pff_profile_result")
         return n.value, ms.value
@@ -410,6 +431,7 @@ class Context:
         return rowptr, col, val
 
     def param_grad(self, v):
+        """(dR/dG_c)^T v, (dR/dlambda)^T v, (dR/dmu)^T v as nodal device tensors (pff_param_grad)."""
         outs = [torch.empty(self.n_nodes, dtype=torch.float64, device=v.device) for _ in range(3)]
         _check(self._lib.pff_param_grad(self._h, _ptr(v, numel=self.n_dofs), *[_ptr(o) for o in outs]),
                "pff_param_grad")
