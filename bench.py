@@ -701,8 +701,12 @@ def cpu_oracle_sample(a, cells=CPU_SAMPLE_CELLS):
 import json, sys, time
 sys.path.insert(0, %r)
 import numpy as np
+import importlib.util
 from oracle import fe, mesh as M, solvers as S
-from paper_2005_00331_gb300 import inputs
+# the seeded input generators alone (numpy only), without the package and the torch import it makes
+spec = importlib.util.spec_from_file_location("pff_inputs", %r)
+inputs = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(inputs)
 dim, p, N, split = %d, %d, %d, %d
 m = M.Mesh(dim, p, N)
 prm = fe.Params(eps=2.0 / N, split=split)
@@ -717,7 +721,8 @@ t = time.perf_counter()
 S.pdas_step(m, prm, U, po, po, solve="gmg", levels_kw=dict(cheb_degree=%d))
 dt = time.perf_counter() - t
 print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt}))
-''' % (ROOT, a.dim, a.degree, cells, a.split, a.cheb_degree)
+''' % (ROOT, os.path.join(ROOT, "paper_2005_00331_gb300", "inputs.py"), a.dim, a.degree, cells, a.split,
+       a.cheb_degree)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
