@@ -1032,7 +1032,7 @@ cudaError_t launch_get_active(int dim, long long nn, const unsigned char* flags,
   return cudaGetLastError();
 }
 
-// Load stepping: u_dim := load on top-face nodes.
+// Load stepping: u_comp := load on top-face nodes (comp = dim - 1: tension test; 0: shear test).
 __global__ void k_lift_top(int comp, long long nn, const unsigned char* __restrict__ flags, double load,
                            double* __restrict__ U) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
