@@ -128,3 +128,19 @@ def test_cusparse_entry_points_resolve():
     """The comparator's SpMV library loads and every entry point it calls resolves (no GPU work)."""
     from paper_2005_00331_gb300 import load_library
     assert load_library().pff_csr_spmv_available() == 1
+
+
+@pytest.mark.parametrize("dim,p,N", [(2, 1, 64), (2, 2, 32), (2, 3, 32), (2, 4, 32), (3, 1, 8), (3, 2, 4),
+                                     (3, 4, 3)])
+def test_pattern_size_closed_form(dim, p, N):
+    """Nothing masked: per direction, an index shares cells with p + 1 indices at the two ends and off
+    the cell vertices, and with 2p + 1 at the N - 1 inner vertices, so sum_i |window_i| =
+    2(p+1) + (N-1)(2p+1) + N(p-1)(p+1) =: S, and the nodes' windows hold S^d entries; displacement
+    rows see d components, phase-field rows d + 1: nnz = (d^2 + d + 1) S^d. Everything masked: the
+    diagonal, nnz = n_dofs."""
+    n1 = p * N + 1
+    S = 2 * (p + 1) + (N - 1) * (2 * p + 1) + N * (p - 1) * (p + 1)
+    rowptr, col = csr_pattern(dim, p, N, np.zeros(n1 ** dim, dtype=np.uint8))
+    assert len(col) == (dim * dim + dim + 1) * S ** dim
+    rowptr, col = csr_pattern(dim, p, N, np.full(n1 ** dim, (1 << (dim + 1)) - 1, dtype=np.uint8))
+    assert np.array_equal(col, np.arange((dim + 1) * n1 ** dim))
