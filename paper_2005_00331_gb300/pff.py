@@ -16,7 +16,9 @@ PFF_MASK_RAW, PFF_MASK_ADJOINT = 4, 8
 PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT = 0x10, 0x20, 0x40
 PFF_PROF_OFF, PFF_PROF_JAC64_L0, PFF_PROF_JAC32_L0, PFF_PROF_JAC64, PFF_PROF_JAC32, PFF_PROF_RESIDUAL = range(6)
 
-PFF_ERR_TOO_LARGE, PFF_ERR_UNAVAILABLE = -8, -9
+PFF_OK = 0
+(PFF_ERR_INVALID_ARG, PFF_ERR_OOM, PFF_ERR_CUDA, PFF_ERR_NAN, PFF_ERR_NOT_CONVERGED, PFF_ERR_BREAKDOWN,
+ PFF_ERR_NO_STATE, PFF_ERR_TOO_LARGE, PFF_ERR_UNAVAILABLE) = range(-1, -10, -1)
 
 
 class PFFError(RuntimeError):

@@ -1,0 +1,55 @@
+"""Failure detection without a GPU fault: a non-finite state, an FGMRES iteration cap and the
+active-set loop's cap come back as status codes (PFF_ERR_NAN, PFF_ERR_NOT_CONVERGED), and the
+context keeps working afterwards. NaN arithmetic does not trap, and every device loop has a fixed
+trip count or a fixed bound, so none of these cases can hang or fault the GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from problems import Problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a, dtype=np.float64):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+def test_nan_state_is_reported_and_the_context_recovers():
+    from paper_2005_00331_gb300 import PFF_ERR_NAN
+    pr = Problem(2, 2, 8, split=1, seed=2, active_frac=0.1)
+    nn = pr.mesh.n_nodes
+    idx = int(np.nonzero(~pr.mask[:nn])[0][nn // 4])  # an unmasked u_x DoF
+    U_bad = pr.U.copy()
+    U_bad[idx] = np.nan
+    act = cuda(pr.active.astype(np.uint8), np.uint8)
+    with pr.context() as ctx:
+        ctx.set_state(cuda(U_bad), cuda(pr.phi_old), cuda(pr.phi_tilde), act)
+        rep = ctx.solve_newton_step(check=False)
+        assert rep["status"] == PFF_ERR_NAN
+        assert np.isnan(ctx.get_state().cpu().numpy()[idx])  # no update was applied
+        ctx.set_state(cuda(pr.U), cuda(pr.phi_old), cuda(pr.phi_tilde), act)
+        rep = ctx.solve_newton_step()  # raises on any error status
+        assert rep["status"] == 0 and np.all(np.isfinite(ctx.get_state().cpu().numpy()))
+
+
+def test_iteration_caps_are_reported():
+    from paper_2005_00331_gb300 import PFF_ERR_NOT_CONVERGED, load_library
+    pr = Problem(2, 2, 8, split=1, seed=3, active_frac=0.2)
+    lib = load_library()
+    with pr.context(mg_precision=32, gmres_max_iters=1, lin_rtol=1e-12) as ctx:
+        b = cuda(np.where(pr.mask, 0.0, np.random.default_rng(4).normal(size=pr.mesh.n_dofs)))
+        x = torch.empty_like(b)
+        its, rel = ctypes.c_int(), ctypes.c_double()
+        st = lib.pff_solve_linear(ctx._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.byref(its), ctypes.byref(rel))
+        assert st == PFF_ERR_NOT_CONVERGED and its.value == 1 and rel.value > 1e-12
+        U0 = ctx.get_state().cpu().numpy()
+        rep = ctx.solve_newton_step(check=False)
+        assert rep["status"] == PFF_ERR_NOT_CONVERGED and rep["gmres_iters"] == 1
+        assert not np.array_equal(ctx.get_state().cpu().numpy(), U0)  # the capped correction is applied
+    with pr.context(mg_precision=32) as ctx:
+        st, reps = ctx.solve_pdas(max_iters=1, check=False)
+        assert st == PFF_ERR_NOT_CONVERGED and len(reps) == 1  # Alg. 1 needs two steps to see A settle

@@ -99,3 +99,17 @@ def test_plain_c_consumer(lib, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+def test_status_codes_match_the_header():
+    """The binding's PFF_OK / PFF_ERR_* constants are the header's values, and every code has a message."""
+    import paper_2005_00331_gb300 as pkg
+    src = open(os.path.join(ROOT, "include", "pff.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"#define (PFF_(?:OK|ERR_\w+))\s+\(?(-?\d+)\)?", src))
+    assert len(codes) >= 10
+    for name, value in codes.items():
+        assert getattr(pkg, name) == value, name
+    lib = pkg.load_library()
+    for name, value in codes.items():
+        if value:
+            assert lib.pff_strerror(value).decode() != "unknown status", name
