@@ -305,6 +305,15 @@ int pff_csr_pattern(int dim, int degree, int n_cells_1d, const unsigned char* fl
  * the probe's y[r] there when the pattern holds that column. Errors: INVALID_ARG. */
 int pff_csr_probe_targets(int dim, int degree, int n_cells_1d, int f, int color, long long* targets);
 
+/* Device memory the context holds (Sec. 6.1 compares memory requirements), in bytes, host outputs,
+ * each may be NULL: level_bytes[l] for each of the n_levels levels (node flags, state, nodal fields,
+ * per-point data in all precisions, diagonals, multigrid work vectors), the FGMRES basis (krylov), the
+ * dense coarse blocks and their inverses (coarse), everything else including the assembled
+ * comparator matrix (other), and the sum (total). Buffers allocated on first use (multigrid work
+ * vectors, gradient scratch, comparator matrix) count once they exist. Errors: INVALID_ARG. */
+int pff_memory(pff_ctx* ctx, long long* level_bytes, long long* krylov, long long* coarse, long long* other,
+               long long* total);
+
 /* Device timing of one kernel family with CUDA events recorded on the context's stream around
  * each launch of that family (for throughput and roofline figures; off by default):
  *   PFF_PROF_OFF, PFF_PROF_JAC64_L0 / PFF_PROF_JAC32_L0 (FP64 / FP32 Jacobian kernels on the finest

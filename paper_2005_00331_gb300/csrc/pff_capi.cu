@@ -155,6 +155,9 @@ struct pff_ctx {
   // FGMRES
   double *V = nullptr, *Z = nullptr, *w = nullptr, *hdev = nullptr, *ydev = nullptr;
   std::vector<void*> allocs;
+  // bytes of device memory held, by owner (dalloc's tag): per level, Krylov basis, coarse blocks, other
+  std::vector<long long> level_bytes;
+  long long krylov_bytes = 0, coarse_bytes = 0, other_bytes = 0;
   // V-cycle replayed as a CUDA graph (captured once on a private stream; buffers never move)
   cudaStream_t cap = nullptr;
   cudaEvent_t fork = nullptr;
@@ -182,8 +185,11 @@ struct pff_ctx {
 
 namespace {
 
+// Owners of device memory for the accounting of pff_memory: a level index (>= 0) or one of these.
+constexpr int TAG_OTHER = -1, TAG_KRYLOV = -2, TAG_COARSE = -3;
+
 template <typename T>
-int dalloc(pff_ctx* c, T** p, long long n) {
+int dalloc(pff_ctx* c, T** p, long long n, int tag = TAG_OTHER) {
   *p = nullptr;
   if (n <= 0) n = 1;
   void* q = nullptr;
@@ -193,6 +199,17 @@ int dalloc(pff_ctx* c, T** p, long long n) {
   }
   c->allocs.push_back(q);
   *p = static_cast<T*>(q);
+  const long long bytes = (long long)sizeof(T) * n;
+  if (tag >= 0) {
+    if ((size_t)tag >= c->level_bytes.size()) c->level_bytes.resize((size_t)tag + 1, 0);
+    c->level_bytes[(size_t)tag] += bytes;
+  } else if (tag == TAG_KRYLOV) {
+    c->krylov_bytes += bytes;
+  } else if (tag == TAG_COARSE) {
+    c->coarse_bytes += bytes;
+  } else {
+    c->other_bytes += bytes;
+  }
   return PFF_OK;
 }
 
@@ -349,7 +366,7 @@ int ensure_work(pff_ctx* c, int l) {
   Real** w = work_of<Real>(L);
   if (w[0]) return PFF_OK;
   for (int i = 0; i < 6; ++i) {
-    CR(dalloc(c, &w[i], L.nd));
+    CR(dalloc(c, &w[i], L.nd, l));
     CK(cudaMemsetAsync(w[i], 0, sizeof(Real) * L.nd, c->s));
   }
   return PFF_OK;
@@ -1064,34 +1081,34 @@ static int setup_impl(pff_ctx* c) {
     make_geom(L, c->dim, c->p);
     make_tabs(L, c->dim, c->p);
     const int nv = qp_nv(c->dim, P.split);
-    CR(dalloc(c, &L.flags, L.nn));
-    CR(dalloc(c, &L.U, L.nd + L.nn));  // U and phi~ contiguous
+    CR(dalloc(c, &L.flags, L.nn, l));
+    CR(dalloc(c, &L.U, L.nd + L.nn, l));  // U and phi~ contiguous
     L.phit = L.U + L.nd;
-    CR(dalloc(c, &L.fields, 3 * L.nn));
+    CR(dalloc(c, &L.fields, 3 * L.nn, l));
     const long long nqp = L.g.ntiles * L.g.qpt;
-    CR(dalloc(c, &L.qp64, nv * nqp));
-    CR(dalloc(c, &L.qp32, nv * nqp));
-    CR(dalloc(c, &L.qpdf, nv * nqp));
+    CR(dalloc(c, &L.qp64, nv * nqp, l));
+    CR(dalloc(c, &L.qp32, nv * nqp, l));
+    CR(dalloc(c, &L.qpdf, nv * nqp, l));
     CK(cudaMemsetAsync(L.qpdf, 0, sizeof(df64) * nv * nqp, c->s));
     CK(cudaMemsetAsync(L.qp64, 0, sizeof(double) * nv * nqp, c->s));
     CK(cudaMemsetAsync(L.qp32, 0, sizeof(float) * nv * nqp, c->s));
     if (l == 0) {
-      CR(dalloc(c, &L.st64, ST_NV * nqp));
+      CR(dalloc(c, &L.st64, ST_NV * nqp, l));
       CK(cudaMemsetAsync(L.st64, 0, sizeof(double) * ST_NV * nqp, c->s));
       if (c->prm.split == 1) {
         const int nm = c->dim == 2 ? 3 : 6;
-        CR(dalloc(c, &L.sp64, (nm + 1) * nqp));
+        CR(dalloc(c, &L.sp64, (nm + 1) * nqp, l));
         CK(cudaMemsetAsync(L.sp64, 0, sizeof(double) * (nm + 1) * nqp, c->s));
       }
     }
-    CR(dalloc(c, &L.d64, L.nd));
-    CR(dalloc(c, &L.di64, L.nd));
-    CR(dalloc(c, &L.d32, L.nd));
-    CR(dalloc(c, &L.di32, L.nd));
-    CR(dalloc(c, &L.lam, 8));
-    CR(dalloc(c, &L.lscal, 16));
-    CR(dalloc(c, &L.lhist, 4 * P.eig_iters));
-    CR(dalloc(c, &L.lpart, 2 * 152 * 2));
+    CR(dalloc(c, &L.d64, L.nd, l));
+    CR(dalloc(c, &L.di64, L.nd, l));
+    CR(dalloc(c, &L.d32, L.nd, l));
+    CR(dalloc(c, &L.di32, L.nd, l));
+    CR(dalloc(c, &L.lam, 8, l));
+    CR(dalloc(c, &L.lscal, 16, l));
+    CR(dalloc(c, &L.lhist, 4 * P.eig_iters, l));
+    CR(dalloc(c, &L.lpart, 2 * 152 * 2, l));
     CK(cudaStreamCreateWithFlags(&L.aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
     std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N);
@@ -1112,31 +1129,31 @@ static int setup_impl(pff_ctx* c) {
   CR(dalloc(c, &c->dres, 32));
   CR(dalloc(c, &c->hist, 4 * P.eig_iters));
   CR(dalloc(c, &c->cnt, 2));
-  CR(dalloc(c, &c->V, (long long)(m + 1) * F.nd));
-  CR(dalloc(c, &c->Z, (long long)m * F.nd));
-  CR(dalloc(c, &c->w, F.nd));
-  CR(dalloc(c, &c->hdev, 3 * (m + 1) + 4));
-  CR(dalloc(c, &c->ydev, m + 1));
+  CR(dalloc(c, &c->V, (long long)(m + 1) * F.nd, TAG_KRYLOV));
+  CR(dalloc(c, &c->Z, (long long)m * F.nd, TAG_KRYLOV));
+  CR(dalloc(c, &c->w, F.nd, TAG_KRYLOV));
+  CR(dalloc(c, &c->hdev, 3 * (m + 1) + 4, TAG_KRYLOV));
+  CR(dalloc(c, &c->ydev, m + 1, TAG_KRYLOV));
   if (cudaMallocHost(&c->pinned, sizeof(double) * (4 * (m + 2) + 64)) != cudaSuccess) return PFF_ERR_OOM;
   LevelData& C = c->lv[c->nlev - 1];
   const long long nnc = C.nn, nuc = c->dim * C.nn;
-  CR(dalloc(c, &c->Au, nuc * nuc));
-  CR(dalloc(c, &c->Ap, nnc * nnc));
-  CR(dalloc(c, &c->Bc, nnc * nuc));
+  CR(dalloc(c, &c->Au, nuc * nuc, TAG_COARSE));
+  CR(dalloc(c, &c->Ap, nnc * nnc, TAG_COARSE));
+  CR(dalloc(c, &c->Bc, nnc * nuc, TAG_COARSE));
   if (c->prm.mg_precision == 32) {
-    CR(dalloc(c, &c->Au32, nuc * nuc));
-    CR(dalloc(c, &c->Ap32, nnc * nnc));
-    CR(dalloc(c, &c->Bc32, nnc * nuc));
-    CR(dalloc(c, &c->gjbuf32, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc)));
-    CR(dalloc(c, &c->cr32, C.nd));
-    CR(dalloc(c, &c->ce32, C.nd));
-    CR(dalloc(c, &c->ct32, C.nd));
+    CR(dalloc(c, &c->Au32, nuc * nuc, TAG_COARSE));
+    CR(dalloc(c, &c->Ap32, nnc * nnc, TAG_COARSE));
+    CR(dalloc(c, &c->Bc32, nnc * nuc, TAG_COARSE));
+    CR(dalloc(c, &c->gjbuf32, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc), TAG_COARSE));
+    CR(dalloc(c, &c->cr32, C.nd, TAG_COARSE));
+    CR(dalloc(c, &c->ce32, C.nd, TAG_COARSE));
+    CR(dalloc(c, &c->ct32, C.nd, TAG_COARSE));
   } else {
-    CR(dalloc(c, &c->gjbuf, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc)));
+    CR(dalloc(c, &c->gjbuf, gj_buffer_size((int)nuc) + gj_buffer_size((int)nnc), TAG_COARSE));
   }
-  CR(dalloc(c, &c->cr, C.nd));
-  CR(dalloc(c, &c->ce, C.nd));
-  CR(dalloc(c, &c->ct, C.nd));
+  CR(dalloc(c, &c->cr, C.nd, TAG_COARSE));
+  CR(dalloc(c, &c->ce, C.nd, TAG_COARSE));
+  CR(dalloc(c, &c->ct, C.nd, TAG_COARSE));
   // lumped phase-field mass: 1D sums of GLL weights times h
   {
     const int n1 = c->p * F.N + 1;
@@ -1368,6 +1385,24 @@ int pff_csr_export(pff_ctx* c, int* rowptr, int* col, double* val) {
   if (col) CK(cudaMemcpyAsync(col, csr_col(c->csr), sizeof(int) * nz, cudaMemcpyDeviceToDevice, c->s));
   if (val) CK(cudaMemcpyAsync(val, csr_val(c->csr), sizeof(double) * nz, cudaMemcpyDeviceToDevice, c->s));
   CK(cudaStreamSynchronize(c->s));
+  return PFF_OK;
+}
+
+int pff_memory(pff_ctx* c, long long* level_bytes, long long* krylov, long long* coarse, long long* other,
+               long long* total) {
+  if (!c) return PFF_ERR_INVALID_ARG;
+  long long sum = c->krylov_bytes + c->coarse_bytes + c->other_bytes;
+  long long csr = 0;
+  if (c->csr) csr = csr_nnz(c->csr) * (long long)(sizeof(int) + sizeof(double)) + (c->lv[0].nd + 1) * (long long)sizeof(int);
+  for (int l = 0; l < c->nlev; ++l) {
+    const long long b = (size_t)l < c->level_bytes.size() ? c->level_bytes[(size_t)l] : 0;
+    if (level_bytes) level_bytes[l] = b;
+    sum += b;
+  }
+  if (krylov) *krylov = c->krylov_bytes;
+  if (coarse) *coarse = c->coarse_bytes;
+  if (other) *other = c->other_bytes + csr;
+  if (total) *total = sum + csr;
   return PFF_OK;
 }
 

@@ -65,6 +65,7 @@ _SIGS = {
     "pff_residual": (_I, [_P, _P]),
     "pff_reaction_force": (_I, [_P, ctypes.POINTER(_D)]),
     "pff_set_load_component": (_I, [_P, _I]),
+    "pff_memory": (_I, [_P, _P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "pff_get_history": (_I, [_P, _P, _P, ctypes.POINTER(_I)]),
     "pff_csr_assemble": (_I, [_P, ctypes.POINTER(_LL)]),
     "pff_csr_spmv": (_I, [_P, _P, _P]),
@@ -354,6 +355,14 @@ class Context:
         if check:
             _check(st, "pff_solve_load_step")
         return st, [reps[i].as_dict() for i in range(n.value)]
+
+    def memory(self):
+        """Device bytes the context holds (pff_memory): {"levels": [...], "krylov", "coarse", "other", "total"}."""
+        lv = (_LL * self.n_levels)()
+        k, c, o, t = _LL(), _LL(), _LL(), _LL()
+        _check(self._lib.pff_memory(self._h, lv, ctypes.byref(k), ctypes.byref(c), ctypes.byref(o), ctypes.byref(t)),
+               "pff_memory")
+        return {"levels": list(lv), "krylov": k.value, "coarse": c.value, "other": o.value, "total": t.value}
 
     def set_load_component(self, comp):
         """Loaded displacement component of the load steps and the reaction force: dim - 1 (tension,

@@ -1,7 +1,8 @@
 """Failure detection without a GPU fault: a non-finite state, an FGMRES iteration cap and the
 active-set loop's cap come back as status codes (PFF_ERR_NAN, PFF_ERR_NOT_CONVERGED), and the
 context keeps working afterwards. NaN arithmetic does not trap, and every device loop has a fixed
-trip count or a fixed bound, so none of these cases can hang or fault the GPU."""
+trip count or a fixed bound, so none of these cases can hang or fault the GPU. Also the device
+memory accounting that these diagnostics report with."""
 import ctypes
 
 import numpy as np
@@ -53,3 +54,23 @@ def test_iteration_caps_are_reported():
     with pr.context(mg_precision=32) as ctx:
         st, reps = ctx.solve_pdas(max_iters=1, check=False)
         assert st == PFF_ERR_NOT_CONVERGED and len(reps) == 1  # Alg. 1 needs two steps to see A settle
+
+
+def test_memory_accounting():
+    """pff_memory: the FGMRES basis to the byte, levels decreasing with the mesh, parts summing to the
+    total, and the comparator matrix and the lazily allocated multigrid work vectors counted once
+    they exist."""
+    pr = Problem(2, 2, 16, split=1, seed=1)
+    nd, m = pr.mesh.n_dofs, 50
+    with pr.context() as ctx:
+        m0 = ctx.memory()
+        assert m0["krylov"] == 8 * ((m + 1) * nd + m * nd + nd + 3 * (m + 1) + 4 + m + 1)
+        lv = m0["levels"]
+        assert len(lv) == ctx.n_levels and all(a > b > 0 for a, b in zip(lv, lv[1:]))
+        assert m0["total"] == sum(lv) + m0["krylov"] + m0["coarse"] + m0["other"] and m0["coarse"] > 0
+        nnz = ctx.csr_assemble()
+        m1 = ctx.memory()
+        assert m1["other"] - m0["other"] == 12 * nnz + 4 * (nd + 1)
+        ctx.solve_newton_step()
+        m2 = ctx.memory()
+        assert all(b >= a for a, b in zip(m1["levels"], m2["levels"])) and m2["levels"][0] > m1["levels"][0]
