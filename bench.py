@@ -694,10 +694,12 @@ CPU_SAMPLE_CELLS = 32
 CPU_BASELINE_CELLS = 96
 
 
-def cpu_oracle_sample(a, cells=CPU_SAMPLE_CELLS):
-    """Times the oracle's PDAS Newton step (FGMRES + V-cycle, sparse direct coarse solve) on the
-    same specimen family with `cells` cells per direction, in one single-threaded process."""
-    code = r'''
+def _oracle_step_code(a, cells, go=None):
+    """Source of a process that times one oracle PDAS Newton step (FGMRES + V-cycle, sparse direct
+    coarse solve) on the specimen with `cells` cells per direction and prints n_dofs, the step's
+    seconds and its wall-clock start and end; with `go` (a time.time() value) the step waits until
+    then, so that concurrent processes start together after their imports and set-up."""
+    return r"""
 import json, sys, time
 sys.path.insert(0, %r)
 import numpy as np
@@ -717,22 +719,86 @@ phi = inputs.uniform_phase(nn, 0)
 phi[m.slit_nodes()] = 0.0
 U[dim * nn:] = phi
 po = inputs.phi_old_above(phi, 0)
+go = %r
+if go is not None and go > time.time():
+    time.sleep(go - time.time())
+w0 = time.time()
 t = time.perf_counter()
 S.pdas_step(m, prm, U, po, po, solve="gmg", levels_kw=dict(cheb_degree=%d))
 dt = time.perf_counter() - t
-print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt}))
-''' % (ROOT, os.path.join(ROOT, "paper_2005_00331_gb300", "inputs.py"), a.dim, a.degree, cells, a.split,
+print(json.dumps({"n_dofs": m.n_dofs, "seconds": dt, "start": w0, "end": time.time()}))
+""" % (ROOT, os.path.join(ROOT, "paper_2005_00331_gb300", "inputs.py"), a.dim, a.degree, cells, a.split, go,
        a.cheb_degree)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+
+
+ORACLE_ENV = dict(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+
+
+def cpu_oracle_sample(a, cells=CPU_SAMPLE_CELLS):
+    """Times the oracle's PDAS Newton step on the same specimen family with `cells` cells per
+    direction, in one single-threaded process."""
+    env = dict(os.environ, **ORACLE_ENV)
+    r = subprocess.run([sys.executable, "-c", _oracle_step_code(a, cells)], capture_output=True, text=True, env=env,
+                       timeout=600)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": d["n_dofs"] / d["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
             "sample": "one oracle PDAS Newton step (FGMRES + GMG) on the %dD Q%d notched specimen with %d^%d "
                       "cells (%d DoFs), %.1f s" % (a.dim, a.degree, cells, a.dim, d["n_dofs"],
-                                                   d["seconds"])}
+                                                   d["seconds"]),
+            "host": host_cpu()}
+
+
+def cpu_oracle_all_cores(a, cells=CPU_SAMPLE_CELLS):
+    """The oracle on every host core at once: one single-threaded process per core, each timing one
+    step; the throughput is the DoFs of all steps over the span from the first start to the last end
+    (process start-up and imports excluded: the steps wait for a common start time)."""
+    n = os.cpu_count() or 1
+    env = dict(os.environ, **ORACLE_ENV)
+    code = _oracle_step_code(a, cells, go=time.time() + 8.0)
+    procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env) for _ in range(n)]
+    outs = []
+    for pr in procs:
+        try:
+            out, err = pr.communicate(timeout=900)
+        except subprocess.TimeoutExpired:
+            pr.kill()
+            out, err = pr.communicate()
+        if pr.returncode != 0:
+            return {"error": (err or "")[-400:]}
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    span = max(d["end"] for d in outs) - min(d["start"] for d in outs)
+    dofs = sum(d["n_dofs"] for d in outs)
+    return {"value": dofs / span, "unit": "DoF/s", "cores": n, "kind": "oracle",
+            "sample": "%d concurrent single-threaded oracle PDAS Newton steps (one per core) on the %dD Q%d notched "
+                      "specimen with %d^%d cells, %.1f s from the first start to the last end"
+                      % (n, a.dim, a.degree, cells, a.dim, span),
+            "host": host_cpu()}
+
+
+def host_cpu():
+    """CPU model and core count of this host (lscpu, else /proc/cpuinfo, else the machine type)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"cpu": model or platform.machine(), "nproc": os.cpu_count()}
 
 
 # ---- main --------------------------------------------------------------------------------------
@@ -849,6 +915,7 @@ def main():
                 "peak_kind": hbm_kind}
     if not a.no_cpu:
         line["cpu_baseline"] = cpu_oracle_sample(a, CPU_BASELINE_CELLS)
+        line["cpu_baseline_all_cores"] = cpu_oracle_all_cores(a)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
