@@ -914,8 +914,12 @@ def main():
                 "achieved": ff["GB_per_s"], "peak": hbm, "unit": "GB/s", "frac": ff["GB_per_s"] / hbm,
                 "peak_kind": hbm_kind}
     if not a.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_sample(a, CPU_BASELINE_CELLS)
-        line["cpu_baseline_all_cores"] = cpu_oracle_all_cores(a)
+        for key, fn in (("cpu_baseline", lambda: cpu_oracle_sample(a, CPU_BASELINE_CELLS)),
+                        ("cpu_baseline_all_cores", lambda: cpu_oracle_all_cores(a))):
+            try:  # the CPU baselines are reported beside the GPU numbers; they must not lose the line
+                line[key] = fn()
+            except (OSError, ValueError, KeyError, subprocess.SubprocessError) as e:
+                line[key] = {"error": "%s: %s" % (type(e).__name__, e)}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
