@@ -913,7 +913,7 @@ def main():
                 "kernel": "FP64 values, double-word arithmetic on the FP32 pipe", "bound": "hbm",
                 "achieved": ff["GB_per_s"], "peak": hbm, "unit": "GB/s", "frac": ff["GB_per_s"] / hbm,
                 "peak_kind": hbm_kind}
-    if not a.no_cpu:
+    if not a.no_cpu and world == 1:  # rank 0 at N = 1 only
         for key, fn in (("cpu_baseline", lambda: cpu_oracle_sample(a, CPU_BASELINE_CELLS)),
                         ("cpu_baseline_all_cores", lambda: cpu_oracle_all_cores(a))):
             try:  # the CPU baselines are reported beside the GPU numbers; they must not lose the line
