@@ -12,4 +12,4 @@ from .pff import (  # noqa: F401
     PFF_FLAG_BOTTOM, PFF_FLAG_SLIT, PFF_FLAG_TOP, PFF_MASK_ADJOINT, PFF_MASK_RAW, PFF_MODE_BLOCKDIAG,
     PFF_MODE_FULL, PFF_MODE_TRANSPOSE, PFF_PROF_JAC32, PFF_PROF_JAC32_L0, PFF_PROF_JAC64,
     PFF_PROF_JAC64_L0, PFF_PROF_OFF, PFF_PROF_RESIDUAL, PFF_SPLIT_MIEHE, PFF_SPLIT_NONE, Context, PFFError, ResidualFunction,
-    csr_pattern, csr_probe_targets, default_params, launch_count, load_library, setup_mesh)
+    csr_pattern, csr_probe_targets, default_params, launch_count, load_library, report_lines, setup_mesh)

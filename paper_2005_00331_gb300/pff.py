@@ -337,24 +337,39 @@ class Context:
         _check(self._lib.pff_profile_result(self._h, ctypes.byref(n), ctypes.byref(ms)), "pff_profile_result")
         return n.value, ms.value
 
-    def solve_pdas(self, max_iters=30, newton_rtol=1e-8, U_out=None, check=True):
-        """Alg. 1 repeated until the active set settles and ||R~|| <= newton_rtol ||R~_0||."""
+    def solve_pdas(self, max_iters=30, newton_rtol=1e-8, U_out=None, check=True, log=None):
+        """Alg. 1 repeated until the active set settles and ||R~|| <= newton_rtol ||R~_0||. With `log`
+        (a text file), one JSON line per Newton step (see report_lines) is written to it."""
         reps = (Report * max_iters)()
         n = _I()
         st = self._lib.pff_solve_pdas(self._h, max_iters, newton_rtol, _ptr(U_out, numel=self.n_dofs), reps,
                                       ctypes.byref(n))
+        out = [reps[i].as_dict() for i in range(n.value)]
+        if log is not None:
+            self._log(log, out, loop_status=st)
         if check:
             _check(st, "pff_solve_pdas")
-        return st, [reps[i].as_dict() for i in range(n.value)]
+        return st, out
 
-    def solve_load_step(self, load, max_iters=30, newton_rtol=1e-8, check=True):
-        """One quasi-static load step (top displacement `load`, phi~ extrapolated, Alg. 1 to tolerance)."""
+    def solve_load_step(self, load, max_iters=30, newton_rtol=1e-8, check=True, log=None):
+        """One quasi-static load step (top displacement `load`, phi~ extrapolated, Alg. 1 to tolerance).
+        With `log` (a text file), one JSON line per Newton step, with the load and the force on the top
+        face after the step."""
         reps = (Report * max_iters)()
         n = _I()
         st = self._lib.pff_solve_load_step(self._h, load, max_iters, newton_rtol, reps, ctypes.byref(n))
+        out = [reps[i].as_dict() for i in range(n.value)]
+        if log is not None:
+            self._log(log, out, loop_status=st, load=load, reaction_force=self.reaction_force())
         if check:
             _check(st, "pff_solve_load_step")
-        return st, [reps[i].as_dict() for i in range(n.value)]
+        return st, out
+
+    def _log(self, fh, reports, **fields):
+        mem = self.memory()
+        for line in report_lines(reports, device_bytes=mem["total"], level_bytes=mem["levels"], **fields):
+            fh.write(line + "\n")
+        fh.flush()
 
     def memory(self):
         """Device bytes the context holds (pff_memory): {"levels": [...], "krylov", "coarse", "other", "total"}."""
@@ -447,6 +462,14 @@ class Context:
         _check(self._lib.pff_param_grad(self._h, _ptr(v, numel=self.n_dofs), *[_ptr(o) for o in outs]),
                "pff_param_grad")
         return outs
+
+
+def report_lines(reports, **fields):
+    """JSON lines, one per Newton step: the step's number and report (||R~||, |A|, active-set changes,
+    FGMRES iterations and relative residual, status, milliseconds per phase) with `fields` added to
+    each line (e.g. the load, the loop's status, device bytes per level; a step's own keys win)."""
+    import json
+    return [json.dumps(dict(fields, newton_step=k, **r)) for k, r in enumerate(reports)]
 
 
 def csr_pattern(dim, degree, n_cells_1d, flags):

@@ -1,5 +1,6 @@
 """Host logic of the load-step checkpoint file (no GPU): round trip, and the checks that reject a
-file of another kind, sizes that do not fit the mesh, a bad history count and a foreign mesh."""
+file of another kind, sizes that do not fit the mesh, a bad history count and a foreign mesh; and
+the per-Newton-step report lines."""
 import numpy as np
 import pytest
 
@@ -75,3 +76,16 @@ def test_truncated_history_on_disk(tmp_path):
     np.savez(path, **parts)
     with pytest.raises(ValueError):
         ck.load(path)
+
+
+def test_report_lines():
+    """One JSON line per Newton step, carrying the step's report and the added fields."""
+    import json
+    from paper_2005_00331_gb300 import report_lines
+    reps = [{"res_norm": 1.0, "n_active": 3, "gmres_iters": 7, "status": 0},
+            {"res_norm": 1e-9, "n_active": 3, "gmres_iters": 5, "status": 0}]
+    lines = report_lines(reps, load=2e-3, level_bytes=[10, 5])
+    assert len(lines) == 2
+    d = [json.loads(x) for x in lines]
+    assert d[1]["newton_step"] == 1 and d[1]["res_norm"] == 1e-9 and d[0]["load"] == 2e-3
+    assert d[0]["level_bytes"] == [10, 5]
