@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pff.h"
 #include "pff_kernels.h"
 #include "pff_csr.h"
@@ -19,6 +21,27 @@
 using namespace pff;
 
 namespace {
+
+// NVTX range over a scope: the entry points and the phases of a Newton step show up by name in
+// profilers that trace NVTX (ncu --nvtx); without such a tool attached the calls do nothing.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+// Consecutive NVTX ranges for the phases of one call (each next() ends the previous phase).
+struct Phases {
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~Phases() {
+    if (open) nvtxRangePop();
+  }
+};
 
 // ---- 1D bases (closed forms for p <= 4) ----------------------------------------------------
 void gll_nodes(int p, double* x) {
@@ -1218,6 +1241,7 @@ int pff_node_flags(pff_ctx* c, int level, unsigned char* flags) {
 int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const double* phi_tilde,
                   const unsigned char* active, const double* gc_field, const double* lambda_field,
                   const double* mu_field) {
+  Range nvtx_range("pff_set_state");
   if (!c || !U || !phi_old) return PFF_ERR_INVALID_ARG;
   LevelData& L = c->lv[0];
   CK(cudaMemcpyAsync(L.U, U, sizeof(double) * L.nd, cudaMemcpyDeviceToDevice, c->s));
@@ -1273,6 +1297,7 @@ int pff_get_active(pff_ctx* c, unsigned char* a) {
 }
 
 int pff_apply_jacobian(pff_ctx* c, int level, const void* x, void* y, int precision, int mode) {
+  Range nvtx_range("pff_apply_jacobian");
   if (!c || !x || !y || level < 0 || level >= c->nlev || !valid_prec(precision) || x == y) return PFF_ERR_INVALID_ARG;
   const int jm = mode & 3;
   if (jm > 2 || (mode & ~15) || ((mode & PFF_MASK_RAW) && (mode & PFF_MASK_ADJOINT))) return PFF_ERR_INVALID_ARG;
@@ -1292,11 +1317,13 @@ int pff_apply_jacobian(pff_ctx* c, int level, const void* x, void* y, int precis
 }
 
 int pff_residual(pff_ctx* c, double* r) {
+  Range nvtx_range("pff_residual");
   if (!c || !r) return PFF_ERR_INVALID_ARG;
   return residual_into(c, r);
 }
 
 int pff_reaction_force(pff_ctx* c, double* force) {
+  Range nvtx_range("pff_reaction_force");
   if (!c || !force) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   LevelData& L = c->lv[0];
@@ -1338,6 +1365,7 @@ int pff_csr_probe_targets(int dim, int degree, int n_cells_1d, int f, int color,
 }
 
 int pff_csr_assemble(pff_ctx* c, long long* nnz) {
+  Range nvtx_range("pff_csr_assemble");
   if (!c) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   CR(ensure_qp(c));
@@ -1371,6 +1399,7 @@ int pff_csr_assemble(pff_ctx* c, long long* nnz) {
 int pff_csr_spmv_available(void) { return csr_spmv_available() ? 1 : 0; }
 
 int pff_csr_spmv(pff_ctx* c, const double* x, double* y) {
+  Range nvtx_range("pff_csr_spmv");
   if (!c || !x || !y || x == y) return PFF_ERR_INVALID_ARG;
   if (!c->csr) return PFF_ERR_NO_STATE;
   return csr_spmv(c->csr, x, y, c->s);
@@ -1515,6 +1544,7 @@ int pff_coarse_solve(pff_ctx* c, const double* r, double* z) {
 }
 
 int pff_vcycle(pff_ctx* c, const double* r, double* z) {
+  Range nvtx_range("pff_vcycle");
   if (!c || !r || !z || r == z) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   CR(mg_setup(c));
@@ -1525,12 +1555,14 @@ int pff_vcycle(pff_ctx* c, const double* r, double* z) {
 }
 
 int pff_solve_linear(pff_ctx* c, const double* b, double* x, int* iters, double* rel) {
+  Range nvtx_range("pff_solve_linear");
   if (!c || !b || !x || b == x) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   return fgmres(c, b, x, iters, rel);
 }
 
 int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
+  Range nvtx_range("pff_solve_newton_step");
   if (!c) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   using clk = std::chrono::steady_clock;
@@ -1541,6 +1573,8 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   pff_report r{};
   CK(cudaStreamSynchronize(c->s));
   const auto t0 = clk::now();
+  Phases phase;
+  phase.next("residual and active set");
   // Alg. 1: residual, active set (phi reset to phi_old on it), residual of the projected state
   CR(residual_into(c, c->R));
   CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
@@ -1556,10 +1590,12 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   r.n_active = cnt[0];
   r.n_changed = cnt[1];
   const auto t1 = clk::now();
+  phase.next("multigrid setup");
   CR(mg_setup(c));
   CK(cudaStreamSynchronize(c->s));
   CR(prof_collect(c));
   const auto t2 = clk::now();
+  phase.next("FGMRES");
   r.status = fgmres(c, c->rhs, c->dU, &r.gmres_iters, &r.gmres_rel);
   if (r.status == PFF_OK || r.status == PFF_ERR_NOT_CONVERGED) {
     CK(launch_axpby<double>(L.nd, 1.0, c->dU, 1.0, L.U, c->s));
@@ -1578,6 +1614,7 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
 }
 
 int pff_solve_pdas(pff_ctx* c, int max_iters, double newton_rtol, double* U_out, pff_report* reps, int* n_steps) {
+  Range nvtx_range("pff_solve_pdas");
   if (!c || max_iters < 1 || !(newton_rtol > 0)) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   double r0 = -1.0;
@@ -1606,6 +1643,7 @@ int pff_solve_pdas(pff_ctx* c, int max_iters, double newton_rtol, double* U_out,
 
 int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rtol, pff_report* reps,
                         int* n_steps) {
+  Range nvtx_range("pff_solve_load_step");
   if (!c || max_iters < 1 || !(newton_rtol > 0)) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   LevelData& L = c->lv[0];
@@ -1631,6 +1669,7 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
 }
 
 int pff_param_grad(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
+  Range nvtx_range("pff_param_grad");
   if (!c || !v) return PFF_ERR_INVALID_ARG;
   CR(ensure_st(c));
   LevelData& L = c->lv[0];
