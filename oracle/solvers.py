@@ -344,29 +344,40 @@ def pdas_step(mesh, prm, U, phi_old, phi_tilde, c=1.0, solve="direct", levels_kw
     return U + dU, act, float(np.linalg.norm(rhs)), info
 
 
-def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, comp=None, return_phit=False, **fields):
+def load_steps(mesh, prm, U, loads, max_iters=30, rtol=1e-8, comp=None, return_phit=False, stats=None,
+               **fields):
     """Quasi-static loading of the tension test (Sec. 5.1; comp = 0: of the shear test, Sec. 5.2, whose
-    top face moves to the right): for each load, u_comp := load on the top face (comp = d-1 by default),
-    phi_old := the previous step's phase field, phi~ := clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2:
-    linear extrapolation from the last two steps, dt = 1; phi^{n-1} for the first step), then Alg. 1
-    repeated until the active set is unchanged and ||R~|| <= rtol ||R~_0||. Returns the states (and,
-    with return_phit, the phi~ each step solved with, which the u-equation of its residual uses)."""
+    top face moves to the right). For each load: u_comp := load on the top face (comp = d-1 by
+    default); phi_old := the phase field of the last solved load step (the phase field of ``U`` before
+    the first); phi~ := clamp(2 phi^{n-1} - phi^{n-2}, 0, 1), the linear extrapolation of Sec. 3.2 from
+    the solutions of the previous two load steps (dt = 1), or phi^{n-1} while fewer than two load steps
+    have been solved: the initial phase field is not the solution of a load step, and extrapolating from
+    it doubles the diffuse profile the first step forms around the slit. Then Alg. 1 is repeated until
+    the active set is unchanged and ||R~|| <= rtol ||R~_0||. Returns the states (and, with return_phit,
+    the phi~ each step solved with, which the u-equation of its residual uses); ``stats``, if a list,
+    receives (iterations, converged) per step. A step that does not converge still becomes the
+    previous step of the next one."""
     d, nn = mesh.dim, mesh.n_nodes
     U = U.copy()
-    h1, h2 = U[d * nn:].copy(), None
+    solved = []               # phase fields of the solved load steps, the last two kept
+    start = U[d * nn:].copy()
     out, phits = [], []
     for load in loads:
         U[mesh.dof(d - 1 if comp is None else comp, mesh.top_nodes())] = load
-        phi_old = h1.copy()
-        phit = h1.copy() if h2 is None else np.clip(2.0 * h1 - h2, 0.0, 1.0)
-        norms, prev = [], None
+        prev_phi = solved[-1] if solved else start
+        phi_old = prev_phi.copy()
+        phit = prev_phi.copy() if len(solved) < 2 else np.clip(2.0 * solved[-1] - solved[-2], 0.0, 1.0)
+        norms, prev, conv = [], None, False
         for _ in range(max_iters):
             U, act, rn, _ = pdas_step(mesh, prm, U, phi_old, phit, **fields)
             norms.append(rn)
             if prev is not None and np.array_equal(prev, act) and rn <= rtol * norms[0]:
+                conv = True
                 break
             prev = act
-        h2, h1 = h1, U[d * nn:].copy()
+        if stats is not None:
+            stats.append((len(norms), conv))
+        solved = (solved + [U[d * nn:].copy()])[-2:]
         out.append(U.copy())
         phits.append(phit)
     return (out, phits) if return_phit else out
