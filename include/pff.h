@@ -220,16 +220,18 @@ int pff_set_load_component(pff_ctx* ctx, int comp);
 /* One quasi-static load step of the tension test (Sec. 5.1; of the shear test with
  * pff_set_load_component) from the current state: the loaded displacement component (u_dim by
  * default) on the top face is set to `load` (all other Dirichlet values kept), phi_old becomes
- * the phase field of the previous load step and phi~ its linear extrapolation from the last two
- * steps, clamp(2 phi^{n-1} - phi^{n-2}, 0, 1) (Sec. 3.2; phi^{n-1} while only one is known); then
- * pff_solve_pdas. The phase-field history starts from the state of the last pff_set_state and
- * advances only when the step converges. Same outputs and errors as pff_solve_pdas. */
+ * the phase field of the last solved load step (the state's own before the first) and phi~ the linear
+ * extrapolation from the solutions of the last two load steps, clamp(2 phi^{n-1} - phi^{n-2}, 0, 1)
+ * (Sec. 3.2), or phi_old while fewer than two load steps have been solved (the phase field given to
+ * pff_set_state is not the solution of a load step); then pff_solve_pdas. The history is cleared by
+ * pff_set_state and advances only when the step converges. Same outputs and errors as
+ * pff_solve_pdas. */
 int pff_solve_load_step(pff_ctx* ctx, double load, int max_iters, double newton_rtol, pff_report* reps,
                         int* n_steps);
 
 /* Phase-field history of the load-step loop, for checkpoint and resume: phi1 = phase field after the
  * last converged load step, phi2 = the one before (device arrays of n_nodes doubles); n_hist (host
- * int) = how many are known (0, 1 or 2). pff_get_history copies the known ones (outputs may be NULL;
+ * int) = how many converged load steps are known (0, 1 or 2; 2 once phi~ is extrapolated). pff_get_history copies the known ones (outputs may be NULL;
  * unknown ones are left untouched). pff_set_history installs a history after pff_set_state (which
  * clears it): with the state U and the history of a checkpoint taken after a converged load step, the
  * next pff_solve_load_step continues that run (same iterates up to the order of the floating-point

@@ -1648,10 +1648,10 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
   if (!c->has_state) return PFF_ERR_NO_STATE;
   LevelData& L = c->lv[0];
   const long long nn = L.nn;
-  if (c->nhist == 0) {
+  // Before the first solved load step the previous phase field is the state's own (held in hist1 as a
+  // work copy, not counted: it is not the solution of a load step, so phi~ is not extrapolated from it).
+  if (c->nhist == 0)
     CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
-    c->nhist = 1;
-  }
   CK(launch_load_step_prep(load_comp(c), nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr,
                            L.phit, c->phi_old, c->s));
   c->qp_valid = false;
@@ -1660,9 +1660,9 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
   c->mg_ready = false;
   const int st = pff_solve_pdas(c, max_iters, newton_rtol, nullptr, reps, n_steps);
   if (st == PFF_OK) {
-    std::swap(c->hist1, c->hist2);
+    if (c->nhist >= 1) std::swap(c->hist1, c->hist2);
     CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
-    c->nhist = 2;
+    c->nhist = c->nhist >= 1 ? 2 : 1;
     CK(cudaStreamSynchronize(c->s));
   }
   return st;

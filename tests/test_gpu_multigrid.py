@@ -190,22 +190,31 @@ def test_param_grad_and_adjoint(dim, p, N, split):
     assert rel(gU, pr.G().T @ vm) <= 1e-12
 
 
-def test_load_steps_against_oracle():
-    """Three quasi-static load steps with the extrapolated phase field: GPU (FGMRES + mixed GMG) against
-    the oracle (direct solves), 2D Q1 16 x 16, Miehe split."""
+@pytest.mark.parametrize("dim,p,N,loads", [(2, 1, 16, [4e-3, 8e-3, 1.2e-2]), (2, 2, 8, [1e-4, 2e-4, 3e-4]),
+                                             (3, 1, 4, [1e-4, 2e-4, 3e-4])])
+def test_load_steps_against_oracle(dim, p, N, loads):
+    """Three quasi-static load steps with the extrapolated phase field, Miehe split: GPU (FGMRES + mixed
+    GMG) against the oracle (direct solves). Every step converges on both sides (status and the
+    oracle's own test), in the same number of Newton iterations up to one, to the same state. The 2D Q2
+    and 3D Q1 cases are ones whose second step never converged when phi~ was extrapolated from the
+    initial phase field."""
     from oracle import mesh as M
     from paper_2005_00331_gb300 import setup_mesh
-    m = M.Mesh(2, 1, 16)
-    prm = fe.Params(121.15, 80.77, 2.7e-3, 2.0 / 16, 1e-10, 1)
+    m = M.Mesh(dim, p, N)
+    prm = fe.Params(121.15, 80.77, 2.7e-3, 2.0 / N, 1e-10, 1)
     U = m.dirichlet_values(0.0)
     phi = np.ones(m.n_nodes)
     phi[m.slit_nodes()] = 0.0
-    U[2 * m.n_nodes:] = phi
-    loads = [4e-3, 8e-3, 1.2e-2]
-    ref = S.load_steps(m, prm, U, loads)
-    ctx = setup_mesh(dim=2, degree=1, n_cells_1d=16, split=1, eps=2.0 / 16, mg_precision=32, lin_rtol=1e-10)
+    U[dim * m.n_nodes:] = phi
+    stats = []
+    ref = S.load_steps(m, prm, U, loads, stats=stats)
+    assert all(conv for _, conv in stats)
+    ctx = setup_mesh(dim=dim, degree=p, n_cells_1d=N, split=1, eps=2.0 / N, mg_precision=32, lin_rtol=1e-10)
     ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
     for k, load in enumerate(loads):
-        st, reps = ctx.solve_load_step(load)
+        st, reps = ctx.solve_load_step(load, check=False)
+        assert st == 0
+        assert abs(len(reps) - stats[k][0]) <= 1
         Ug = ctx.get_state().cpu().numpy()
         assert rel(Ug, ref[k]) <= 1e-6
+        assert ctx.get_history()[0] == min(k + 1, 2)
