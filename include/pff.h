@@ -76,7 +76,8 @@ typedef struct {
   double eps;         /* phase-field length scale epsilon */
   double kappa;       /* degradation regularisation: g(phi) = (1 - kappa) phi^2 + kappa */
   double as_c;        /* constant c of the active-set rule of Alg. 1 (default 1) */
-  int mg_precision;   /* 64: FP64 multigrid; 32: FP32 levels, smoothers, transfers (coarse solve FP64) */
+  int mg_precision;   /* 64: FP64 multigrid; 32: FP32 levels, smoothers, transfers (coarse solve per
+                         coarse_precision) */
   int cheb_degree;    /* Chebyshev-Jacobi smoother degree (paper: 5) */
   double cheb_lo;     /* smoothing interval [cheb_lo, cheb_hi] * lambda_max (paper: 0.24, 1.2) */
   double cheb_hi;
@@ -87,6 +88,9 @@ typedef struct {
   double lin_rtol;    /* FGMRES relative tolerance (paper: 1e-6) */
   int fp64_mode;      /* FP64 Jacobian applies: 0 native FP64 arithmetic; 1 double-word (float-float)
                          arithmetic on the FP32 pipe, about 48 significant bits */
+  int coarse_precision; /* coarse solve of the FP32 multigrid: 64 (default) FP64 inverses of the FP64
+                           coarse blocks, the cycle's vector cast to FP64 and back around it; 32 FP32
+                           inverses of the rounded blocks. Ignored (always 64) by the FP64 multigrid. */
 } pff_params;
 
 typedef struct {
@@ -100,7 +104,8 @@ typedef struct {
 } pff_report;
 
 /* Defaults: the paper's tension test (lambda 121.15, mu 80.77, G_c 2.7e-3, kappa 1e-10), split none,
- * dim 2, p 1, N 32, eps 2/N, c 1, FP32 multigrid, Chebyshev degree 5 on [0.24, 1.2] lambda_max,
+ * dim 2, p 1, N 32, eps 2/N, c 1, FP32 multigrid with FP64 coarse solve, Chebyshev degree 5 on
+ * [0.24, 1.2] lambda_max,
  * 15 eigen iterations, restart 50, relative tolerance 1e-6 (Sec. 5.1, Sec. 6.2), native FP64 applies.
  * Never fails. */
 void pff_default_params(pff_params* p);
@@ -185,8 +190,9 @@ int pff_smooth(pff_ctx* ctx, int level, const void* f, void* x, int precision);
 
 /* Coarse-level solve: z = G_c^{-1} r by block forward substitution over the block lower triangular
  * coarse matrix (Sec. 3.3), r and z FP64 in the coarsest level's layout. The dense inverses of the
- * diagonal blocks are held in the params' mg_precision: with mg_precision 32 they are computed and
- * applied in FP32 (r is rounded to FP32 on entry), as inside the FP32 V-cycle. */
+ * diagonal blocks are FP64 (Gauss-Jordan on the FP64 coarse blocks), the precision the FP32 V-cycle
+ * uses too; only with mg_precision 32 and coarse_precision 32 are they FP32 copies, computed and
+ * applied in FP32 (r is then rounded to FP32 on entry). */
 int pff_coarse_solve(pff_ctx* ctx, const double* r, double* z);
 
 /* One V-cycle of GMG(G) (Sec. 3.3) on the finest level: z = M^{-1} r, FP64 in and out; inside it
@@ -254,9 +260,10 @@ int pff_param_grad(pff_ctx* ctx, const double* v, double* g_gc, double* g_lambda
  * on first use; this entry point uses a fixed array in device global memory instead, of
  * PFF_NOALLOC_SCRATCH_DOUBLES doubles (16 MiB), which every GPU that loads the library holds until
  * the process exits. Problems that need more (3 * N^dim * (p+1)^dim doubles) are rejected with
- * PFF_ERR_TOO_LARGE before any work is queued. The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. No call allocates (no cudaMalloc, cudaFree or allocating library routine).
+ * PFF_ERR_TOO_LARGE before any work is queued. The context's device (that of the stream given to
+ * pff_setup_mesh) must be the current device, else PFF_ERR_INVALID_ARG: the array's address is a
+ * per-device one. The first call on a device looks up that address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. No call allocates (no cudaMalloc, cudaFree or allocating library routine).
  * All calls share the array: calls whose work overlaps on the GPU (other streams, other contexts)
  * race on it, so serialise them. Every scratch entry read is written earlier in the same call, so
  * the contents left by a previous call do not matter. Same arguments, results and requirements as

@@ -200,11 +200,15 @@ struct pff_ctx {
   long long prof_n = 0;
   bool capturing = false;
   bool use_graph = true;
+  int device = -1;  // the device of the context's stream, recorded at setup
   // kernel-family timing (pff_profile)
   int prof = 0;
   std::vector<cudaEvent_t> ev;
   int nev = 0;
 };
+
+// The coarse solve runs in FP32 only when the FP32 multigrid asks for it (coarse_precision 32).
+inline bool coarse32(const pff_ctx* c) { return c->prm.mg_precision == 32 && c->prm.coarse_precision == 32; }
 
 namespace {
 
@@ -601,8 +605,8 @@ int mg_level_branch(pff_ctx* c, int l) {
     // coarse level: dense blocks and their inverses (block forward substitution, Sec. 3.3)
     const int nn = (int)L.nn, nu = c->dim * nn;
     CK(launch_coarse_assemble(c->dim, c->p, c->prm.split, L.qp64, L.flags, L.g, L.t64, c->Au, c->Ap, c->Bc, c->s));
-    if (c->prm.mg_precision == 32) {
-      // the FP32 multigrid inverts FP32 copies (its coarse solve runs in FP32 like the rest of the cycle)
+    if (coarse32(c)) {
+      // FP32 coarse solve (non-default, coarse_precision 32): FP32 copies of the blocks inverted in FP32
       CK(launch_cast<double, float>((long long)nu * nu, c->Au, c->Au32, c->s));
       CK(launch_cast<double, float>((long long)nn * nn, c->Ap, c->Ap32, c->s));
       CK(launch_cast<double, float>((long long)nn * nu, c->Bc, c->Bc32, c->s));
@@ -710,7 +714,8 @@ int mg_setup(pff_ctx* c) {
   return PFF_OK;
 }
 
-// z = G_c^{-1} r on the coarsest level, in the multigrid's precision:
+// z = G_c^{-1} r on the coarsest level, in FP64 unless the FP32 multigrid asks for an FP32 coarse solve
+// (an FP32 cycle casts its vector to FP64 and back around the FP64 solve):
 // z_u = Au^{-1} r_u, z_phi = Ap^{-1} (r_phi - B z_u) (block forward substitution).
 template <typename Real>
 int coarse_solve_blocks(pff_ctx* c, const Real* Au, const Real* Ap, const Real* Bc, Real* ct, const Real* r, Real* z) {
@@ -727,7 +732,7 @@ template <typename Real>
 int coarse_solve(pff_ctx* c, const Real* r, Real* z);
 template <>
 int coarse_solve<double>(pff_ctx* c, const double* r, double* z) {
-  if (c->prm.mg_precision != 32) return coarse_solve_blocks<double>(c, c->Au, c->Ap, c->Bc, c->ct, r, z);
+  if (!coarse32(c)) return coarse_solve_blocks<double>(c, c->Au, c->Ap, c->Bc, c->ct, r, z);
   const long long n = c->lv[c->nlev - 1].nd;
   CK(launch_cast<double, float>(n, r, c->cr32, c->s));
   CR(coarse_solve_blocks<float>(c, c->Au32, c->Ap32, c->Bc32, c->ct32, c->cr32, c->ce32));
@@ -736,7 +741,7 @@ int coarse_solve<double>(pff_ctx* c, const double* r, double* z) {
 }
 template <>
 int coarse_solve<float>(pff_ctx* c, const float* r, float* z) {
-  if (c->prm.mg_precision == 32) return coarse_solve_blocks<float>(c, c->Au32, c->Ap32, c->Bc32, c->ct32, r, z);
+  if (coarse32(c)) return coarse_solve_blocks<float>(c, c->Au32, c->Ap32, c->Bc32, c->ct32, r, z);
   const long long n = c->lv[c->nlev - 1].nd;
   CK(launch_cast<float, double>(n, r, c->cr, c->s));
   CR(coarse_solve_blocks<double>(c, c->Au, c->Ap, c->Bc, c->ct, c->cr, c->ce));
@@ -1033,6 +1038,7 @@ void pff_default_params(pff_params* p) {
   p->kappa = 1e-10;
   p->as_c = 1.0;
   p->mg_precision = 32;
+  p->coarse_precision = 64;
   p->cheb_degree = 5;
   p->cheb_lo = 0.24;
   p->cheb_hi = 1.2;
@@ -1163,7 +1169,7 @@ static int setup_impl(pff_ctx* c) {
   CR(dalloc(c, &c->Au, nuc * nuc, TAG_COARSE));
   CR(dalloc(c, &c->Ap, nnc * nnc, TAG_COARSE));
   CR(dalloc(c, &c->Bc, nnc * nuc, TAG_COARSE));
-  if (c->prm.mg_precision == 32) {
+  if (coarse32(c)) {
     CR(dalloc(c, &c->Au32, nuc * nuc, TAG_COARSE));
     CR(dalloc(c, &c->Ap32, nnc * nnc, TAG_COARSE));
     CR(dalloc(c, &c->Bc32, nnc * nuc, TAG_COARSE));
@@ -1201,12 +1207,18 @@ int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream) {
       p->coarse_min < 1 || (p->split != PFF_SPLIT_NONE && p->split != PFF_SPLIT_MIEHE) ||
       !valid_prec(p->mg_precision) || p->cheb_degree < 1 || !(p->cheb_hi > p->cheb_lo) || !(p->cheb_lo > 0) ||
       p->eig_iters < 1 || p->eig_iters > 64 || p->gmres_restart < 1 || p->gmres_max_iters < 1 ||
-      !(p->lin_rtol > 0) || !(p->eps > 0) || (p->fp64_mode != 0 && p->fp64_mode != 1))
+      !(p->lin_rtol > 0) || !(p->eps > 0) || (p->fp64_mode != 0 && p->fp64_mode != 1) ||
+      !valid_prec(p->coarse_precision))
     return PFF_ERR_INVALID_ARG;
   pff_ctx* c = new (std::nothrow) pff_ctx();
   if (!c) return PFF_ERR_OOM;
   c->prm = *p;
   c->s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamGetDevice(c->s, &c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PFF_ERR_CUDA;
+  }
   const int st = setup_impl(c);
   if (st != PFF_OK) {
     pff_destroy(c);
@@ -1733,11 +1745,12 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 std::mutex g_noalloc_mutex;
 
-// Device address of the scratch array on the current device (looked up once per device).
-int noalloc_scratch(double** out) {
+// Device address of the scratch array on the context's device (looked up once per device). The symbol
+// address belongs to whichever device is current, so the context's device must be the current one.
+int noalloc_scratch(const pff_ctx* c, double** out) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PFF_ERR_INVALID_ARG;
+  if (dev != c->device || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PFF_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
@@ -1750,6 +1763,7 @@ int noalloc_scratch(double** out) {
 }  // namespace
 
 extern "C" int pff_param_grad_noalloc(pff_ctx* c, const double* v, double* g_gc, double* g_lambda, double* g_mu) {
+  Range nvtx_range("pff_param_grad_noalloc");
   if (!c || !v) return PFF_ERR_INVALID_ARG;
   if (!c->has_state) return PFF_ERR_NO_STATE;
   LevelData& L = c->lv[0];
@@ -1757,7 +1771,7 @@ extern "C" int pff_param_grad_noalloc(pff_ctx* c, const double* v, double* g_gc,
   const int nq = c->dim == 2 ? (c->p + 1) * (c->p + 1) : (c->p + 1) * (c->p + 1) * (c->p + 1);
   if (3 * ncell * nq > PFF_NOALLOC_SCRATCH_DOUBLES) return PFF_ERR_TOO_LARGE;
   double* tmp = nullptr;
-  CR(noalloc_scratch(&tmp));
+  CR(noalloc_scratch(c, &tmp));
   CR(ensure_st(c));
   MatConst mc{c->prm.lambda, c->prm.mu, c->prm.gc, c->prm.eps, c->prm.kappa};
   double* vm = c->scratch;  // allocated with the context

@@ -35,7 +35,8 @@ class Params(ctypes.Structure):
                 ("mg_precision", ctypes.c_int), ("cheb_degree", ctypes.c_int),
                 ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int),
                 ("eig_seed", ctypes.c_ulonglong), ("gmres_restart", ctypes.c_int),
-                ("gmres_max_iters", ctypes.c_int), ("lin_rtol", ctypes.c_double), ("fp64_mode", ctypes.c_int)]
+                ("gmres_max_iters", ctypes.c_int), ("lin_rtol", ctypes.c_double), ("fp64_mode", ctypes.c_int),
+                ("coarse_precision", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

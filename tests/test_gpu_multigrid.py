@@ -102,9 +102,56 @@ def test_eigen_smoother_coarse_vcycle_fp64(dim, p, N, split):
     assert rel(z, S.vcycle(lv, r)) <= 1e-9
 
 
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_coarse_solve_precision(dim, p, N, split):
+    """The FP32 multigrid's coarse solve is FP64 by default (dense FP64 inverses): the direct solve of the
+    oracle's coarse operator to 1e-10. The FP32 variant (coarse_precision 32) only to FP32 accuracy."""
+    pr = Problem(dim, p, N, split=split, seed=5, active_frac=0.2)
+    Lc = oracle_levels(pr)[-1]
+    r = np.where(Lc.mask, 0.0, np.random.default_rng(9).normal(size=Lc.mesh.n_dofs))
+    ref = spla.spsolve(Lc.G.tocsc(), r)
+    with pr.context(mg_precision=32) as ctx:
+        assert rel(ctx.coarse_solve(cuda(r)).cpu().numpy(), ref) <= 1e-10
+    with pr.context(mg_precision=32, coarse_precision=32) as ctx:
+        err = rel(ctx.coarse_solve(cuda(r)).cpu().numpy(), ref)
+        assert 1e-10 < err <= 1e-3
+
+
+@pytest.mark.parametrize("dim,p,N,split", MG_CASES)
+def test_smoother_fp32(dim, p, N, split):
+    """The FP32 smoother of every smoothed level against the oracle's FP64 smoother with the same
+    eigenvalue estimate: the FP32 multigrid's own lambda_max agrees with the oracle's to 1e-5 and one
+    degree-5 application to 2e-5 (rounding of a few dozen FP32 operations per entry, amplified by at
+    most the Chebyshev polynomial's growth on the spectrum)."""
+    pr = Problem(dim, p, N, split=split, seed=5, active_frac=0.2)
+    lv = oracle_levels(pr, cheb_degree=5)
+    with pr.context(mg_precision=32) as ctx:
+        for l in range(len(lv) - 1):
+            lam = ctx.lambda_max(l)
+            for b in range(2):
+                assert abs(lam[b] - lv[l].lam_max[b]) <= 1e-5 * lv[l].lam_max[b]
+            f = np.where(lv[l].mask, 0.0, np.random.default_rng(l).normal(size=lv[l].mesh.n_dofs))
+            x = ctx.smooth(l, cuda(f, np.float32), precision=32).cpu().numpy().astype(np.float64)
+            assert rel(x, S.smooth(lv[l], f)) <= 2e-5
+
+
+@pytest.mark.parametrize("dim,p,N,split,cmin", [(2, 1, 32, 1, 3), (2, 2, 32, 1, 3), (3, 1, 16, 0, 2)])
+def test_vcycle_fp32_four_levels(dim, p, N, split, cmin):
+    """The FP32 V-cycle (FP64 coarse solve) on four levels against the oracle's FP64 cycle."""
+    pr = Problem(dim, p, N, split=split, seed=6, active_frac=0.2)
+    lv = S.build_levels(pr.dim, pr.p, pr.N, pr.prm, pr.U, pr.phi_tilde, pr.active, cheb_degree=5,
+                        eig_iters=15, eig_seed=0, coarse_min=cmin)
+    assert len(lv) >= 4
+    with pr.context(mg_precision=32, coarse_min=cmin) as ctx:
+        assert ctx.n_levels == len(lv)
+        r = np.where(lv[0].mask, 0.0, np.random.default_rng(11).normal(size=pr.mesh.n_dofs))
+        assert rel(ctx.vcycle(cuda(r)).cpu().numpy(), S.vcycle(lv, r)) <= 1e-3
+
+
 @pytest.mark.parametrize("dim,p,N,split", [(2, 2, 8, 1), (3, 1, 8, 0)])
 def test_vcycle_fp32(dim, p, N, split):
-    """Mixed precision: FP32 levels and FP32 coarse inverses; agrees with the FP64 cycle to FP32 accuracy."""
+    """Mixed precision: FP32 levels, smoothers and transfers, FP64 coarse solve; agrees with the FP64
+    cycle to FP32 accuracy."""
     pr = Problem(dim, p, N, split=split, seed=6, active_frac=0.2)
     lv = oracle_levels(pr)
     ctx = pr.context(mg_precision=32)
