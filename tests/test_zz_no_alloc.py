@@ -21,18 +21,26 @@ def cuda(a):
 
 
 def test_noalloc_matches_param_grad_on_two_calls():
+    """Two calls in a row on a fresh context (the shared scratch keeps the previous call's contents)
+    equal pff_param_grad within 1e-12 and leave the context's device memory unchanged; the ordinary
+    entry point called afterwards allocates its scratch, which shows the accounting would see it."""
     pr = Problem(2, 2, 16, split=1, seed=31, fields=True)
     ctx = pr.context()
     nn = pr.mesh.n_nodes
-    outs = [torch.empty(nn, dtype=torch.float64, device="cuda") for _ in range(3)]
-    for call in range(2):  # two calls in a row: the shared scratch keeps the previous call's contents
-        v = cuda(np.random.default_rng(100 + call).normal(size=pr.mesh.n_dofs))
+    vs = [cuda(np.random.default_rng(100 + call).normal(size=pr.mesh.n_dofs)) for call in range(2)]
+    m0 = ctx.memory()
+    got = []
+    for v in vs:
+        outs = [torch.empty(nn, dtype=torch.float64, device="cuda") for _ in range(3)]
+        got.append([g.clone() for g in ctx.param_grad_noalloc(*outs, v)])
+    torch.cuda.synchronize()
+    assert ctx.memory() == m0
+    for v, g in zip(vs, got):
         ref = ctx.param_grad(v)
-        got = ctx.param_grad_noalloc(*outs, v)
-        torch.cuda.synchronize()
-        for a, b in zip(got, ref):
+        for a, b in zip(g, ref):
             a, b = a.cpu().numpy(), b.cpu().numpy()
             assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+    assert ctx.memory()["total"] > m0["total"]
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
