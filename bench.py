@@ -12,8 +12,12 @@ unless --mg-precision 64; the outer FP64 operator in double-word arithmetic unle
 
 value = DoFs processed per second of full Newton steps (n_dofs * steps / time, summed over
 ranks). Extra keys: the Jacobian-apply sweep (p = 1..4, FP64 and FP32), the Newton step with the
-FP64 multigrid, the roofline of the dominant kernel, the end-to-end figure through host buffers,
-SM clocks during the timed region and the CPU oracle baseline.
+FP64 multigrid, the full active-set solve to the 1e-8 Newton tolerance with the mixed and with the
+plain FP64 multigrid (pdas_1e8; its final residual recomputed by the oracle), the error of the
+Newton update against the oracle's direct-solve step (oracle_error), the roofline of the dominant
+kernel, the end-to-end figure through host buffers (the mean over the same number of steps as
+value), SM clocks during the timed region and the CPU oracle baseline. The oracle runs only in the
+CPU leg (rank 0 at N = 1; --no-cpu skips it), after the GPU timings.
 """
 import argparse
 import json
@@ -170,7 +174,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -312,7 +316,7 @@ def run_native(a, rank, world):
     U_d = torch.empty(nd, dtype=torch.float64, device=dev)
     po_d = torch.empty_like(phi_old)
     e2e = []
-    for i in range(0 if a.no_e2e else max(2, min(a.steps, 3))):
+    for i in range(0 if a.no_e2e else a.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -323,7 +327,7 @@ def run_native(a, rank, world):
         U_back.copy_(U_d, non_blocking=True)
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t)
-    out["e2e_s"] = statistics.median(e2e) if e2e else float("nan")
+    out["e2e_s"] = statistics.mean(e2e) if e2e else float("nan")  # same statistic as the device-timed value
     out["h2d"] = 8 * (nd + ctx.n_nodes)
     out["d2h"] = 8 * nd
 
@@ -355,8 +359,116 @@ def run_native(a, rank, world):
         out["fp64_mg"] = {"step_ms": min(t64), "gmres_iters": rep64["gmres_iters"], "status": rep64["status"],
                           "rel_diff_vs_mixed": float((Um - U64).norm() / (U64 - U).norm())}
         ctx64.close()
+        out["pdas_1e8"], out["pdas_finals"] = pdas_to_tolerance(a, dev, U_h, phi_old_h)
+        out["phi_old_h"] = phi_old_h
     ctx.close()
     return out
+
+
+def oracle_specimen(dim, p, N, split, state):
+    """The specimen of the workload as the oracle builds it (its own mesh, Dirichlet lift and slit), fed
+    from the seeded input generators: (mesh, params, U, phi_old)."""
+    from oracle import fe, mesh as M
+    from paper_2005_00331_gb300 import inputs
+    m = M.Mesh(dim, p, N)
+    prm = fe.Params(eps=2.0 / N, split=split)
+    nn = m.n_nodes
+    U = m.dirichlet_values(1e-3)
+    if state == "tension":
+        phi = np.ones(nn)
+        phi[m.slit_nodes()] = 0.0
+        U[dim * nn:] = phi
+        return m, prm, U, phi.copy()
+    U[:dim * nn] += np.where(m.dirichlet_mask()[:dim * nn], 0.0, inputs.displacement_noise(nn, dim, 0))
+    phi = inputs.uniform_phase(nn, 0)
+    phi[m.slit_nodes()] = 0.0
+    U[dim * nn:] = phi
+    return m, prm, U, inputs.phi_old_above(phi, 0)
+
+
+ORACLE_CHECK_CASES = ((2, 1, 32, "tension"), (2, 2, 64, "random"))
+
+
+def oracle_errors(a, dev):
+    """Error of the GPU's Newton update against the oracle's (one step of Alg. 1 with a sparse direct
+    solve), with the mixed multigrid (double-word outer operator, as timed) and with the FP64 one (native
+    FP64 outer operator): ||U_gpu - U_oracle|| / ||U_oracle - U||, and whether the active sets agree
+    bit for bit. Sizes the oracle finishes in seconds: the 32 x 32 Q1 tension test from rest and the
+    2D Q2 64 x 64 random state of the workload family. The linear solves stop at relative 1e-6."""
+    import torch
+
+    from oracle import solvers as S
+    from paper_2005_00331_gb300 import setup_mesh
+    out = {}
+    for dim, p, N, state in ORACLE_CHECK_CASES:
+        m, prm, U, po = oracle_specimen(dim, p, N, state=state, split=a.split)
+        U_ref, act_ref, _, _ = S.pdas_step(m, prm, U, po, po)
+        step = float(np.linalg.norm(U_ref - U))
+        case = {"n_dofs": m.n_dofs, "state": state, "active": int(act_ref.sum())}
+        for name, mg, fm in (("mixed", 32, 1), ("fp64", 64, 0)):
+            with setup_mesh(dim=dim, degree=p, n_cells_1d=N, split=a.split, eps=2.0 / N, mg_precision=mg,
+                            cheb_degree=a.cheb_degree, fp64_mode=fm) as ctx:
+                t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+                ctx.set_state(t(U), t(po), t(po), None)
+                rep = ctx.solve_newton_step(check=False)
+                Ug = ctx.get_state().cpu().numpy()
+                act = ctx.get_active().cpu().numpy().astype(bool)
+            case[name] = {"rel_err_update": float(np.linalg.norm(Ug - U_ref)) / step,
+                          "active_set_equal": bool(np.array_equal(act, act_ref)), "gmres_iters": rep["gmres_iters"],
+                          "gmres_rel": rep["gmres_rel"]}
+        out["%dD_Q%d_%d" % (dim, p, N)] = case
+    return out
+
+
+def pdas_to_tolerance(a, dev, U_h, po_h, rtol=1e-8):
+    """The full active-set Newton solve of the workload (Alg. 1 until the active set is unchanged and
+    ||R~|| <= rtol ||R~_0||) with the mixed multigrid (FP32 levels, FP64 coarse solve, double-word outer
+    operator, as timed) and with the plain FP64 one (FP64 multigrid, native FP64 outer operator): time
+    per Newton step (CUDA events, after a warm-up solve), Newton and FGMRES iterations, and the final
+    reduced residual recomputed by the oracle at the GPU's final state (Dirichlet and final active rows
+    removed) relative to the loop's ||R~_0||."""
+    import torch
+
+    from paper_2005_00331_gb300 import setup_mesh
+    stream = torch.cuda.current_stream()
+    out, finals = {"newton_rtol": rtol}, {}
+    U = torch.from_numpy(U_h).to(dev)
+    po = torch.from_numpy(po_h).to(dev)
+    for name, mg, fm in (("mixed", 32, a.fp64_mode), ("fp64", 64, 0)):
+        with setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
+                        mg_precision=mg, cheb_degree=a.cheb_degree, fp64_mode=fm) as ctx:
+            ctx.set_state(U, po, po, None)
+            ctx.solve_pdas(max_iters=30, newton_rtol=rtol, check=False)  # warm-up: graph capture
+            ctx.set_state(U, po, po, None)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, reps = ctx.solve_pdas(max_iters=30, newton_rtol=rtol, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            Uf = ctx.get_state().cpu().numpy()
+            act = ctx.get_active().cpu().numpy().astype(bool)
+        finals[name] = (Uf, act)
+        out[name] = {"status": st, "newton_steps": len(reps), "ms": ms, "ms_per_newton_step": ms / max(1, len(reps)),
+                     "gmres_iters": [r["gmres_iters"] for r in reps], "res_norm_0": reps[0]["res_norm"],
+                     "res_rel_last_step": reps[-1]["res_norm"] / reps[0]["res_norm"],
+                     "n_active": reps[-1]["n_active"]}
+    out["rel_diff_mixed_vs_fp64"] = float(np.linalg.norm(finals["mixed"][0] - finals["fp64"][0]) /
+                                          np.linalg.norm(finals["fp64"][0] - U_h))
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_newton_step"] / out["mixed"]["ms_per_newton_step"]
+    return out, finals
+
+
+def oracle_final_residuals(a, po_h, finals, pdas):
+    """The final reduced residual of each 1e-8 solve recomputed by the oracle at the GPU's final state
+    (Dirichlet rows and the final active set removed), relative to the loop's ||R~_0||."""
+    from oracle import fe
+    m, prm, _, _ = oracle_specimen(a.dim, a.degree, a.cells, a.split, "random")
+    for name, (Uf, act) in finals.items():
+        R = fe.residual(m, prm, Uf, po_h)
+        R[a.dim * m.n_nodes:][act] = 0.0
+        pdas[name]["oracle_final_res_rel"] = float(np.linalg.norm(R)) / pdas[name]["res_norm_0"]
 
 
 def apply_sweep(a, dev, flush, reps=20):
@@ -825,6 +937,9 @@ def main():
                 return
             vals.append(c)
         v = statistics.median([c["value"] for c in vals])
+        config["sample"] = ("each step times one oracle PDAS Newton step on the %dD Q%d specimen with %d^%d cells "
+                            "(%s); the oracle's DoF/s varies by under 3 %% between 32^2 and 96^2 cells"
+                            % (a.dim, a.degree, CPU_SAMPLE_CELLS, a.dim, vals[0]["sample"].split("(")[-1].split(")")[0]))
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DoF/s", "n_gpus": a.gpus,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": (time.perf_counter() - t) * 1e3 / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -901,6 +1016,7 @@ def main():
     if "sweep" in r:
         line["jacobian_apply"] = r["sweep"]
         line["fp64_mg_newton_step"] = r["fp64_mg"]
+        line["pdas_1e8"] = r["pdas_1e8"]
         fp64 = r["sweep"].get("p%d_fp64" % a.degree)
         if fp64:
             line["jacobian_apply_fp64_roofline"] = {
@@ -913,7 +1029,10 @@ def main():
                 "kernel": "FP64 values, double-word arithmetic on the FP32 pipe", "bound": "hbm",
                 "achieved": ff["GB_per_s"], "peak": hbm, "unit": "GB/s", "frac": ff["GB_per_s"] / hbm,
                 "peak_kind": hbm_kind}
-    if not a.no_cpu and world == 1:  # rank 0 at N = 1 only
+    if not a.no_cpu and world == 1:  # rank 0 at N = 1 only: the oracle's timings and checks
+        if "pdas_finals" in r:
+            oracle_final_residuals(a, r["phi_old_h"], r["pdas_finals"], line["pdas_1e8"])
+            line["oracle_error"] = oracle_errors(a, torch.device("cuda", torch.cuda.current_device()))
         for key, fn in (("cpu_baseline", lambda: cpu_oracle_sample(a, CPU_BASELINE_CELLS)),
                         ("cpu_baseline_all_cores", lambda: cpu_oracle_all_cores(a))):
             try:  # the CPU baselines are reported beside the GPU numbers; they must not lose the line
