@@ -5,7 +5,7 @@ of Eq. (G) and element residuals of Eq. (residual), no sum factorisation); the G
 whole vector in the launch configuration the benchmark times. Sizes:
 * 2D Q2 256 x 256 (789,507 DoFs), state u ~ N(0, 1e-6), phi ~ U(0.9, 1), phi_old = phi (every
   phase-field DoF active by the configured rule phi_old - phi < 1e-8) and a mixed variant;
-* 3D Q2 64^3 (8,586,756 DoFs), notched cube;
+* 3D Q2 64^3 (8,586,756 DoFs) and 3D Q3 48^3 (12,194,500 DoFs), notched cube;
 * 2D Q2 128 x 128 (198,147 DoFs) with a lognormal nodal G_c field: adjoint and parameter gradients.
 """
 import numpy as np
@@ -82,6 +82,22 @@ class Big:
         y = np.where(self.mask, x, y)
         return y[dofs]
 
+    def rows_apply_many(self, dofs, xs):
+        """rows_apply for several inputs, with the element matrices of the sampled cells built once."""
+        m = self.m
+        cells = cells_of_nodes(m, dofs % m.n_nodes)
+        T = fe.Tables(m)
+        cd = m.cell_dofs()[cells]
+        K = np.concatenate([fe.element_matrices(m, self.prm, self.U, self.phi_old, cells[s:s + 256], T, **self.fields)
+                            for s in range(0, len(cells), 256)])
+        out = []
+        for x in xs:
+            xm = np.where(self.mask, 0.0, x)
+            y = np.zeros(m.n_dofs)
+            np.add.at(y, cd, np.einsum("cij,cj->ci", K, xm[cd]))
+            out.append(np.where(self.mask, x, y)[dofs])
+        return out
+
     def rows_residual(self, dofs):
         m = self.m
         cells = cells_of_nodes(m, dofs % m.n_nodes)
@@ -114,14 +130,36 @@ def test_c2_apply_and_residual_sampled(mixed):
     assert rel(r[dofs], big.rows_residual(dofs)) <= 1e-12
 
 
+def _apply_all_precisions(big, x, dofs):
+    """Sampled rows of the masked apply in FP64 (double-word and native arithmetic, 1e-12) and in FP32
+    (2e-5 against the oracle applied to the FP32-rounded input), each in the launch configuration of a
+    context on the full mesh."""
+    ref, ref32 = big.rows_apply_many(dofs, [x, x.astype(np.float32).astype(np.float64)])
+    for kw, prec, tol, r in (({"fp64_mode": 1}, 64, 1e-12, ref), ({"fp64_mode": 0}, 64, 1e-12, ref),
+                             ({}, 32, 2e-5, ref32)):
+        ctx = big.context(**kw)
+        xd = cuda(x, np.float32 if prec == 32 else np.float64)
+        y = ctx.apply_jacobian(xd).cpu().numpy().astype(np.float64)
+        assert rel(y[dofs], r) <= tol, (kw, prec)
+        ctx.close()
+        del ctx
+
+
 def test_c3_apply_sampled():
+    """3D Q2 64^3 notched cube (8.6 M DoFs)."""
     big = Big(3, 2, 64, seed=2, mixed=True)
-    x = inputs.normal_vector(big.m.n_dofs, 4)
-    dofs = big.sample(120, seed=5)
-    ref = big.rows_apply(dofs, x)
-    ctx = big.context(fp64_mode=1)
-    y = ctx.apply_jacobian(cuda(x)).cpu().numpy()
-    assert rel(y[dofs], ref) <= 1e-12
+    _apply_all_precisions(big, inputs.normal_vector(big.m.n_dofs, 4), big.sample(120, seed=5))
+
+
+def test_c5_apply_and_residual_sampled():
+    """3D Q3 48^3 notched cube (12.2 M DoFs), the size of the load-step configuration: applies in all
+    precisions and the FP64 residual on sampled rows."""
+    big = Big(3, 3, 48, seed=3, mixed=True)
+    dofs = big.sample(40, seed=6)
+    _apply_all_precisions(big, inputs.normal_vector(big.m.n_dofs, 5), dofs)
+    ctx = big.context()
+    r = ctx.residual().cpu().numpy()
+    assert rel(r[dofs], big.rows_residual(dofs)) <= 1e-12
 
 
 def test_c4_adjoint_sampled():
