@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--max-seconds", type=float, default=600.0,
                     help="--mode loadsteps: stop a precision's loading after this many seconds (partial result)")
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
+    ap.add_argument("--fp32-tangent", type=int, default=0,
+                    help="FP32 applies (2D): 0 stored per-point values, 1 recompute the tangent from the nodal state")
     ap.add_argument("--fp64-mode", type=int, default=1,
                     help="FP64 Jacobian applies: 0 native FP64, 1 double-word arithmetic on the FP32 pipe (2D)")
     return ap.parse_args()
@@ -235,6 +237,13 @@ def apply_bytes_per_dof(dim, p, split, real_bytes):
     return 2 * real_bytes + per_cell / dofs_per_cell + 1.0 / (dim + 1)
 
 
+def method_bytes_per_dof(dim, real_bytes):
+    """Algorithmic (method-minimum) bytes per DoF of one Jacobian apply: read x and write y (one value
+    per DoF each), read the nodal state (u, phi, phi~: d + 2 values per node, from which the tangent can
+    be recomputed) and one flag byte per node; d + 1 DoFs per node."""
+    return 2 * real_bytes + (dim + 2) * real_bytes / (dim + 1) + 1.0 / (dim + 1)
+
+
 def apply_flops_per_dof(dim, p, split):
     """Floating-point operations per DoF of one Jacobian apply as the kernels k_op2d / k_op3d do it
     (two per fused multiply-add; amortised over large tiles, seams neglected). n = p + 1 points per
@@ -260,7 +269,8 @@ def run_native(a, rank, world):
     stream = torch.cuda.current_stream()
     eps = 2.0 / a.cells
     ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=eps,
-                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode,
+                     fp32_tangent=a.fp32_tangent)
     U_h, phi_old_h = make_state(ctx, a, seed=rank)
     U = torch.from_numpy(U_h).to(dev)
     phi_old = torch.from_numpy(phi_old_h).to(dev)
@@ -436,9 +446,12 @@ def pdas_to_tolerance(a, dev, U_h, po_h, rtol=1e-8):
     out, finals = {"newton_rtol": rtol}, {}
     U = torch.from_numpy(U_h).to(dev)
     po = torch.from_numpy(po_h).to(dev)
-    for name, mg, fm in (("mixed", 32, a.fp64_mode), ("fp64", 64, 0)):
+    # mixed_native_outer separates the two changes between "mixed" and "fp64": the multigrid precision and
+    # the outer operator's arithmetic (double-word vs native FP64)
+    for name, mg, fm in (("mixed", 32, a.fp64_mode), ("mixed_native_outer", 32, 0), ("fp64", 64, 0)):
         with setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
-                        mg_precision=mg, cheb_degree=a.cheb_degree, fp64_mode=fm) as ctx:
+                        mg_precision=mg, cheb_degree=a.cheb_degree, fp64_mode=fm,
+                        fp32_tangent=a.fp32_tangent) as ctx:
             ctx.set_state(U, po, po, None)
             ctx.solve_pdas(max_iters=30, newton_rtol=rtol, check=False)  # warm-up: graph capture
             ctx.set_state(U, po, po, None)
@@ -459,6 +472,8 @@ def pdas_to_tolerance(a, dev, U_h, po_h, rtol=1e-8):
     out["rel_diff_mixed_vs_fp64"] = float(np.linalg.norm(finals["mixed"][0] - finals["fp64"][0]) /
                                           np.linalg.norm(finals["fp64"][0] - U_h))
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_newton_step"] / out["mixed"]["ms_per_newton_step"]
+    out["speedup_mixed_native_outer_vs_fp64"] = (out["fp64"]["ms_per_newton_step"] /
+                                                 out["mixed_native_outer"]["ms_per_newton_step"])
     return out, finals
 
 
@@ -530,7 +545,8 @@ def run_apply_only(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
-                     mg_precision=32, fp64_mode=a.fp64_mode)
+                     mg_precision=32, fp64_mode=a.fp64_mode,
+                     fp32_tangent=a.fp32_tangent)
     U_h, po_h = make_state(ctx, a, seed=0)
     U = torch.from_numpy(U_h).to(dev)
     po = torch.from_numpy(po_h).to(dev)
@@ -716,7 +732,8 @@ def run_vcycle(a):
     from paper_2005_00331_gb300 import setup_mesh
     dev = torch.device("cuda", torch.cuda.current_device())
     ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
-                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+                     mg_precision=a.mg_precision, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode,
+                     fp32_tangent=a.fp32_tangent)
     U_h, po_h = make_state(ctx, a, seed=0)
     ctx.set_state(torch.from_numpy(U_h).to(dev), torch.from_numpy(po_h).to(dev),
                   torch.from_numpy(po_h).to(dev), None)
@@ -923,7 +940,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     config = {"workload": workload_name(a), "dim": a.dim, "degree": a.degree, "cells_per_dir": a.cells,
               "split": "miehe" if a.split else "none", "mg_precision": a.mg_precision,
-              "cheb_degree": a.cheb_degree, "linear_rtol": 1e-6, "parallelism": "replicas" if world > 1 else "1 GPU",
+              "cheb_degree": a.cheb_degree, "linear_rtol": 1e-6,
+              "fp32_tangent": "recomputed from the nodal state" if a.fp32_tangent else "stored per-point values", "parallelism": "replicas" if world > 1 else "1 GPU",
               "l2": "256 MB buffer written before every timed step (flushes the 135 MB L2)"}
     if a.impl == "reference":
         if rank != 0:
@@ -990,7 +1008,7 @@ def main():
     hbm, hbm_kind = peaks()
     real_bytes = 4 if a.mg_precision == 32 else 8
     per_launch = r["kern_ms"] / max(1, r["kern_launches"])
-    bpd = apply_bytes_per_dof(a.dim, a.degree, a.split, real_bytes)
+    bpd = method_bytes_per_dof(a.dim, real_bytes)
     achieved = bpd * r["n_dofs"] / (per_launch * 1e-3) / 1e9 if r["kern_launches"] else None
     rep = r["reports"][-1]
     line = {
@@ -1009,7 +1027,8 @@ def main():
                      "frac": (achieved / hbm) if achieved else None,
                      "traffic": measured_traffic(a, r["n_dofs"]) if a.mg_precision == 32 else None,
                      "peak_kind": hbm_kind, "launches": r["kern_launches"], "avg_launch_ms": per_launch,
-                     "bytes_per_dof": bpd},
+                     "bytes_per_dof": bpd, "bytes_kind": "method minimum: x, y, nodal state (u, phi, phi~), flags",
+                     "stored_tangent_bytes_per_dof": apply_bytes_per_dof(a.dim, a.degree, a.split, real_bytes)},
         "e2e": {"value": r["n_dofs"] * world / r["e2e_s"], "unit": "DoF/s", "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
         "clocks": r["clocks"],

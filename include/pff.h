@@ -62,6 +62,7 @@ extern "C" {
 #define PFF_FLAG_TOP 0x10u            /* node on the top face */
 #define PFF_FLAG_BOTTOM 0x20u         /* node on the bottom face */
 #define PFF_FLAG_SLIT 0x40u           /* node on the slit / notch (last coord 1/2, x <= 1/2) */
+#define PFF_FLAG_COPY 0x80u           /* copy of a slit node used by the cells below a cut slit */
 
 typedef struct pff_ctx pff_ctx; /* opaque: mesh hierarchy, states, per-point data, workspaces */
 
@@ -91,6 +92,22 @@ typedef struct {
   int coarse_precision; /* coarse solve of the FP32 multigrid: 64 (default) FP64 inverses of the FP64
                            coarse blocks, the cycle's vector cast to FP64 and back around it; 32 FP32
                            inverses of the rounded blocks. Ignored (always 64) by the FP64 multigrid. */
+  int slit_cut;       /* 0 (default): one node per grid point, the slit enters through the state (phi = 0
+                         on its nodes). 1: the slit is cut into the finest mesh (Sec. 5.1): every node
+                         on the slit except the tip (last coordinate 1/2, x < 1/2) gets a second copy,
+                         which the cells below the slit use. The copies are numbered after the
+                         (pN+1)^dim grid nodes, x fastest (then y in 3D), and carry PFF_FLAG_COPY, so
+                         n_nodes = (pN+1)^dim + pN/2 (2D) or + (pN/2)(pN+1) (3D); in 2D the DoF counts are
+                         those of the paper's table of slit DoFs. Needs N even with N/2 a multiple of
+                         the tile height along the last axis (2D: 16 cells for p = 1, 8 for p = 2, 4 for
+                         p = 3, 4; 3D: 2 for p <= 3, 1 for p = 4), else INVALID_ARG. Coarse levels keep one
+                         node per grid point (the prolongation gives a copy its slit node's value, the
+                         restriction adds it back). The assembled-matrix comparator is not available. */
+  int fp32_tangent;   /* FP32 Jacobian applies in 2D (the FP32 multigrid): 0 (default) read stored
+                         per-point values (precomputed in FP64 and rounded); 1 recompute the tangent of
+                         Eq. (G) at every Gauss point from the nodal state (u, phi, phi~), which the apply
+                         reads instead: the method's minimum of DRAM traffic, but more arithmetic (slower
+                         on GB300 at 2D Q2). Nodal material fields and 3D always use stored values. */
 } pff_params;
 
 typedef struct {
@@ -133,7 +150,9 @@ int pff_node_flags(pff_ctx* ctx, int level, unsigned char* flags);
  *   phi_old  previous load step's phase field, one per node (required): bound phi <= phi_old;
  *   phi_tilde extrapolated phase field used in g(phi~) of the u-equation (NULL: phi_old);
  *   active   one byte per node, nonzero = phase-field DoF in the active set A (NULL: the set is
- *            computed by the rule of Alg. 1 from the residual at U and phi is reset to phi_old on it);
+ *            computed by the rule of Alg. 1 from the residual at U and phi is reset to phi_old on it;
+ *            that is the first step of Alg. 1, so the next pff_solve_newton_step goes on from it
+ *            instead of determining the set again);
  *   gc_field, lambda_field, mu_field: nodal material fields (NULL: the constants of the params).
  * Copies every input. Computes the per-quadrature-point tangent data of the finest level in FP64
  * (and FP32 when mg_precision is 32). Multigrid level data are built lazily by the first
@@ -281,7 +300,8 @@ int pff_param_grad_noalloc(pff_ctx* ctx, const double* v, double* g_gc, double* 
  * matrix-free operator with coloured probe vectors (two nodes of one colour never share a row).
  * The matrix is a snapshot of the state: later state changes do not update it; assembling again
  * replaces it. *nnz (host, may be NULL) receives the number of entries. Synchronous.
- * Errors: NO_STATE, TOO_LARGE (n_dofs + 1 or nnz above 2^31 - 1), OOM, CUDA. */
+ * Errors: INVALID_ARG (a context with a cut slit), NO_STATE, TOO_LARGE (n_dofs + 1 or nnz above
+ * 2^31 - 1), OOM, CUDA. */
 int pff_csr_assemble(pff_ctx* ctx, long long* nnz);
 
 /* y = A x with the assembled matrix, by cuSPARSE SpMV (FP64, default algorithm; the library is

@@ -9,9 +9,9 @@ template <int P, int SPLIT>
 static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* flags, const Geom& g, const Tab<df64>& tb,
                              const df64* qp, int mode, int inmask, int outmask, cudaStream_t s,
                              const ChebEpi<double>& ce) {
-  constexpr size_t smem = jac2_staged_smem<P, df64, double, SPLIT>();
+  constexpr size_t smem = jac2_staged_smem<P, df64, double, SPLIT, 0>();
   static int grid_per_sm = 0;
-  auto kern = k_jac2_staged<P, df64, double, SPLIT>;
+  auto kern = k_jac2_staged<P, df64, double, SPLIT, 0>;
   if (!grid_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -29,7 +29,7 @@ static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* 
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce);
+  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, MatConst32{});
   return cudaSuccess;
 }
 

@@ -62,8 +62,8 @@ cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, co
 }
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s, const ChebEpi<float>* ce) {
-  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce)
+                       cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc) {
+  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, rc)
                   : launch_jac_d3(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s);
 }
 

@@ -129,6 +129,7 @@ struct LevelData {
   double* sp64 = nullptr;   // finest level, Miehe split: sigma+ (Mandel) and E_s+ per point of the current u
   double* d64 = nullptr;    // diagonal of diag(G_uu, G_phiphi), masked rows 1
   double* di64 = nullptr;   // its inverse (Jacobi scaling)
+  float* s32 = nullptr;     // 2D: the state (u_x, u_y, phi, phi~) in FP32, read by the recomputed FP32 Jacobian
   float* d32 = nullptr;     // the diagonal computed in FP32 from the FP32 per-point data (FP32 multigrid)
   float* di32 = nullptr;
   double* lam = nullptr;    // device [lmax_u, lmax_phi, lower bounds]
@@ -200,6 +201,7 @@ struct pff_ctx {
   long long prof_n = 0;
   bool capturing = false;
   bool use_graph = true;
+  bool fresh_active = false;  // the active set was just computed from the current U (set_state, active = NULL)
   int device = -1;  // the device of the context's stream, recorded at setup
   // kernel-family timing (pff_profile)
   int prof = 0;
@@ -209,6 +211,10 @@ struct pff_ctx {
 
 // The coarse solve runs in FP32 only when the FP32 multigrid asks for it (coarse_precision 32).
 inline bool coarse32(const pff_ctx* c) { return c->prm.mg_precision == 32 && c->prm.coarse_precision == 32; }
+// With fp32_tangent = 1 the FP32 Jacobian of a 2D level is recomputed at the Gauss points from the nodal
+// state (rather than read from the stored per-point data), unless nodal material fields are set (the
+// recomputation takes constant lambda, mu, G_c).
+inline bool use_rc32(const pff_ctx* c) { return c->dim == 2 && c->prm.fp32_tangent == 1 && !c->has_fields; }
 
 namespace {
 
@@ -255,15 +261,20 @@ int dalloc(pff_ctx* c, T** p, long long n, int tag = TAG_OTHER) {
     if (r_ != PFF_OK) return r_; \
   } while (0)
 
-void make_geom(LevelData& L, int dim, int p) {
+void make_geom(LevelData& L, int dim, int p, bool cut) {
   Geom& g = L.g;
   g.dim = dim;
   g.p = p;
   g.N = L.N;
   g.n1 = p * L.N + 1;
   g.nn = L.nn;
+  g.ngrid = dim == 2 ? (long long)g.n1 * g.n1 : (long long)g.n1 * g.n1 * g.n1;
   int t[3];
   tile_shape(dim, p, t);
+  g.cut = cut ? 1 : 0;
+  g.cut_row = p * L.N / 2;
+  g.cut_x = p * L.N / 2;
+  g.cut_tile = cut ? (L.N / 2) / t[dim - 1] - 1 : -1;
   for (int i = 0; i < 3; ++i) {
     g.tdim[i] = t[i];
     g.ntile[i] = (i < dim) ? (L.N + t[i] - 1) / t[i] : 1;
@@ -335,7 +346,14 @@ void make_xfer(XferTab& xt, int p) {
 }
 
 // Node flags of a level (tension test: Dirichlet faces, slit), computed on the host.
-std::vector<unsigned char> host_flags(int dim, int p, int N) {
+// Number of copied slit nodes of a mesh with the slit cut into it: x index < p N / 2 on the slit, every y
+// index in 3D.
+long long cut_copies(int dim, int p, int N) {
+  const long long n1 = (long long)p * N + 1;
+  return (long long)(p * N / 2) * (dim == 2 ? 1 : n1);
+}
+
+std::vector<unsigned char> host_flags(int dim, int p, int N, bool cut) {
   const int n1 = p * N + 1;
   double xn[MAXN];
   gll_nodes(p, xn);
@@ -366,6 +384,15 @@ std::vector<unsigned char> host_flags(int dim, int p, int N) {
       for (int c = 0; c < dim; ++c) f |= (unsigned char)(1u << c);
     if (std::fabs(x1[vert] - 0.5) <= 1e-12 && x1[ijk[0]] <= 0.5 + 1e-12) f |= PFF_FLAG_SLIT;
     fl[i] = f;
+  }
+  if (cut) {  // copies of the slit nodes (x index < p N / 2), x fastest, then y (3D)
+    const int half = p * N / 2;
+    const long long ny = dim == 2 ? 1 : n1;
+    for (long long y = 0; y < ny; ++y)
+      for (int x = 0; x < half; ++x) {
+        const long long gnode = x + n1 * (dim == 2 ? (long long)half : y + n1 * half);
+        fl.push_back((unsigned char)(fl[gnode] | PFF_FLAG_COPY));
+      }
   }
   return fl;
 }
@@ -454,11 +481,26 @@ int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask,
     else
       CK(launch_jac_df3(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
                         L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s));
+  } else if (sizeof(Real) == 4 && L.s32 && use_rc32(c)) {
+    const float ke = (float)c->prm.kappa;
+    const Rc32 rc{L.s32, MatConst32{(float)c->prm.lambda, (float)c->prm.mu, (float)(c->prm.gc * c->prm.eps),
+                                    (float)(c->prm.gc / c->prm.eps), 1.0f - ke, ke}};
+    CK(launch_jac(c->dim, c->p, c->prm.split, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
+                  L.flags, L.g, L.t32, L.qp32, mode, inmask, outmask, c->s,
+                  reinterpret_cast<const ChebEpi<float>*>(ce), &rc));
   } else {
     CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
                   outmask, c->s, ce));
   }
   if (timed) CR(prof_mark(c));
+  return PFF_OK;
+}
+
+// FP32 copy of a level's state for the recomputed FP32 Jacobian: U (u_x, u_y, phi) and phi~ are
+// contiguous, so one cast covers the four fields.
+int state32_level(pff_ctx* c, int l) {
+  LevelData& L = c->lv[l];
+  if (L.s32) CK(launch_cast<double, float>((c->dim + 2) * L.nn, L.U, L.s32, c->s));
   return PFF_OK;
 }
 
@@ -469,7 +511,7 @@ int qp_setup_level(pff_ctx* c, int l) {
   CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
                      c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
                      L.qp64, L.qp32, L.qpdf, L.st64, c->s));
-  return PFF_OK;
+  return state32_level(c, l);
 }
 
 int ensure_st(pff_ctx* c);
@@ -502,6 +544,7 @@ int ensure_qp(pff_ctx* c) {
     CK(launch_qp_setup(c->dim, c->p, c->prm.split, L.U, L.phit, c->has_fields ? F : nullptr,
                        c->has_fields ? F + L.nn : nullptr, c->has_fields ? F + 2 * L.nn : nullptr, L.g, L.t64, mc,
                        L.qp64, L.qp32, L.qpdf, nullptr, c->s, L.sp64, QP_PHASE));
+    CR(state32_level(c, 0));
   } else {
     CR(qp_setup_level(c, 0));
     c->st_valid = true;
@@ -1039,6 +1082,8 @@ void pff_default_params(pff_params* p) {
   p->as_c = 1.0;
   p->mg_precision = 32;
   p->coarse_precision = 64;
+  p->slit_cut = 0;
+  p->fp32_tangent = 0;
   p->cheb_degree = 5;
   p->cheb_lo = 0.24;
   p->cheb_hi = 1.2;
@@ -1105,9 +1150,10 @@ static int setup_impl(pff_ctx* c) {
     L.N = sizes[l];
     L.h = 1.0 / L.N;
     long long n1 = (long long)c->p * L.N + 1;
-    L.nn = c->dim == 2 ? n1 * n1 : n1 * n1 * n1;
+    const bool cut = l == 0 && c->prm.slit_cut;  // coarse levels keep one node per grid point
+    L.nn = (c->dim == 2 ? n1 * n1 : n1 * n1 * n1) + (cut ? cut_copies(c->dim, c->p, L.N) : 0);
     L.nd = (c->dim + 1) * L.nn;
-    make_geom(L, c->dim, c->p);
+    make_geom(L, c->dim, c->p, cut);
     make_tabs(L, c->dim, c->p);
     const int nv = qp_nv(c->dim, P.split);
     CR(dalloc(c, &L.flags, L.nn, l));
@@ -1130,6 +1176,7 @@ static int setup_impl(pff_ctx* c) {
         CK(cudaMemsetAsync(L.sp64, 0, sizeof(double) * (nm + 1) * nqp, c->s));
       }
     }
+    if (c->dim == 2) CR(dalloc(c, &L.s32, (c->dim + 2) * L.nn, l));
     CR(dalloc(c, &L.d64, L.nd, l));
     CR(dalloc(c, &L.di64, L.nd, l));
     CR(dalloc(c, &L.d32, L.nd, l));
@@ -1140,7 +1187,7 @@ static int setup_impl(pff_ctx* c) {
     CR(dalloc(c, &L.lpart, 2 * 152 * 2, l));
     CK(cudaStreamCreateWithFlags(&L.aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
-    std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N);
+    std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N, cut);
     CK(cudaMemcpyAsync(L.flags, fl.data(), fl.size(), cudaMemcpyHostToDevice, c->s));
     CK(cudaStreamSynchronize(c->s));
   }
@@ -1191,10 +1238,34 @@ static int setup_impl(pff_ctx* c) {
     std::vector<double> w1(n1, 0.0);
     for (int cc = 0; cc < F.N; ++cc)
       for (int k = 0; k <= c->p; ++k) w1[cc * c->p + k] += wg[k] * F.h;
-    double* dw1;
-    CR(dalloc(c, &dw1, n1));
-    CK(cudaMemcpyAsync(dw1, w1.data(), sizeof(double) * n1, cudaMemcpyHostToDevice, c->s));
-    CK(launch_lumped_mass(c->dim, F.nn, n1, dw1, c->mass, c->s));
+    if (!F.g.cut) {
+      double* dw1;
+      CR(dalloc(c, &dw1, n1));
+      CK(cudaMemcpyAsync(dw1, w1.data(), sizeof(double) * n1, cudaMemcpyHostToDevice, c->s));
+      CK(launch_lumped_mass(c->dim, F.nn, n1, dw1, c->mass, c->s));
+    } else {
+      // cut slit: the slit's grid nodes see only the cells above it, their copies only those below;
+      // GLL weights are symmetric, so each side carries half the tensor-product weight
+      std::vector<double> m(F.nn);
+      const long long ng = F.g.ngrid;
+      for (long long i = 0; i < ng; ++i) {
+        long long rem = i;
+        double v = 1.0;
+        int ijk[3] = {0, 0, 0};
+        for (int t = 0; t < c->dim; ++t) {
+          ijk[t] = int(rem % n1);
+          v *= w1[ijk[t]];
+          rem /= n1;
+        }
+        if (ijk[c->dim - 1] == F.g.cut_row && ijk[0] < F.g.cut_x) v *= 0.5;
+        m[i] = v;
+      }
+      const long long ny = c->dim == 2 ? 1 : n1;
+      for (long long y = 0; y < ny; ++y)
+        for (int x = 0; x < F.g.cut_x; ++x)
+          m[cut_copy(F.g, x, (int)y)] = m[x + (long long)n1 * (c->dim == 2 ? F.g.cut_row : y + (long long)n1 * F.g.cut_row)];
+      CK(cudaMemcpyAsync(c->mass, m.data(), sizeof(double) * F.nn, cudaMemcpyHostToDevice, c->s));
+    }
     CK(cudaStreamSynchronize(c->s));
   }
   return PFF_OK;
@@ -1208,8 +1279,14 @@ int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream) {
       !valid_prec(p->mg_precision) || p->cheb_degree < 1 || !(p->cheb_hi > p->cheb_lo) || !(p->cheb_lo > 0) ||
       p->eig_iters < 1 || p->eig_iters > 64 || p->gmres_restart < 1 || p->gmres_max_iters < 1 ||
       !(p->lin_rtol > 0) || !(p->eps > 0) || (p->fp64_mode != 0 && p->fp64_mode != 1) ||
-      !valid_prec(p->coarse_precision))
+      !valid_prec(p->coarse_precision) || (p->slit_cut != 0 && p->slit_cut != 1) ||
+      (p->fp32_tangent != 0 && p->fp32_tangent != 1))
     return PFF_ERR_INVALID_ARG;
+  if (p->slit_cut) {  // the slit must lie on a boundary between tile rows of the finest mesh
+    int t[3];
+    tile_shape(p->dim, p->degree, t);
+    if (p->n_cells_1d % 2 || (p->n_cells_1d / 2) % t[p->dim - 1]) return PFF_ERR_INVALID_ARG;
+  }
   pff_ctx* c = new (std::nothrow) pff_ctx();
   if (!c) return PFF_ERR_OOM;
   c->prm = *p;
@@ -1280,17 +1357,18 @@ int pff_set_state(pff_ctx* c, const double* U, const double* phi_old, const doub
   c->strain_valid = false;
   c->mg_ready = false;
   c->nhist = 0;
+  c->fresh_active = false;
   if (active) {
     CK(launch_set_active(c->dim, L.nn, active, L.flags, c->s));
   } else {
-    std::vector<unsigned char> none(L.nn, 0);
     unsigned char* dz = reinterpret_cast<unsigned char*>(c->scratch);
-    CK(cudaMemcpyAsync(dz, none.data(), L.nn, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemsetAsync(dz, 0, L.nn, c->s));
     CK(launch_set_active(c->dim, L.nn, dz, L.flags, c->s));
-    CK(cudaStreamSynchronize(c->s));
     CR(residual_into(c, c->R));
     CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
     c->qp_valid = false;
+    // this is the first step of Alg. 1 at U: the next Newton step starts from it
+    c->fresh_active = true;
   }
   return PFF_OK;
 }
@@ -1378,7 +1456,7 @@ int pff_csr_probe_targets(int dim, int degree, int n_cells_1d, int f, int color,
 
 int pff_csr_assemble(pff_ctx* c, long long* nnz) {
   Range nvtx_range("pff_csr_assemble");
-  if (!c) return PFF_ERR_INVALID_ARG;
+  if (!c || c->prm.slit_cut) return PFF_ERR_INVALID_ARG;  // its pattern assumes one node per grid point
   if (!c->has_state) return PFF_ERR_NO_STATE;
   CR(ensure_qp(c));
   LevelData& L = c->lv[0];
@@ -1587,9 +1665,13 @@ int pff_solve_newton_step(pff_ctx* c, double* U_out, pff_report* rep) {
   const auto t0 = clk::now();
   Phases phase;
   phase.next("residual and active set");
-  // Alg. 1: residual, active set (phi reset to phi_old on it), residual of the projected state
-  CR(residual_into(c, c->R));
-  CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
+  // Alg. 1: residual, active set (phi reset to phi_old on it), residual of the projected state. After
+  // pff_set_state with active = NULL the active set of this U is already there.
+  if (!c->fresh_active) {
+    CR(residual_into(c, c->R));
+    CK(launch_active_set(c->dim, L.nn, c->R, c->mass, c->phi_old, c->prm.as_c, L.U, L.flags, c->cnt, c->s));
+  }
+  c->fresh_active = false;
   c->qp_valid = false;
   c->mg_ready = false;
   CR(residual_into(c, c->R));
@@ -1666,6 +1748,7 @@ int pff_solve_load_step(pff_ctx* c, double load, int max_iters, double newton_rt
     CK(cudaMemcpyAsync(c->hist1, L.U + c->dim * nn, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->s));
   CK(launch_load_step_prep(load_comp(c), nn, L.flags, load, L.U, c->hist1, c->nhist >= 2 ? c->hist2 : nullptr,
                            L.phit, c->phi_old, c->s));
+  c->fresh_active = false;  // the load and phi_old changed
   c->qp_valid = false;
   c->st_valid = false;
   c->strain_valid = false;

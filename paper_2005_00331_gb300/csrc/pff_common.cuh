@@ -73,13 +73,40 @@ inline void tile_shape(int dim, int p, int* t) {
 // Geometry of one level as the kernels see it.
 struct Geom {
   int dim, p, N, n1;
-  long long nn;            // nodes
+  long long nn;            // nodes (grid nodes and, with a cut slit, their copies)
   int tdim[3];             // cells per tile in x, y, z
   int ntile[3];            // tiles per direction
   int qpx, qpy, qpz;       // quadrature points of a tile per direction
   long long qpt;           // quadrature points per tile
   long long ntiles;
+  // Slit cut into the mesh (Sec. 5.1): the nodes on the slit (last coordinate 1/2, x < 1/2; the tip
+  // stays shared) get a second copy, numbered after the grid nodes, which the cells below the slit use.
+  // The slit lies on a boundary between tile rows (tiles along the last axis).
+  int cut;                 // 1: slit cut into the mesh, 0: one node per grid point
+  int cut_row;             // grid index of the slit along the last axis (p N / 2)
+  int cut_x;               // copied slit nodes have x index < cut_x (= p N / 2)
+  int cut_tile;            // tile index along the last axis of the tiles just below the slit
+  long long ngrid;         // grid nodes
 };
+
+// Material constants of the recomputed FP32 Jacobian (pw_jac_rc2).
+struct MatConst32 {
+  float lam, mu, gc_eps, gc_over_eps, omk, kappa;  // omk = 1 - kappa
+};
+
+// Copy of slit node (gx, gy) (gy: y index in 3D, 0 in 2D), numbered x fastest after the grid nodes.
+__host__ __device__ __forceinline__ long long cut_copy(const Geom& g, int gx, int gy) {
+  return g.ngrid + gx + (long long)g.cut_x * gy;
+}
+// Whether patch layer rl (along the last axis, npl layers) of tile layer tl at x index gx is the slit
+// seen from below (those nodes are the copies) or from above (the grid nodes, not shared with the tiles
+// below).
+__host__ __device__ __forceinline__ bool cut_below(const Geom& g, int tl, int rl, int npl, int gx) {
+  return g.cut && tl == g.cut_tile && rl == npl - 1 && gx < g.cut_x;
+}
+__host__ __device__ __forceinline__ bool cut_above(const Geom& g, int tl, int rl, int gx) {
+  return g.cut && tl == g.cut_tile + 1 && rl == 0 && gx < g.cut_x;
+}
 
 // Chebyshev-Jacobi step fused into the block-diagonal apply (Sec. 3.3 smoother): for a node that
 // only this tile touches, y = (G x)_i is final in registers, so the update

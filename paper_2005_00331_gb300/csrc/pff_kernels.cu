@@ -156,6 +156,11 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
   const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (nd >= gf.nn) return;
   long long rem = nd;
+  if (nd >= gf.ngrid) {  // copy of a cut slit node: the coarse function's value at its grid point
+    const long long k = nd - gf.ngrid;
+    const long long x = k % gf.cut_x, y = k / gf.cut_x;
+    rem = x + (long long)gf.n1 * (DIM == 2 ? gf.cut_row : y + (long long)gf.n1 * gf.cut_row);
+  }
   int C[3] = {0, 0, 0}, o[3] = {0, 0, 0};
 #pragma unroll
   for (int t = 0; t < DIM; ++t) {
@@ -254,6 +259,14 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
 #pragma unroll
         for (int f = 0; f <= DIM; ++f)
           if (!((ff >> f) & 1u)) acc[f] += w * xf[f * gf.nn + fn];
+        if (gf.cut && (DIM == 2 ? iy : iz) == gf.cut_row && ix < gf.cut_x) {
+          // a cut slit node: its copy sees the same coarse functions (restriction = transpose)
+          const long long fc = cut_copy(gf, ix, DIM == 3 ? iy : 0);
+          const unsigned char fcm = mask_fine ? flf[fc] : 0;
+#pragma unroll
+          for (int f = 0; f <= DIM; ++f)
+            if (!((fcm >> f) & 1u)) acc[f] += w * xf[f * gf.nn + fc];
+        }
       }
     }
   }

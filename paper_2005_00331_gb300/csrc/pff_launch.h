@@ -41,9 +41,15 @@ inline cudaError_t launch_k(void (*k)(KP...), dim3 grid, dim3 block, size_t smem
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask,
                        int outmask, cudaStream_t s, const ChebEpi<double>* ce = nullptr);
+// FP32 Jacobian recomputed at the points from the nodal state (2D; see pw_jac_rc2): state = u_x, u_y,
+// phi, phi~ as 4 blocks of g.nn floats, mc the material constants. Passed as `rc`, it replaces qp.
+struct Rc32 {
+  const float* state;
+  MatConst32 mc;
+};
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s, const ChebEpi<float>* ce = nullptr);
+                       cudaStream_t s, const ChebEpi<float>* ce = nullptr, const Rc32* rc = nullptr);
 template <typename Store>
 cudaError_t launch_cheb_seam(const Geom& g, Store* y, const ChebEpi<Store>& ce, cudaStream_t s);
 cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
@@ -51,7 +57,7 @@ cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y,
                           cudaStream_t s, const ChebEpi<double>* ce);
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                           const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s, const ChebEpi<float>* ce);
+                          cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc = nullptr);
 cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
                           cudaStream_t s);

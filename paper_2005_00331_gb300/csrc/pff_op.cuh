@@ -101,6 +101,85 @@ struct PWJac {
 };
 
 // -------------------------------------------------------------------------------------------
+// Pointwise Jacobian of Eq. (G) in FP32, 2D, recomputed at the point from the nodal state instead of
+// read from stored per-point data: st = (d u_x/dx, d u_x/dy, d u_y/dx, d u_y/dy, phi, phi~) at the
+// point. With the eigenvalues l1 >= l2 of e = e(u) and the eigenvector angle t, R = v1 v1^T - v2 v2^T
+// = [[cos 2t, sin 2t], [sin 2t, -cos 2t]] and J = v1 v2^T + v2 v1^T = [[-sin 2t, cos 2t], [cos 2t,
+// sin 2t]]; a strain direction is e(du) = a I + b R + c J (a = tr/2, b = e(du):R/2, c = e(du):J/2) and
+// the derivative of e+ (Alg. 2 in its divided-difference form) is diagonal in that basis:
+//   de+[e(du)] = (H1 + H2)/2 (a I + b R) + (H1 - H2)/2 (b I + a R) + theta c J,
+// theta = (l1+ - l2+)/(l1 - l2), H(l1) when l1 = l2. Then tau = lambda (g H(tr) + 1 - H(tr)) tr(e(du)) I
+// + 2 mu (e(du) + (g(phi~) - 1) de+[e(du)]), the coupling g'(phi) sigma+ : e(du) with sigma+ =
+// lambda <tr>+ I + 2 mu e+, and c = g'' E_s+ + G_c/eps, k = G_c eps, all times JxW. Eigenvalues and the
+// trace within 1e-6 of the largest eigenvalue magnitude count as 0 (their sign is FP32 rounding).
+// Split none: tau = g(phi~) (lambda tr(e(du)) I + 2 mu e(du)), sigma+ = sigma, E_s+ = E_s.
+template <int SPLIT>
+__device__ __forceinline__ void pw_jac_rc2(const float st[6], float jxw, const MatConst32& mc, int mode,
+                                           const QPIn<2, float>& in, QPOut<2, float>& out) {
+  const float exx = st[0], eyy = st[3], exy = 0.5f * (st[1] + st[2]);
+  const float g = fmaf(mc.omk * st[5], st[5], mc.kappa), dg = 2.0f * mc.omk * st[4], ddg = 2.0f * mc.omk;
+  const float dxx = in.gu[0][0], dyy = in.gu[1][1], dxy = 0.5f * (in.gu[0][1] + in.gu[1][0]);
+  const float dtr = dxx + dyy;
+  float txx, tyy, txy, sxx, syy, sxy, Esp;
+  if constexpr (SPLIT == 0) {
+    const float tr = exx + eyy;
+    txx = g * fmaf(mc.lam, dtr, 2.0f * mc.mu * dxx);
+    tyy = g * fmaf(mc.lam, dtr, 2.0f * mc.mu * dyy);
+    txy = g * 2.0f * mc.mu * dxy;
+    sxx = fmaf(mc.lam, tr, 2.0f * mc.mu * exx);
+    syy = fmaf(mc.lam, tr, 2.0f * mc.mu * eyy);
+    sxy = 2.0f * mc.mu * exy;
+    Esp = 0.5f * mc.lam * tr * tr + mc.mu * (exx * exx + eyy * eyy + 2.0f * exy * exy);
+  } else {
+    float tr = exx + eyy;
+    // half the eigenvalue gap r and its reciprocal from one rsqrt (no division): l1 - l2 = 2 r
+    const float dd = 0.5f * (exx - eyy), r2 = fmaf(dd, dd, exy * exy);
+    const float ir = r2 > 0.0f ? rsqrtf(r2) : 0.0f, r = r2 * ir;
+    float l1 = 0.5f * tr + r, l2 = 0.5f * tr - r;
+    const float tol = 1e-6f * fmaxf(fabsf(l1), fabsf(l2));
+    if (fabsf(l1) <= tol) l1 = 0.0f;
+    if (fabsf(l2) <= tol) l2 = 0.0f;
+    if (fabsf(tr) <= tol) tr = 0.0f;
+    const float c2 = r2 > 0.0f ? dd * ir : 1.0f, s2 = exy * ir;
+    const float H1 = l1 >= 0.0f ? 1.0f : 0.0f, H2 = l2 >= 0.0f ? 1.0f : 0.0f, Ht = tr >= 0.0f ? 1.0f : 0.0f;
+    const float p1 = fmaxf(l1, 0.0f), p2 = fmaxf(l2, 0.0f), trp = fmaxf(tr, 0.0f);
+    // divided difference (p1 - p2) / (l1 - l2) with l1 - l2 = 2 r (a snapped eigenvalue moves it by at
+    // most the snapping tolerance); H(l1) when the snapped eigenvalues coincide
+    const float theta = l1 == l2 ? H1 : (p1 - p2) * (0.5f * ir);
+    const float dm = dxx - dyy;
+    const float a = 0.5f * dtr, b = 0.5f * fmaf(c2, dm, 2.0f * s2 * dxy), cj = 0.5f * fmaf(-s2, dm, 2.0f * c2 * dxy);
+    const float Hs = 0.5f * (H1 + H2), Hd = 0.5f * (H1 - H2);
+    const float A = fmaf(Hs, a, Hd * b), B = fmaf(Hd, a, Hs * b), T = theta * cj;
+    const float pxx = A + B * c2 - T * s2, pyy = A - B * c2 + T * s2, pxy = fmaf(B, s2, T * c2);
+    const float gm1 = g - 1.0f, m2 = 2.0f * mc.mu, lt = mc.lam * fmaf(g, Ht, 1.0f - Ht) * dtr;
+    txx = lt + m2 * fmaf(gm1, pxx, dxx);
+    tyy = lt + m2 * fmaf(gm1, pyy, dyy);
+    txy = m2 * fmaf(gm1, pxy, dxy);
+    const float Ep = 0.5f * (p1 + p2), Em = 0.5f * (p1 - p2), lp = mc.lam * trp;
+    sxx = lp + m2 * fmaf(Em, c2, Ep);
+    syy = lp + m2 * fmaf(-Em, c2, Ep);
+    sxy = m2 * Em * s2;
+    Esp = fmaf(0.5f * mc.lam * trp, trp, mc.mu * fmaf(p1, p1, p2 * p2));
+  }
+  const float cc = fmaf(ddg, Esp, mc.gc_over_eps) * jxw, kk = mc.gc_eps * jxw, dgj = dg * jxw;
+  out.cu[0][0] = txx * jxw;
+  out.cu[1][1] = tyy * jxw;
+  out.cu[0][1] = out.cu[1][0] = txy * jxw;
+  float cv = cc * in.ph;
+  if (mode == JM_FULL) {
+    cv = fmaf(dgj, fmaf(sxx, dxx, fmaf(syy, dyy, 2.0f * sxy * dxy)), cv);
+  } else if (mode == JM_TRANSPOSE) {
+    const float w = dgj * in.ph;
+    out.cu[0][0] = fmaf(w, sxx, out.cu[0][0]);
+    out.cu[1][1] = fmaf(w, syy, out.cu[1][1]);
+    out.cu[0][1] = out.cu[1][0] = fmaf(w, sxy, out.cu[0][1]);
+  }
+  out.cv = cv;
+  out.cg[0] = kk * in.gph[0];
+  out.cg[1] = kk * in.gph[1];
+}
+
+// -------------------------------------------------------------------------------------------
 // Pointwise residual of Eq. (residual) from the evaluated state (FP64):
 // u-test  g(phi~) sigma^+ + sigma^-,  phi-test  g'(phi) E_s^+ - (G_c/eps)(1 - phi),
 // grad-test G_c eps grad phi. Stored per point: g(phi~), G_c, lambda, mu.
@@ -261,7 +340,7 @@ k_op2d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned ch
       const int gx = x0 + s;
       Real v[NF] = {Real(0), Real(0), Real(0)};
       if (gx < g.n1 && gy < g.n1) {
-        const long long node = gx + (long long)g.n1 * gy;
+        const long long node = cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
         unsigned char m = 0;
         if (oa.inmask != IN_RAW) {
           m = flags[node];
@@ -386,9 +465,11 @@ k_op2d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned ch
           }
         }
       }
-      const long long node = gx + (long long)g.n1 * gy;
-      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0);
-      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1);
+      // a cut slit separates the tile rows above and below it: its nodes are shared only along x
+      const bool below = cut_below(g, tiy, r, NPY, gx);
+      const long long node = below ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
+      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1 && !below);
       unsigned char m = 0;
       if (oa.outmask != OUT_RAW) {
         m = flags[node];
@@ -460,50 +541,65 @@ __device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, 
     gy = int(u / g.n1 + 1) * tpy;
     gx = int(u % g.n1);
     if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
+    // a cut slit's nodes are shared along x only: the tiles finished them, except on vertical seams
+    if (g.cut && gy == g.cut_row && gx < g.cut_x) return;
   }
-  const long long node = gx + (long long)g.n1 * gy;
-  for (int f = 0; f < 3; ++f) {
-    const long long gi = f * g.nn + node;
-    const Store yv = y[gi];
-    const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - yv));
-    ce.d[gi] = dn;
-    if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
-    else ce.x[gi] = ce.x[gi] + dn;
-    y[gi] = Store(0);
+  const bool both = g.cut && gy == g.cut_row && gx < g.cut_x;  // a vertical seam crossing a cut slit
+  for (int k = 0; k < (both ? 2 : 1); ++k) {
+    const long long node = k ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+    for (int f = 0; f < 3; ++f) {
+      const long long gi = f * g.nn + node;
+      const Store yv = y[gi];
+      const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - yv));
+      ce.d[gi] = dn;
+      if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
+      else ce.x[gi] = ce.x[gi] + dn;
+      y[gi] = Store(0);
+    }
   }
 }
 
 // Register budget per thread that keeps the CTAs resident which fit in shared memory (FP32 Q2: five
-// per SM; double-word Q2: two): FP32 64 up to Q2 and 96 above (64 would spill there), double-word 80
-// for Q1 and 168 for Q2/Q3; native FP64 and double-word Q4 unconstrained.
-template <int P, typename Real>
+// per SM; double-word Q2 to Q4: two): FP32 64 up to Q2 and 96 above (64 would spill there), double-word
+// 80 for Q1 and 168 above (unconstrained, Q4 took 255 registers and ran one CTA of 5 warps per SM; at
+// 168 it spills 8 to 16 bytes); native FP64 unconstrained.
+// The recomputed FP32 tangent (RC) keeps the state's contractions live: 96 up to Q2 (80 spilled), 128 above.
+template <int P, typename Real, int RC = 0>
 constexpr int jac2_reg_budget() {
-  return std::is_same<Real, float>::value ? (P <= 2 ? 64 : 96)
-         : std::is_same<Real, df64>::value ? (P == 1 ? 80 : (P <= 3 ? 168 : 0))
+  return std::is_same<Real, float>::value ? (RC ? (P <= 2 ? 96 : 128) : (P <= 2 ? 64 : 96))
+         : std::is_same<Real, df64>::value ? (P == 1 ? 80 : 168)
                                            : 0;
 }
-template <int P, typename Real>
+template <int P, typename Real, int RC = 0>
 constexpr int jac2_min_blocks() {
-  return jac2_reg_budget<P, Real>() ? 65536 / (Tile2<P>::NT * jac2_reg_budget<P, Real>()) : 1;
+  return jac2_reg_budget<P, Real, RC>() ? 65536 / (Tile2<P>::NT * jac2_reg_budget<P, Real, RC>()) : 1;
 }
 
-template <int P, typename Real, typename Store, int SPLIT>
-__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real>())
+// RC = 1 (FP32 only): the pointwise Jacobian is recomputed from the nodal state (u_x, u_y, phi, phi~;
+// qpg then points to those 4 fields of n_nodes floats each) by pw_jac_rc2 instead of read from stored
+// per-point data: the tile stages 4 state values per node instead of NV values per Gauss point.
+template <int P, typename Real, typename Store, int SPLIT, int RC>
+__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real, RC>())
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
-              Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce) {
+              Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce,
+              MatConst32 mc) {
   pdl_wait();
   using T = Tile2<P>;
   constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
   constexpr int NPX = T::NPX, NPY = T::NPY, QPX = T::QPX;
   constexpr int QPT = T::QPX * T::QPY;
-  constexpr int NV = qp_nv(2, SPLIT);
+  constexpr int NV = RC ? 0 : qp_nv(2, SPLIT);
+  constexpr int NSF = RC ? 4 : 0;  // staged state fields
   constexpr int NS = Stage2<P, Real>::NSTAGE;
   constexpr int NT = T::NT;
   constexpr int XS = NF * NPY * NPX;
+  constexpr int NNODE = NPY * NPX, NIT = (NNODE + NT - 1) / NT;
+  static_assert(!RC || std::is_same<Real, float>::value, "the recomputed tangent is FP32 only");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* QPs = reinterpret_cast<Real*>(smem_raw);                  // [NS][NV][QPT]
   Store* Xs = reinterpret_cast<Store*>(QPs + NS * NV * QPT);      // [NS][NF][NPY][NPX] raw copies
-  Real* X = reinterpret_cast<Real*>(Xs + NS * XS);                // [NF][NPY][NPX] masked, compute type
+  Store* Ss = Xs + NS * XS;                                       // [NS][NSF][NPY][NPX] state (RC)
+  Real* X = reinterpret_cast<Real*>(Ss + NS * NSF * NNODE);       // [NF][NPY][NPX] masked, compute type
   Real* UB = X + XS;                                              // [NF][TY][n][QPX]
   Real* UD = UB + NF * TY * n * QPX;
   Real* sS = UD + NF * TY * n * QPX;
@@ -524,7 +620,6 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   }
   const long long ntiles = g.ntiles;
   // node phases (copy, masking, store): this thread handles patch nodes tid + k NT, all fields
-  constexpr int NNODE = NPY * NPX, NIT = (NNODE + NT - 1) / NT;
   auto prefetch = [&](long long tile, int st) {
     const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
     const int x0 = tix * TX * P, y0 = tiy * TY * P;
@@ -536,15 +631,25 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
       const bool ok = gx < g.n1 && gy < g.n1;
-      const Store* sp = src + (ok ? gx + (long long)g.n1 * gy : 0);
+      const long long node = cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const Store* sp = src + (ok ? node : 0);
       Store* dp = xs + rs;
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async_bytes(dp + f * NNODE, sp + (ok ? f * g.nn : 0), ok, (int)sizeof(Store));
+      if constexpr (RC != 0) {
+        const Store* stp = reinterpret_cast<const Store*>(qpg) + (ok ? node : 0);
+        Store* sdp = Ss + st * NSF * NNODE + rs;
+#pragma unroll
+        for (int f = 0; f < NSF; ++f)
+          cp_async_bytes(sdp + f * NNODE, stp + (ok ? f * g.nn : 0), ok, (int)sizeof(Store));
+      }
     }
-    const char* qsrc = reinterpret_cast<const char*>(qpg + tile * (long long)NV * QPT);
-    char* qdst = reinterpret_cast<char*>(QPs + st * NV * QPT);
-    constexpr int NCH = NV * QPT * (int)sizeof(Real) / 16;
-    for (int i = tid; i < NCH; i += NT) cp_async16(qdst + 16 * i, qsrc + 16 * i);
+    if constexpr (RC == 0) {
+      const char* qsrc = reinterpret_cast<const char*>(qpg + tile * (long long)NV * QPT);
+      char* qdst = reinterpret_cast<char*>(QPs + st * NV * QPT);
+      constexpr int NCH = NV * QPT * (int)sizeof(Real) / 16;
+      for (int i = tid; i < NCH; i += NT) cp_async16(qdst + 16 * i, qsrc + 16 * i);
+    }
   };
 
   int it = 0;
@@ -573,7 +678,7 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       const int gx = x0 + s, gy = y0 + r;
       unsigned char m = 0;
       if (oa.inmask != IN_RAW && gx < g.n1 && gy < g.n1) {
-        m = flags[gx + (long long)g.n1 * gy];
+        m = flags[cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy];
         if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
       }
 #pragma unroll
@@ -614,6 +719,25 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         ub[f][l] = Real(0);
         ud[f][l] = Real(0);
       }
+    // RC: x-contractions of the nodal state (u_x, u_y with their x-derivatives, phi and phi~)
+    Real sb[RC ? 4 : 1][n], sd[RC ? 2 : 1][n];
+    if constexpr (RC != 0) {
+      const Store* ss = Ss + st * NSF * NNODE;
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          const Store* row = ss + (f * NPY + ty * P + l) * NPX + cx * P;
+          Real b = Sq[0] * row[0], d = Dq[0] * row[0];
+#pragma unroll
+          for (int k = 1; k < n; ++k) {
+            b = fmac(Sq[k], row[k], b);
+            if (f < 2) d = fmac(Dq[k], row[k], d);
+          }
+          sb[f][l] = b;
+          if (f < 2) sd[f][l] = d;
+        }
+    }
     if (inside) {
       PWJac<2, Real, SPLIT> pw;
       pw.qp = QPs + st * NV * QPT;
@@ -653,7 +777,27 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
           in.gph[1] = gy;
         }
         QPOut<2, Real> o;
-        pw(0, (long long)(ty * n + qj) * QPX + tx, in, o);
+        if constexpr (RC != 0) {
+          float pst[6];
+          pst[0] = sj[0] * sd[0][0];
+          pst[1] = dj[0] * sb[0][0];
+          pst[2] = sj[0] * sd[1][0];
+          pst[3] = dj[0] * sb[1][0];
+          pst[4] = sj[0] * sb[2][0];
+          pst[5] = sj[0] * sb[3][0];
+#pragma unroll
+          for (int l = 1; l < n; ++l) {
+            pst[0] = fmac(sj[l], sd[0][l], pst[0]);
+            pst[1] = fmac(dj[l], sb[0][l], pst[1]);
+            pst[2] = fmac(sj[l], sd[1][l], pst[2]);
+            pst[3] = fmac(dj[l], sb[1][l], pst[3]);
+            pst[4] = fmac(sj[l], sb[2][l], pst[4]);
+            pst[5] = fmac(sj[l], sb[3][l], pst[5]);
+          }
+          pw_jac_rc2<SPLIT>(pst, tb.hd * tb.W[qi] * tb.W[qj], mc, mode, in, o);
+        } else {
+          pw(0, (long long)(ty * n + qj) * QPX + tx, in, o);
+        }
 #pragma unroll
         for (int l = 0; l < n; ++l) {
 #pragma unroll
@@ -705,9 +849,10 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
           }
         }
       }
-      const long long node = gx + (long long)g.n1 * gy;
-      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0);
-      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1);
+      const bool below = cut_below(g, tiy, r, NPY, gx);
+      const long long node = below ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
+      const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1 && !below);
       unsigned char m = 0;
       if (oa.outmask != OUT_RAW) {
         m = flags[node];
@@ -747,12 +892,13 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, Ch
   cheb_seam_node<Store>(g, tpx, tpy, y, ce, t, Store(ce.c1), c2);
 }
 
-template <int P, typename Real, typename Store, int SPLIT>
+template <int P, typename Real, typename Store, int SPLIT, int RC = 0>
 constexpr size_t jac2_staged_smem() {
   using T = Tile2<P>;
   constexpr int NS = Stage2<P, Real>::NSTAGE;
   constexpr int XS = 3 * T::NPY * T::NPX;
-  return sizeof(Real) * (size_t)NS * qp_nv(2, SPLIT) * T::QPX * T::QPY + sizeof(Store) * (size_t)NS * XS +
+  constexpr int NV = RC ? 0 : qp_nv(2, SPLIT), NSF = RC ? 4 : 0;
+  return sizeof(Real) * (size_t)NS * NV * T::QPX * T::QPY + sizeof(Store) * (size_t)NS * (XS + NSF * T::NPY * T::NPX) +
          sizeof(Real) * (size_t)(XS + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
 }
 
@@ -809,7 +955,7 @@ k_op3d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned ch
         const int gx = x0 + s, gy = y0 + r, gz = z0 + t;
         Real v[NF] = {Real(0), Real(0), Real(0), Real(0)};
         if (gx < g.n1 && gy < g.n1 && gz < g.n1) {
-          const long long node = gx + n1 * gy + n1sq * gz;
+          const long long node = cut_below(g, tiz, t, NPZ, gx) ? cut_copy(g, gx, gy) : gx + n1 * gy + n1sq * gz;
           unsigned char m = 0;
           if (oa.inmask != IN_RAW) {
             m = flags[node];
@@ -996,10 +1142,11 @@ k_op3d(const Store* __restrict__ src, Store* __restrict__ dst, const unsigned ch
             }
           }
         }
-        const long long node = gx + n1 * gy + n1sq * gz;
-        const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0) || (t == 0 && tiz > 0);
+        const bool below = cut_below(g, tiz, t, NPZ, gx);
+        const long long node = below ? cut_copy(g, gx, gy) : gx + n1 * gy + n1sq * gz;
+        const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0) || (t == 0 && tiz > 0 && !cut_above(g, tiz, t, gx));
         const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1) ||
-                          (t == NPZ - 1 && tiz < g.ntile[2] - 1);
+                          (t == NPZ - 1 && tiz < g.ntile[2] - 1 && !below);
         unsigned char m = 0;
         if (oa.outmask != OUT_RAW) {
           m = flags[node];

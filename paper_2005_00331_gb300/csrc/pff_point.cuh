@@ -42,7 +42,12 @@ struct CellQP {
   __device__ long long node(int a, const Geom& g) const {
     constexpr int n = P + 1;
     const int ax = a % n, ay = (a / n) % n, az = DIM == 3 ? a / (n * n) : 0;
-    long long nd = (c[0] * P + ax) + (long long)g.n1 * (c[1] * P + ay);
+    const int gx = c[0] * P + ax;
+    // a cell just below a cut slit uses the copies of the slit's nodes (its top face, x < 1/2)
+    if (g.cut && (DIM == 2 ? (c[1] * P + ay == g.cut_row && ay == P) : (c[2] * P + az == g.cut_row && az == P)) &&
+        gx < g.cut_x)
+      return cut_copy(g, gx, DIM == 3 ? c[1] * P + ay : 0);
+    long long nd = gx + (long long)g.n1 * (c[1] * P + ay);
     if (DIM == 3) nd += (long long)g.n1 * g.n1 * (c[2] * P + az);
     return nd;
   }

@@ -13,7 +13,7 @@ from . import build as _build
 PFF_SPLIT_NONE, PFF_SPLIT_MIEHE = 0, 1
 PFF_MODE_FULL, PFF_MODE_BLOCKDIAG, PFF_MODE_TRANSPOSE = 0, 1, 2
 PFF_MASK_RAW, PFF_MASK_ADJOINT = 4, 8
-PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT = 0x10, 0x20, 0x40
+PFF_FLAG_TOP, PFF_FLAG_BOTTOM, PFF_FLAG_SLIT, PFF_FLAG_COPY = 0x10, 0x20, 0x40, 0x80
 PFF_PROF_OFF, PFF_PROF_JAC64_L0, PFF_PROF_JAC32_L0, PFF_PROF_JAC64, PFF_PROF_JAC32, PFF_PROF_RESIDUAL = range(6)
 
 PFF_OK = 0
@@ -36,7 +36,8 @@ class Params(ctypes.Structure):
                 ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double), ("eig_iters", ctypes.c_int),
                 ("eig_seed", ctypes.c_ulonglong), ("gmres_restart", ctypes.c_int),
                 ("gmres_max_iters", ctypes.c_int), ("lin_rtol", ctypes.c_double), ("fp64_mode", ctypes.c_int),
-                ("coarse_precision", ctypes.c_int)]
+                ("coarse_precision", ctypes.c_int), ("slit_cut", ctypes.c_int),
+                ("fp32_tangent", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):

@@ -1,6 +1,7 @@
 /* A plain C99 consumer of include/pff.h: compiled with gcc and linked against libpff by
  * tests/test_library_abi.py, it calls the host-only entry points (no GPU needed) and checks their
  * results. Exit status 0 = every check passed; otherwise the number of the failed check. */
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -11,6 +12,8 @@ int main(void) {
   pff_params p;
   pff_default_params(&p);
   if (p.dim != 2 && p.dim != 3) return 1;
+  /* defaults of the fields appended last: FP64 coarse solve, one node per grid point */
+  if (p.coarse_precision != 64 || p.slit_cut != 0) return 13;
   if (!pff_strerror(PFF_ERR_UNAVAILABLE) || !strlen(pff_strerror(PFF_ERR_UNAVAILABLE))) return 2;
 
   /* 2D Q1, 2 x 2 cells, nothing masked: 3 x 3 nodes whose cell-coupling windows hold 2, 3, 2 indices
@@ -41,6 +44,9 @@ int main(void) {
   if (pff_set_load_component(NULL, 0) != PFF_ERR_INVALID_ARG) return 12;
   free(rowptr);
   free(col);
+  /* the struct layout, for the binding's ctypes mirror */
+  printf("layout %zu %zu %zu %zu\n", sizeof(pff_params), offsetof(pff_params, fp64_mode),
+         offsetof(pff_params, coarse_precision), offsetof(pff_params, slit_cut));
   printf("ok\n");
   return 0;
 }

@@ -76,3 +76,12 @@ def test_algorithmic_bytes_per_dof():
     assert bench.apply_bytes_per_dof(3, 2, 1, 4) == pytest.approx(8 + 97.875 + 0.25)
     # FP64: twice the vector and per-point bytes
     assert bench.apply_bytes_per_dof(2, 2, 1, 8) == pytest.approx(16 + 66 + 1 / 3)
+
+
+def test_method_minimum_bytes_per_dof():
+    """The roofline's algorithmic bytes (SURVEY's method minimum): x and y once each, d + 2 state values
+    per node over d + 1 DoFs per node, one flag byte per node."""
+    import bench
+    assert bench.method_bytes_per_dof(2, 4) == pytest.approx(8 + 16 / 3 + 1 / 3)   # 13.67
+    assert bench.method_bytes_per_dof(2, 8) == pytest.approx(16 + 32 / 3 + 1 / 3)  # 27.0
+    assert bench.method_bytes_per_dof(3, 4) == pytest.approx(8 + 20 / 4 + 1 / 4)   # 13.25

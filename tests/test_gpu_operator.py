@@ -131,3 +131,26 @@ def test_apply_float_float_fp64(dim, p, N, split):
     dmask = pr.mesh.dirichlet_mask()
     y = ctx.apply_jacobian(xd, mode=PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT).cpu().numpy()
     assert rel(y, G.T @ np.where(dmask, 0.0, x)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("dim,p,N", [(2, 1, 9), (2, 2, 9), (2, 3, 6), (2, 4, 5)])
+@pytest.mark.parametrize("split", [0, 1])
+def test_apply_fp32_recomputed_tangent(dim, p, N, split):
+    """fp32_tangent = 1: the FP32 Jacobian recomputed at the Gauss points from the nodal state (no stored
+    per-point data) in every mode and masking, against the oracle within the FP32 tolerance; also the
+    tension state from rest, whose points mostly have e = 0 (repeated eigenvalues 0, H(0) = 1)."""
+    from paper_2005_00331_gb300 import PFF_MASK_ADJOINT, PFF_MASK_RAW, PFF_MODE_BLOCKDIAG, PFF_MODE_TRANSPOSE
+    for zero_u in (False, True):
+        pr = Problem(dim, p, N, split=split, seed=60 + p, active_frac=0.2, zero_u=zero_u)
+        ctx = pr.context(fp32_tangent=1)
+        x = np.random.default_rng(p + 61).normal(size=pr.mesh.n_dofs)
+        x32 = x.astype(np.float32).astype(np.float64)
+        xd = cuda(x, np.float32)
+        G, Gb = pr.G(), pr.G(fe.MODE_BLOCKDIAG)
+        dmask = pr.mesh.dirichlet_mask()
+        for mode, ref in ((0, fe.masked(G, pr.mask) @ x32), (PFF_MASK_RAW, G @ x32),
+                          (PFF_MODE_BLOCKDIAG, fe.masked(Gb, pr.mask) @ x32),
+                          (PFF_MODE_TRANSPOSE, fe.masked(G.T.tocsr(), pr.mask) @ x32),
+                          (PFF_MODE_TRANSPOSE | PFF_MASK_ADJOINT, G.T @ np.where(dmask, 0.0, x32))):
+            y = ctx.apply_jacobian(xd, mode=mode).cpu().numpy()
+            assert rel(y, ref) <= FP32_TOL, (mode, zero_u)

@@ -98,7 +98,15 @@ def test_plain_c_consumer(lib, tmp_path):
                         "-Wl,-rpath," + libdir], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
-    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+    lines = r.stdout.strip().splitlines()
+    assert r.returncode == 0 and lines[-1] == "ok", (r.returncode, r.stdout, r.stderr)
+    # the binding's ctypes mirror of pff_params has the C layout
+    import ctypes
+    from paper_2005_00331_gb300.pff import Params
+    size, off_fp64, off_coarse, off_slit = (int(v) for v in lines[0].split()[1:])
+    assert ctypes.sizeof(Params) == size
+    assert (Params.fp64_mode.offset, Params.coarse_precision.offset, Params.slit_cut.offset) == \
+        (off_fp64, off_coarse, off_slit)
 
 
 def test_status_codes_match_the_header():
