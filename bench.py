@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--max-seconds", type=float, default=600.0,
                     help="--mode loadsteps: stop a precision's loading after this many seconds (partial result)")
     ap.add_argument("--precision", type=int, default=64, help="precision of --mode apply")
+    ap.add_argument("--coarse-precision", type=int, default=64,
+                    help="coarse solve of the FP32 multigrid: 64 FP64 inverses (default), 32 FP32 inverses")
     ap.add_argument("--fp32-tangent", type=int, default=0,
                     help="FP32 applies (2D): 0 stored per-point values, 1 recompute the tangent from the nodal state")
     ap.add_argument("--fp64-mode", type=int, default=1,
@@ -657,11 +659,13 @@ def run_pdas(a):
 
     from paper_2005_00331_gb300 import setup_mesh
     dev = torch.device("cuda", torch.cuda.current_device())
-    out = {"mode": "pdas", "workload": workload_name(a), "state": a.state, "newton_rtol": a.newton_rtol}
+    out = {"mode": "pdas", "workload": workload_name(a), "state": a.state, "newton_rtol": a.newton_rtol,
+           "coarse_precision_of_fp32_mg": a.coarse_precision}
     finals = {}
     for prec in (32, 64):
         ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
-                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode)
+                         mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode,
+                         coarse_precision=a.coarse_precision)
         U_h, po_h = make_state(ctx, a, seed=0)
         U = torch.from_numpy(U_h).to(dev)
         po = torch.from_numpy(po_h).to(dev)
@@ -775,7 +779,7 @@ def run_loadsteps(a):
     for prec in (32, 64):
         ctx = setup_mesh(dim=a.dim, degree=a.degree, n_cells_1d=a.cells, split=a.split, eps=2.0 / a.cells,
                          mg_precision=prec, cheb_degree=a.cheb_degree, fp64_mode=a.fp64_mode,
-                         gmres_max_iters=a.gmres_max)
+                         gmres_max_iters=a.gmres_max, coarse_precision=a.coarse_precision)
         U_h, po_h = make_state(ctx, b, seed=0)
         U = torch.from_numpy(U_h).to(dev)
         po = torch.from_numpy(po_h).to(dev)
