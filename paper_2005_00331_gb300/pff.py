@@ -417,13 +417,13 @@ class Context:
         n, phi1, phi2 = self.get_history()
         host = (lambda t: t.cpu().numpy() if t is not None else None)
         return ck.Checkpoint(self.params.dim, self.params.degree, self.params.n_cells_1d, float(load),
-                             self.get_state().cpu().numpy(), n, host(phi1), host(phi2))
+                             self.get_state().cpu().numpy(), n, host(phi1), host(phi2), self.params.slit_cut)
 
     def resume(self, ckpt, gc_field=None, lambda_field=None, mu_field=None):
         """Restores a checkpoint into this context (same mesh): set_state with phi_old = the last
         converged phase field (the state's own phase field when no step has converged), then the
         history. The next solve_load_step continues the checkpointed run."""
-        ckpt.check_mesh(self.params.dim, self.params.degree, self.params.n_cells_1d)
+        ckpt.check_mesh(self.params.dim, self.params.degree, self.params.n_cells_1d, self.params.slit_cut)
         dev = self._dev()
         dvec = (lambda a: torch.from_numpy(a).to(device=dev, dtype=torch.float64).contiguous())
         U = dvec(ckpt.U)

@@ -89,3 +89,32 @@ def test_report_lines():
     d = [json.loads(x) for x in lines]
     assert d[1]["newton_step"] == 1 and d[1]["res_norm"] == 1e-9 and d[0]["load"] == 2e-3
     assert d[0]["level_bytes"] == [10, 5]
+
+
+@pytest.mark.parametrize("dim,degree,cells", [(2, 2, 8), (3, 1, 4)])
+def test_cut_slit_round_trip_and_mesh_check(tmp_path, dim, degree, cells):
+    """A checkpoint of a mesh with the slit cut into it holds the copies of the slit's nodes (as many as
+    the oracle's cut mesh has), survives a round trip, and is refused by an uncut mesh of the same size."""
+    from oracle import mesh as M
+    m = M.Mesh(dim, degree, cells, slit="duplicate")
+    rng = np.random.default_rng(3)
+    a = ck.Checkpoint(dim, degree, cells, 1e-3, rng.normal(size=m.n_dofs), 1, rng.uniform(size=m.n_nodes), None,
+                      slit_cut=1)
+    assert a.n_nodes == m.n_nodes
+    path = str(tmp_path / "cut.npz")
+    ck.save(path, a)
+    b = ck.load(path)
+    assert b.slit_cut == 1 and np.array_equal(b.U, a.U)
+    b.check_mesh(dim, degree, cells, 1)
+    with pytest.raises(ValueError):
+        b.check_mesh(dim, degree, cells, 0)
+
+
+def test_four_entry_mesh_record_reads_as_uncut(tmp_path):
+    """Files whose mesh record has no slit_cut entry (written before it existed) load as uncut meshes."""
+    a = make(1)
+    path = str(tmp_path / "old.npz")
+    np.savez(path, format=np.array(ck.FORMAT), mesh=np.array([a.dim, a.degree, a.n_cells_1d, a.n_hist]),
+             load=np.array(a.load), U=a.U, phi1=a.phi1, phi2=np.zeros(0))
+    b = ck.load(path)
+    assert b.slit_cut == 0 and np.array_equal(b.phi1, a.phi1)
