@@ -160,3 +160,36 @@ def test_newton_step_on_cut_mesh(dim, p, N, mg):
     assert rel(Ug - U, U_ref - U) <= 1e-7
     uz = Ug[(dim - 1) * nn:dim * nn]
     assert np.all(uz[m.n_grid_nodes:] < uz[m.dup_of])  # the slit opens under tension
+
+
+def test_load_steps_and_resume_on_cut_mesh(tmp_path):
+    """Three quasi-static load steps of the tension test on the cut 2D Q2 16 x 16 mesh (Miehe split):
+    every step converges on both sides and the GPU states equal the oracle's load steps (direct solves);
+    a checkpoint after the second step, resumed in a fresh context, continues to the same third state."""
+    from paper_2005_00331_gb300 import checkpoint, setup_mesh
+    m = M.Mesh(2, 2, 16, slit="duplicate")
+    prm = fe.Params(LAM, MU, GC, 2.0 / 16, KAPPA, 1)
+    U = m.dirichlet_values(0.0)
+    phi = np.ones(m.n_nodes)
+    U[2 * m.n_nodes:] = phi
+    loads = [1e-3, 2e-3, 3e-3]
+    stats = []
+    ref = S.load_steps(m, prm, U, loads, stats=stats)
+    assert all(conv for _, conv in stats)
+    kw = dict(dim=2, degree=2, n_cells_1d=16, split=1, eps=2.0 / 16, slit_cut=1, mg_precision=32, lin_rtol=1e-10)
+    path = str(tmp_path / "cut_step2.npz")
+    with setup_mesh(**kw) as ctx:
+        ctx.set_state(cuda(U), cuda(phi), cuda(phi), None)
+        for k, load in enumerate(loads):
+            st, reps = ctx.solve_load_step(load, check=False)
+            assert st == 0
+            assert rel(ctx.get_state().cpu().numpy(), ref[k]) <= 1e-6
+            if k == 1:
+                checkpoint.save(path, ctx.checkpoint(load))
+        U_run = ctx.get_state().cpu().numpy()
+    ck = checkpoint.load(path)
+    assert ck.slit_cut == 1
+    with setup_mesh(**kw) as ctx:
+        ctx.resume(ck)
+        ctx.solve_load_step(loads[2])
+        assert rel(ctx.get_state().cpu().numpy(), U_run) <= 1e-7
