@@ -110,6 +110,10 @@ const char* g_last_cuda = "";
 }  // namespace
 
 // ---- context --------------------------------------------------------------------------------
+// Work vectors per level and precision: r, e, t, res, dv, s, and the second iterate / direction buffers
+// and two more seam-sum buffers of the 2D smoother (xb, db, t0, t2).
+constexpr int NWORK = 10;
+
 struct LevelData {
   int N = 0;
   long long nn = 0, nd = 0;
@@ -140,8 +144,8 @@ struct LevelData {
   cudaStream_t aux = nullptr;
   cudaEvent_t join = nullptr;
   // multigrid work vectors, per precision: r, e, t, res, dv, s
-  double* w64[6] = {};
-  float* w32[6] = {};
+  double* w64[NWORK] = {};
+  float* w32[NWORK] = {};
 };
 
 struct pff_ctx {
@@ -419,7 +423,7 @@ int ensure_work(pff_ctx* c, int l) {
   LevelData& L = c->lv[l];
   Real** w = work_of<Real>(L);
   if (w[0]) return PFF_OK;
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < NWORK; ++i) {
     CR(dalloc(c, &w[i], L.nd, l));
     CK(cudaMemsetAsync(w[i], 0, sizeof(Real) * L.nd, c->s));
   }
@@ -500,7 +504,7 @@ int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask,
 // contiguous, so one cast covers the four fields.
 int state32_level(pff_ctx* c, int l) {
   LevelData& L = c->lv[l];
-  if (L.s32) CK(launch_cast<double, float>((c->dim + 2) * L.nn, L.U, L.s32, c->s));
+  if (L.s32 && use_rc32(c)) CK(launch_cast<double, float>((c->dim + 2) * L.nn, L.U, L.s32, c->s));
   return PFF_OK;
 }
 
@@ -822,25 +826,54 @@ int smooth(pff_ctx* c, int l, const Real* f, Real* x, Real* t, Real* dv, bool st
   // theta_b = (hi + lo) lambda_b / 2, delta_b = (hi - lo) lambda_b / 2
   if (!started) CK(launch_cheb<Real>(0, n, nu, f, nullptr, dinv_of<Real>(L), dv, x, il, 2.0 / (hi + lo), 0.0, 0.0, c->s));
   bool added = false;
-  for (int k = 1; k < deg; ++k) {
-    const double rho_new = 1.0 / (2.0 * sigma - rho);
-    if (c->dim == 2) {
-      // the apply finishes the step on single-tile nodes; the seam nodes follow
-      ChebEpi<Real> ce;
+  if (c->dim == 2 && deg > 1) {
+    // Steps 1 .. K fused into the block-diagonal apply. Step k reads x_k from X[k % 2] and d_{k-1} from
+    // D[(k-1) % 2] and writes x_{k+1}, d_k to the other buffers on the nodes of a single tile; its seam
+    // sums go to T[k % 3], and step k+1 finishes step k on the seam nodes while it stages its patch
+    // (ChebEpi). Only the last step's seam nodes take a separate launch. Every T buffer is all zero on
+    // entry and again on exit.
+    CR(ensure_work<Real>(c, l));
+    Real** w = work_of<Real>(L);
+    Real* X[2] = {w[6], x};
+    Real* D[2] = {dv, w[7]};
+    Real* T[3] = {w[8], t, w[9]};
+    const int K = deg - 1;
+    double c1p = 0.0, c2sp = 0.0;
+    for (int k = 1; k <= K; ++k) {
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      ChebEpi<Real> ce{};
       ce.f = f;
       ce.dinv = dinv_of<Real>(L);
-      ce.d = dv;
-      ce.x = x;
       ce.inv_lam = il;
+      ce.x = X[k % 2];
+      ce.x_out = X[(k + 1) % 2];
+      ce.d = D[(k - 1) % 2];
+      ce.d_out = D[k % 2];
       ce.c1 = rho_new * rho;
       ce.c2s = 4.0 * rho_new / (hi - lo);
-      ce.acc = (acc && k == deg - 1) ? acc : nullptr;
+      ce.acc = (acc && k == K) ? acc : nullptr;
       ce.on = 1;
-      added = ce.acc != nullptr;
-      // t is all zero on entry (work vectors start zeroed; every use below leaves it zeroed)
-      CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce, true));
-      CK(launch_cheb_seam<Real>(L.g, t, ce, c->s));
-    } else {
+      ce.pp = k >= 2;
+      ce.tp = T[(k - 1) % 3];
+      ce.tz = k >= 3 ? T[(k - 2) % 3] : nullptr;
+      ce.c1p = c1p;
+      ce.c2sp = c2sp;
+      CR(apply_level<Real>(c, l, X[k % 2], T[k % 3], JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, &ce, true));
+      if (k == K) {
+        ce.tz = T[(K - 1) % 3];  // no later step reads the previous seam sums
+        CK(launch_cheb_seam<Real>(L.g, T[K % 3], ce, c->s));
+      }
+      c1p = ce.c1;
+      c2sp = ce.c2s;
+      rho = rho_new;
+    }
+    added = acc != nullptr;
+    // x_{K+1} is in X[(K + 1) % 2]; the caller's buffer is X[1]
+    if (!acc && (K + 1) % 2 != 1) CK(cudaMemcpyAsync(x, X[0], sizeof(Real) * n, cudaMemcpyDeviceToDevice, c->s));
+  }
+  for (int k = 1; k < deg && c->dim != 2; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    {
       CR(apply_level<Real>(c, l, x, t, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY));
       CK(launch_cheb<Real>(k, n, nu, f, t, dinv_of<Real>(L), dv, x, il, 0.0, rho_new * rho, 4.0 * rho_new / (hi - lo),
                            c->s));

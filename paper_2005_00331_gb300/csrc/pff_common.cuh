@@ -127,6 +127,19 @@ struct ChebEpi {
   double c1, c2s;
   Store* acc;
   int on;
+  // Iterate and direction in two buffers each, seam sums in three (no seam launch between steps):
+  // step k reads x_k from x and d_{k-1} from d and writes x_{k+1} to x_out and d_k to d_out on the nodes
+  // of a single tile. With pp = 1 it first finishes step k-1 on the seam nodes of its patch, whose
+  // y_{k-1} is complete in tp: d_{k-1} = c1p d_{k-2} + c2p dinv (f - y_{k-1}) with d_{k-2} in d_out, and
+  // x_k = x_{k-1} + d_{k-1} with x_{k-1} in x_out; the tile that owns the node writes d_{k-1} to d and
+  // x_k to x, and zeroes tz there (the seam sums of step k-2, which no one reads any more).
+  // x_out = d_out = null: the single-buffer scheme, in place, seams by launch_cheb_seam.
+  Store* x_out;
+  Store* d_out;
+  const Store* tp;
+  Store* tz;
+  double c1p, c2sp;
+  int pp;
 };
 
 // First Chebyshev step with zero initial guess, x = d = (c0s / lambda_b) dinv f, done by the kernel

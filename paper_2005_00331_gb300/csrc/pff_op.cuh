@@ -545,16 +545,19 @@ __device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, 
     if (g.cut && gy == g.cut_row && gx < g.cut_x) return;
   }
   const bool both = g.cut && gy == g.cut_row && gx < g.cut_x;  // a vertical seam crossing a cut slit
+  Store* const x_out = ce.x_out ? ce.x_out : ce.x;
+  Store* const d_out = ce.d_out ? ce.d_out : ce.d;
   for (int k = 0; k < (both ? 2 : 1); ++k) {
     const long long node = k ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
     for (int f = 0; f < 3; ++f) {
       const long long gi = f * g.nn + node;
       const Store yv = y[gi];
       const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - yv));
-      ce.d[gi] = dn;
+      d_out[gi] = dn;
       if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
-      else ce.x[gi] = ce.x[gi] + dn;
+      else x_out[gi] = ce.x[gi] + dn;
       y[gi] = Store(0);
+      if (ce.tz) ce.tz[gi] = Store(0);  // the previous step's seam sums (two-buffer scheme)
     }
   }
 }
@@ -613,11 +616,19 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   }
   // Chebyshev coefficients per block (field < 2: u block), in the storage precision
   Store ch_c1 = Store(0), ch_c2[2] = {Store(0), Store(0)};
+  Store pc1 = Store(0), pc2[2] = {Store(0), Store(0)};  // the previous step's (seam completion)
   if (ce.on) {
     ch_c2[0] = Store(ce.c2s) * ce.inv_lam[0];
     ch_c2[1] = Store(ce.c2s) * ce.inv_lam[1];
     ch_c1 = Store(ce.c1);
+    if (ce.pp) {
+      pc2[0] = Store(ce.c2sp) * ce.inv_lam[0];
+      pc2[1] = Store(ce.c2sp) * ce.inv_lam[1];
+      pc1 = Store(ce.c1p);
+    }
   }
+  Store* const x_out = ce.x_out ? ce.x_out : ce.x;
+  Store* const d_out = ce.d_out ? ce.d_out : ce.d;
   const long long ntiles = g.ntiles;
   // node phases (copy, masking, store): this thread handles patch nodes tid + k NT, all fields
   auto prefetch = [&](long long tile, int st) {
@@ -676,15 +687,39 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       if (rs >= NNODE) break;
       const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
+      const long long node = cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
       unsigned char m = 0;
       if (oa.inmask != IN_RAW && gx < g.n1 && gy < g.n1) {
-        m = flags[cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy];
+        m = flags[node];
         if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
+      }
+      Store xv[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) xv[f] = xs[f * NNODE + rs];
+      if (ce.on && ce.pp && gx < g.n1 && gy < g.n1) {
+        // a seam node of the previous step (shared with a neighbouring tile, as in the store phase):
+        // finish that step here from its complete seam sums
+        const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
+        const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) ||
+                          (r == NPY - 1 && tiy < g.ntile[1] - 1 && !cut_below(g, tiy, r, NPY, gx));
+        if (low || high) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const long long gi = f * g.nn + node;
+            const Store dk = pc1 * d_out[gi] + pc2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - ce.tp[gi]));
+            xv[f] = x_out[gi] + dk;
+            if (!low) {  // the owning tile writes the finished step back
+              ce.d[gi] = dk;
+              ce.x[gi] = xv[f];
+              if (ce.tz) ce.tz[gi] = Store(0);
+            }
+          }
+        }
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const int i = f * NNODE + rs;
-        X[i] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(xs[i]);
+        X[i] = ((m >> f) & 1u) ? Real(0) : cvt<Real>(xv[f]);
       }
     }
     __syncthreads();
@@ -866,9 +901,9 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
           // node of this tile only: finish the smoothing step here
           const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
           const Store dn = ch_c1 * ce.d[gi] + ch_c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y));
-          ce.d[gi] = dn;
+          d_out[gi] = dn;
           if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
-          else ce.x[gi] = ce.x[gi] + dn;
+          else x_out[gi] = ce.x[gi] + dn;
         } else if (masked) {
           if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
         } else if (low || high) {
