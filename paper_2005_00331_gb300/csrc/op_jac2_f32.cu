@@ -4,13 +4,13 @@
 
 namespace pff {
 
-template <int P, int SPLIT, int RC>
+template <int P, int SPLIT, int RC, int CG>
 static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
                              const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
-                             const ChebEpi<float>& ce, const MatConst32& mc) {
+                             const ChebEpi<float>& ce, const MatConst32& mc, const CgEpi<float>& cg) {
   constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC>();
   static int grid_per_sm = 0;
-  auto kern = k_jac2_staged<P, float, float, SPLIT, RC>;
+  auto kern = k_jac2_staged<P, float, float, SPLIT, RC, CG>;
   if (!grid_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -28,28 +28,29 @@ static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags
   if (grid > g.ntiles) grid = g.ntiles;
   OpArgs oa{inmask, outmask};
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, mc);
+  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, mc, cg);
   return cudaSuccess;
 }
 
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags, const Geom& g,
                        const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
-                       const ChebEpi<float>* ce, const Rc32* rc) {
+                       const ChebEpi<float>* ce, const Rc32* rc, const CgEpi<float>* cg) {
   ChebEpi<float> off{};
   off.on = 0;
   const ChebEpi<float>& e = ce ? *ce : off;
+  const CgEpi<float> cg_off{};
+  const CgEpi<float>& cgr = cg ? *cg : cg_off;
   if (dim != 2) return cudaErrorInvalidValue;
-  if (rc) {
-#define PFF_CASE(PP, SS) \
-    if (p == PP && split == SS) \
-      return run_jac2<PP, SS, 1>(x, y, flags, g, tb, rc->state, mode, inmask, outmask, s, e, rc->mc);
-    PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
-    PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
-#undef PFF_CASE
-    return cudaErrorInvalidValue;
+  // the CG-Lanczos epilogue and the recomputed tangent are separate instantiations, so that the plain
+  // apply keeps its own code
+  const bool cgo = cgr.on != 0;
+#define PFF_CASE(PP, SS)                                                                                       \
+  if (p == PP && split == SS) {                                                                                \
+    if (rc && cgo) return run_jac2<PP, SS, 1, 1>(x, y, flags, g, tb, rc->state, mode, inmask, outmask, s, e, rc->mc, cgr); \
+    if (rc) return run_jac2<PP, SS, 1, 0>(x, y, flags, g, tb, rc->state, mode, inmask, outmask, s, e, rc->mc, cgr);        \
+    if (cgo) return run_jac2<PP, SS, 0, 1>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, MatConst32{}, cgr);        \
+    return run_jac2<PP, SS, 0, 0>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, MatConst32{}, cgr);                 \
   }
-#define PFF_CASE(PP, SS) \
-  if (p == PP && split == SS) return run_jac2<PP, SS, 0>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, MatConst32{});
   PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)
   PFF_CASE(1, 1) PFF_CASE(2, 1) PFF_CASE(3, 1) PFF_CASE(4, 1)
 #undef PFF_CASE

@@ -56,14 +56,14 @@ cudaError_t launch_res(int dim, int p, int split, const double* U, double* r, co
 
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s, const ChebEpi<double>* ce) {
-  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce)
+                       cudaStream_t s, const ChebEpi<double>* ce, const CgEpi<double>* cg) {
+  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, cg)
                   : launch_jac_d3(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s);
 }
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc) {
-  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, rc)
+                       cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc, const CgEpi<float>* cg) {
+  return dim == 2 ? launch_jac_d2(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, rc, cg)
                   : launch_jac_d3(dim, p, split, x, y, flags, g, tb, qp, mode, inmask, outmask, s);
 }
 

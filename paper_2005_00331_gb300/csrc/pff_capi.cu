@@ -468,20 +468,21 @@ bool prof_jac(pff_ctx* c, int l) {
          (l == 0 && prof_on(c, d ? PFF_PROF_JAC64_L0 : PFF_PROF_JAC32_L0));
 }
 
-// y = G x on level l (y zeroed first). With ce (2D), a fused Chebyshev step: see launch_jac; such
+// y = G x on level l (y zeroed first). With ce (2D), a fused Chebyshev step, with cg (2D) a CG-Lanczos
+// step: see launch_jac; such
 // launches are not timed by pff_profile (they move more than the apply's bytes).
 template <typename Real>
 int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask, int outmask,
-                const ChebEpi<Real>* ce = nullptr, bool y_is_zero = false) {
+                const ChebEpi<Real>* ce = nullptr, bool y_is_zero = false, const CgEpi<Real>* cg = nullptr) {
   LevelData& L = c->lv[l];
   if (!y_is_zero) CK(cudaMemsetAsync(y, 0, sizeof(Real) * L.nd, c->s));
-  const bool timed = !ce && prof_jac<Real>(c, l);
+  const bool timed = !ce && !cg && prof_jac<Real>(c, l);  // plain applies only
   if (timed) CR(prof_mark(c));
   if (sizeof(Real) == 8 && c->prm.fp64_mode == 1) {
     if (c->dim == 2)
       CK(launch_jac_df(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
                        L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s,
-                       reinterpret_cast<const ChebEpi<double>*>(ce)));
+                       reinterpret_cast<const ChebEpi<double>*>(ce), reinterpret_cast<const CgEpi<double>*>(cg)));
     else
       CK(launch_jac_df3(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
                         L.flags, L.g, L.tdf, L.qpdf, mode, inmask, outmask, c->s));
@@ -491,10 +492,15 @@ int apply_level(pff_ctx* c, int l, const Real* x, Real* y, int mode, int inmask,
                                     (float)(c->prm.gc / c->prm.eps), 1.0f - ke, ke}};
     CK(launch_jac(c->dim, c->p, c->prm.split, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                   L.flags, L.g, L.t32, L.qp32, mode, inmask, outmask, c->s,
-                  reinterpret_cast<const ChebEpi<float>*>(ce), &rc));
+                  reinterpret_cast<const ChebEpi<float>*>(ce), &rc, reinterpret_cast<const CgEpi<float>*>(cg)));
+  } else if (sizeof(Real) == 4) {
+    CK(launch_jac(c->dim, c->p, c->prm.split, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
+                  L.flags, L.g, L.t32, L.qp32, mode, inmask, outmask, c->s,
+                  reinterpret_cast<const ChebEpi<float>*>(ce), nullptr, reinterpret_cast<const CgEpi<float>*>(cg)));
   } else {
-    CK(launch_jac(c->dim, c->p, c->prm.split, x, y, L.flags, L.g, tab_of<Real>(L), qp_of<Real>(L), mode, inmask,
-                  outmask, c->s, ce));
+    CK(launch_jac(c->dim, c->p, c->prm.split, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y),
+                  L.flags, L.g, L.t64, L.qp64, mode, inmask, outmask, c->s,
+                  reinterpret_cast<const ChebEpi<double>*>(ce), reinterpret_cast<const CgEpi<double>*>(cg)));
   }
   if (timed) CR(prof_mark(c));
   return PFF_OK;
@@ -619,12 +625,32 @@ int eig_estimate(pff_ctx* c, int l) {
   CK(cudaMemsetAsync(L.lhist, 0, 4 * it_max * sizeof(double), c->s));
   CK(cudaMemsetAsync(Ap, 0, sizeof(Real) * n, c->s));
   CK(launch_cg_init<Real>(n, nu, c->prm.eig_seed, L.flags, L.nn, dinv_of<Real>(L), r, z, pv, L.lpart, scal, c->s));
-  for (int it = 0; it < it_max; ++it) {
-    // Ap is zero here: zeroed above, then by every update
-    CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, nullptr, true));
-    CK(launch_cg_pap<Real>(n, nu, pv, Ap, L.lpart, scal, ah, it, it_max, c->s));
-    CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, L.lpart, bh, it, it_max, c->s));
-    CK(launch_cg_pupdate<Real>(n, nu, z, scal, pv, c->s));
+  if (c->dim == 2) {
+    // the direction update p = z + beta p and <p, A p> (with alpha) are done by the apply (CgEpi): two
+    // launches per step. p alternates between pv and w[6] (another tile may still read the old p).
+    Real* P[2] = {pv, w[6]};
+    for (int it = 0; it < it_max; ++it) {
+      CgEpi<Real> cg{};
+      cg.on = 1;
+      cg.p_old = P[it % 2];  // beta is 0 at the first step (scal zeroed above)
+      cg.p_out = P[(it + 1) % 2];
+      cg.scal = scal;
+      cg.part = L.lpart;
+      cg.ah = ah;
+      cg.it = it;
+      cg.iters = it_max;
+      // Ap is zero here: zeroed above, then by every update
+      CR(apply_level<Real>(c, l, z, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, nullptr, true, &cg));
+      CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, L.lpart, bh, it, it_max, c->s));
+    }
+  } else {
+    for (int it = 0; it < it_max; ++it) {
+      // Ap is zero here: zeroed above, then by every update
+      CR(apply_level<Real>(c, l, pv, Ap, JM_BLOCKDIAG, IN_ALL, OUT_IDENTITY, nullptr, true));
+      CK(launch_cg_pap<Real>(n, nu, pv, Ap, L.lpart, scal, ah, it, it_max, c->s));
+      CK(launch_cg_update<Real>(n, nu, Ap, dinv_of<Real>(L), scal, r, z, L.lpart, bh, it, it_max, c->s));
+      CK(launch_cg_pupdate<Real>(n, nu, z, scal, pv, c->s));
+    }
   }
   CK(launch_tridiag_eig(it_max, ah, bh, L.lam, c->s));
   CK(cudaMemsetAsync(pv, 0, sizeof(Real) * n, c->s));  // w[2] is the smoother's zeroed apply buffer
@@ -1217,7 +1243,7 @@ static int setup_impl(pff_ctx* c) {
     CR(dalloc(c, &L.lam, 8, l));
     CR(dalloc(c, &L.lscal, 16, l));
     CR(dalloc(c, &L.lhist, 4 * P.eig_iters, l));
-    CR(dalloc(c, &L.lpart, 2 * 152 * 2, l));
+    CR(dalloc(c, &L.lpart, 2 * 152 * 32, l));  // 2 partial sums per CTA of the CG-Lanczos reductions
     CK(cudaStreamCreateWithFlags(&L.aux, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&L.join, cudaEventDisableTiming));
     std::vector<unsigned char> fl = host_flags(c->dim, c->p, L.N, cut);

@@ -142,6 +142,38 @@ struct ChebEpi {
   int pp;
 };
 
+// One CG-Lanczos step (lambda_max estimate) folded into the block-diagonal 2D apply: the apply's input
+// is p = z + beta p_old (beta per block from scal[6..7], 0 at the first step), built while the tile is
+// staged (the apply's src is z); the tile that owns a node writes p there to p_out. Each tile adds p_i
+// times its own contribution to (A p)_i over its nodes, per block: over all tiles that is <p, A p>, seam
+// nodes included. The last CTA to finish adds the per-CTA partials in a fixed order and takes alpha
+// (cg_take_alpha), which the update kernel then reads.
+template <typename Store>
+struct CgEpi {
+  int on;
+  const Store* p_old;
+  Store* p_out;
+  double* scal;  // CG-Lanczos scalars: rz, pAp, alpha, beta, rz_new, dead flags (2 each), counter at [12]
+  double* part;  // per-CTA partial sums, 2 per CTA
+  double* ah;    // alpha history
+  int it, iters;
+};
+
+// alpha = rz / <p, A p> per block from the reduced <p, A p> (r0, r1); a block whose recurrence broke
+// down stays dead (alpha 0).
+__device__ __forceinline__ void cg_take_alpha(double* scal, double* ah, int it, int iters, double r0, double r1) {
+  scal[2] = r0;
+  scal[3] = r1;
+  for (int b = 0; b < 2; ++b) {
+    const double rz = scal[b], pAp = scal[2 + b];
+    double al = 0.0;
+    if (scal[10 + b] == 0.0 && pAp > 0.0 && rz > 0.0 && pAp < 1e300) al = rz / pAp;
+    else scal[10 + b] = 1.0;
+    scal[4 + b] = al;
+    ah[b * iters + it] = al;
+  }
+}
+
 // First Chebyshev step with zero initial guess, x = d = (c0s / lambda_b) dinv f, done by the kernel
 // that produces f (the restriction, the V-cycle's residual update). nu: first phase-field DoF.
 template <typename Real>

@@ -728,18 +728,8 @@ __global__ void __launch_bounds__(BLK) k_cg_pap(long long n, long long nu, const
     else s1 += v;
   }
   double r0, r1;
-  if (cg_reduce_last(s0, s1, part, reinterpret_cast<unsigned*>(scal + 12), r0, r1) && threadIdx.x == 0) {
-    scal[2] = r0;
-    scal[3] = r1;
-    for (int b = 0; b < 2; ++b) {
-      const double rz = scal[b], pAp = scal[2 + b];
-      double al = 0.0;
-      if (scal[10 + b] == 0.0 && pAp > 0.0 && rz > 0.0 && pAp < 1e300) al = rz / pAp;
-      else scal[10 + b] = 1.0;
-      scal[4 + b] = al;
-      ah[b * iters + it] = al;
-    }
-  }
+  if (cg_reduce_last(s0, s1, part, reinterpret_cast<unsigned*>(scal + 12), r0, r1) && threadIdx.x == 0)
+    cg_take_alpha(scal, ah, it, iters, r0, r1);
 }
 
 // r -= alpha Ap, z = D^{-1} r, Ap = 0 (the next apply accumulates into it), <r, z>, then

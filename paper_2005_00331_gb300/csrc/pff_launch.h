@@ -35,12 +35,14 @@ inline cudaError_t launch_k(void (*k)(KP...), dim3 grid, dim3 block, size_t smem
 
 // y (+)= G x on one level from the stored per-point data (qp: [tile][nv][qpt]); y must be
 // zeroed by the caller (seam nodes are accumulated atomically). mode: JM_*; masks: In/OutMask.
+// With cg != nullptr (2D only) it is one step of the CG-Lanczos estimate (CgEpi).
 // With ce != nullptr (2D only) the block-diagonal apply finishes a Chebyshev step on the nodes of a
 // single tile (x and d updated in place) and accumulates only seam nodes into y; launch_cheb_seam
 // then completes the step on the seam nodes.
 cudaError_t launch_jac(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                        const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask,
-                       int outmask, cudaStream_t s, const ChebEpi<double>* ce = nullptr);
+                       int outmask, cudaStream_t s, const ChebEpi<double>* ce = nullptr,
+                       const CgEpi<double>* cg = nullptr);
 // FP32 Jacobian recomputed at the points from the nodal state (2D; see pw_jac_rc2): state = u_x, u_y,
 // phi, phi~ as 4 blocks of g.nn floats, mc the material constants. Passed as `rc`, it replaces qp.
 struct Rc32 {
@@ -49,15 +51,17 @@ struct Rc32 {
 };
 cudaError_t launch_jac(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                        const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                       cudaStream_t s, const ChebEpi<float>* ce = nullptr, const Rc32* rc = nullptr);
+                       cudaStream_t s, const ChebEpi<float>* ce = nullptr, const Rc32* rc = nullptr,
+                       const CgEpi<float>* cg = nullptr);
 template <typename Store>
 cudaError_t launch_cheb_seam(const Geom& g, Store* y, const ChebEpi<Store>& ce, cudaStream_t s);
 cudaError_t launch_jac_d2(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s, const ChebEpi<double>* ce);
+                          cudaStream_t s, const ChebEpi<double>* ce, const CgEpi<double>* cg = nullptr);
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags,
                           const Geom& g, const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc = nullptr);
+                          cudaStream_t s, const ChebEpi<float>* ce, const Rc32* rc = nullptr,
+                          const CgEpi<float>* cg = nullptr);
 cudaError_t launch_jac_d3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<double>& tb, const double* qp, int mode, int inmask, int outmask,
                           cudaStream_t s);
@@ -67,7 +71,7 @@ cudaError_t launch_jac_d3(int dim, int p, int split, const float* x, float* y, c
 // The same Jacobian in double-word arithmetic (FP64 vectors, per-point data as df64 pairs); 2D.
 cudaError_t launch_jac_df(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                           const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
-                          cudaStream_t s, const ChebEpi<double>* ce = nullptr);
+                          cudaStream_t s, const ChebEpi<double>* ce = nullptr, const CgEpi<double>* cg = nullptr);
 cudaError_t launch_jac_df3(int dim, int p, int split, const double* x, double* y, const unsigned char* flags,
                            const Geom& g, const Tab<df64>& tb, const df64* qp, int mode, int inmask, int outmask,
                            cudaStream_t s);

@@ -520,6 +520,20 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
+// Sum of v over the CTA (threads numbered tid < nt, nt a multiple of 32); valid in tid 0.
+__device__ __forceinline__ double block_sum_lin(double v, int tid, int nt, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (tid < 32) {
+    r = tid < nt / 32 ? sh[tid] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
 template <int P, typename Real>
 struct Stage2 {
   static constexpr int NSTAGE = 1;  // kept as a parameter: the kernel supports 2
@@ -581,11 +595,11 @@ constexpr int jac2_min_blocks() {
 // RC = 1 (FP32 only): the pointwise Jacobian is recomputed from the nodal state (u_x, u_y, phi, phi~;
 // qpg then points to those 4 fields of n_nodes floats each) by pw_jac_rc2 instead of read from stored
 // per-point data: the tile stages 4 state values per node instead of NV values per Gauss point.
-template <int P, typename Real, typename Store, int SPLIT, int RC>
+template <int P, typename Real, typename Store, int SPLIT, int RC, int CG>
 __global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real, RC>())
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
               Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce,
-              MatConst32 mc) {
+              MatConst32 mc, CgEpi<Store> cg) {
   pdl_wait();
   using T = Tile2<P>;
   constexpr int TX = T::TX, TY = T::TY, n = T::n, NF = 3;
@@ -629,6 +643,12 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   }
   Store* const x_out = ce.x_out ? ce.x_out : ce.x;
   Store* const d_out = ce.d_out ? ce.d_out : ce.d;
+  Store cg_beta[2] = {Store(0), Store(0)};
+  double cg_dot[2] = {0.0, 0.0};  // this thread's share of <p, A p>, per block
+  if constexpr (CG != 0) {
+    cg_beta[0] = Store(cg.scal[6]);
+    cg_beta[1] = Store(cg.scal[7]);
+  }
   const long long ntiles = g.ntiles;
   // node phases (copy, masking, store): this thread handles patch nodes tid + k NT, all fields
   auto prefetch = [&](long long tile, int st) {
@@ -696,12 +716,24 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       Store xv[NF];
 #pragma unroll
       for (int f = 0; f < NF; ++f) xv[f] = xs[f * NNODE + rs];
+      // a node shared with a neighbouring tile (as in the store phase), and whether this tile owns it
+      bool low = false, high = false;
+      if (CG != 0 || (ce.on && ce.pp)) {
+        low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
+        high = (s == NPX - 1 && tix < g.ntile[0] - 1) ||
+               (r == NPY - 1 && tiy < g.ntile[1] - 1 && !cut_below(g, tiy, r, NPY, gx));
+      }
+      if (CG != 0 && gx < g.n1 && gy < g.n1) {
+        // CG-Lanczos: the apply's input p = z + beta p_old (z is the staged src)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const long long gi = f * g.nn + node;
+          xv[f] = xv[f] + cg_beta[f < 2 ? 0 : 1] * cg.p_old[gi];
+          if (!low) cg.p_out[gi] = xv[f];
+        }
+      }
       if (ce.on && ce.pp && gx < g.n1 && gy < g.n1) {
-        // a seam node of the previous step (shared with a neighbouring tile, as in the store phase):
-        // finish that step here from its complete seam sums
-        const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
-        const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) ||
-                          (r == NPY - 1 && tiy < g.ntile[1] - 1 && !cut_below(g, tiy, r, NPY, gx));
+        // a seam node of the previous step: finish that step here from its complete seam sums
         if (low || high) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
@@ -897,6 +929,8 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       for (int f = 0; f < NF; ++f) {
         const long long gi = f * g.nn + node;
         const bool masked = (m >> f) & 1u;
+        if constexpr (CG != 0)
+          if (!masked) cg_dot[f < 2 ? 0 : 1] += cvt<double>(X[f * NNODE + rs]) * cvt<double>(acc[f]);
         if (ce.on && !low && !high) {
           // node of this tile only: finish the smoothing step here
           const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
@@ -915,6 +949,33 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
     }
   }
   cp_async_wait<0>();
+  if constexpr (CG != 0) {
+    // per-CTA partial of <p, A p>; the last CTA adds the partials in CTA order and takes alpha
+    __shared__ double sh[32];
+    __shared__ int last;
+    const double r0 = block_sum_lin(cg_dot[0], tid, NT, sh), r1 = block_sum_lin(cg_dot[1], tid, NT, sh);
+    unsigned* cnt = reinterpret_cast<unsigned*>(cg.scal + 12);
+    if (tid == 0) {
+      cg.part[2 * blockIdx.x] = r0;
+      cg.part[2 * blockIdx.x + 1] = r1;
+      __threadfence();
+      last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double t0 = 0.0, t1 = 0.0;
+      for (int b = tid; b < (int)gridDim.x; b += NT) {
+        t0 += __ldcg(cg.part + 2 * b);
+        t1 += __ldcg(cg.part + 2 * b + 1);
+      }
+      const double s0 = block_sum_lin(t0, tid, NT, sh), s1 = block_sum_lin(t1, tid, NT, sh);
+      if (tid == 0) {
+        *cnt = 0u;
+        cg_take_alpha(cg.scal, cg.ah, cg.it, cg.iters, s0, s1);
+      }
+    }
+  }
 }
 
 template <typename Store>
