@@ -39,8 +39,9 @@ extern "C" {
 #define PFF_ERR_NOT_CONVERGED (-5) /* FGMRES reached its iteration cap */
 #define PFF_ERR_BREAKDOWN (-6)     /* Krylov breakdown (zero norm before convergence) */
 #define PFF_ERR_NO_STATE (-7)      /* pff_set_state has not been called */
-#define PFF_ERR_TOO_LARGE (-8)     /* problem exceeds the fixed scratch of pff_param_grad_noalloc, or
-                                      the 32-bit indices of the assembled comparator matrix */
+#define PFF_ERR_TOO_LARGE (-8)     /* problem exceeds the fixed scratch of pff_param_grad_noalloc, the
+                                      32-bit indices of the assembled comparator matrix, or 2^31 - 1
+                                      DoFs (the operator kernels index DoFs with 32-bit integers) */
 #define PFF_ERR_UNAVAILABLE (-9)   /* an optional library (cuSPARSE, for pff_csr_spmv) cannot be loaded */
 
 /* Splits of the elastic energy (Sec. 2.1): none = isotropic model, miehe = spectral split. */
@@ -129,7 +130,8 @@ void pff_default_params(pff_params* p);
 
 /* Builds the mesh hierarchy and allocates per-level storage (Sec. 3.3 nested meshes).
  * `stream` is a cudaStream_t (NULL = legacy default stream). On success *out owns the context.
- * Errors: INVALID_ARG (dim, degree, N, tolerances out of range), OOM, CUDA. */
+ * Errors: INVALID_ARG (dim, degree, N, tolerances out of range), TOO_LARGE (more than 2^31 - 1 DoFs
+ * on the finest level, counting a cut slit's copies; far above what device memory holds), OOM, CUDA. */
 int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream);
 
 /* Frees everything the context owns (synchronises its stream first). NULL is allowed. */

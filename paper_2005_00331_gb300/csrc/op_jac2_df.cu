@@ -9,7 +9,7 @@ template <int P, int SPLIT, int CG>
 static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* flags, const Geom& g, const Tab<df64>& tb,
                              const df64* qp, int mode, int inmask, int outmask, cudaStream_t s,
                              const ChebEpi<double>& ce, const CgEpi<double>& cg) {
-  constexpr size_t smem = jac2_staged_smem<P, df64, double, SPLIT, 0>();
+  constexpr size_t smem = jac2_staged_smem<P, df64, double, SPLIT, 0, CG>();
   static int grid_per_sm = 0;
   auto kern = k_jac2_staged<P, df64, double, SPLIT, 0, CG>;
   if (!grid_per_sm) {
@@ -27,7 +27,7 @@ static cudaError_t run_jac2_df(const double* x, double* y, const unsigned char* 
   }
   long long grid = (long long)sms * grid_per_sm;
   if (grid > g.ntiles) grid = g.ntiles;
-  OpArgs oa{inmask, outmask};
+  const OpArgs oa = op_args(inmask, outmask, grid, g.ntile[0]);
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
   if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, MatConst32{}, cg);
   return cudaSuccess;

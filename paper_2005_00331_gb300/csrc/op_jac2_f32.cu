@@ -8,7 +8,7 @@ template <int P, int SPLIT, int RC, int CG>
 static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
                              const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
                              const ChebEpi<float>& ce, const MatConst32& mc, const CgEpi<float>& cg) {
-  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC>();
+  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC, CG>();
   static int grid_per_sm = 0;
   auto kern = k_jac2_staged<P, float, float, SPLIT, RC, CG>;
   if (!grid_per_sm) {
@@ -26,7 +26,7 @@ static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags
   }
   long long grid = (long long)sms * grid_per_sm;
   if (grid > g.ntiles) grid = g.ntiles;
-  OpArgs oa{inmask, outmask};
+  const OpArgs oa = op_args(inmask, outmask, grid, g.ntile[0]);
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
   if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, mc, cg);
   return cudaSuccess;

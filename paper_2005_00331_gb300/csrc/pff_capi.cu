@@ -1346,6 +1346,11 @@ int pff_setup_mesh(pff_ctx** out, const pff_params* p, void* stream) {
     tile_shape(p->dim, p->degree, t);
     if (p->n_cells_1d % 2 || (p->n_cells_1d / 2) % t[p->dim - 1]) return PFF_ERR_INVALID_ARG;
   }
+  {  // the operator kernels index DoFs (field-major node arrays) with 32-bit integers
+    const double n1 = (double)p->degree * p->n_cells_1d + 1.0;  // in double: no integer overflow
+    const double nodes = p->dim == 2 ? n1 * n1 + n1 : n1 * n1 * n1 + n1 * n1;
+    if ((p->dim + 1) * nodes > 2147483647.0) return PFF_ERR_TOO_LARGE;
+  }
   pff_ctx* c = new (std::nothrow) pff_ctx();
   if (!c) return PFF_ERR_OOM;
   c->prm = *p;

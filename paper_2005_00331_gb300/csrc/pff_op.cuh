@@ -253,7 +253,15 @@ struct PWRes {
 // -------------------------------------------------------------------------------------------
 struct OpArgs {
   int inmask, outmask;
+  // persistent 2D kernels: gridDim.x tiles = step_y tile rows + step_x tiles (step_x < tiles per row)
+  int step_x = 0, step_y = 0;
 };
+inline OpArgs op_args(int inmask, int outmask, long long grid, int ntile_x) {
+  OpArgs a{inmask, outmask};
+  a.step_x = int(grid % ntile_x);
+  a.step_y = int(grid / ntile_x);
+  return a;
+}
 
 __device__ __forceinline__ unsigned char dirichlet_bits(int dim) { return (unsigned char)((1u << dim) - 1u); }
 
@@ -539,6 +547,15 @@ struct Stage2 {
   static constexpr int NSTAGE = 1;  // kept as a parameter: the kernel supports 2
 };
 
+// Whether the 2D Jacobian kernel masks its staged node patch in place (the raw copy is already in the
+// compute type, and nothing reads the masked patch after the next tile's copies have started: the
+// CG-Lanczos epilogue does, so it keeps a separate buffer). Saves 3.5 KB per CTA for FP32 Q2, which
+// makes room for a fifth CTA per SM.
+template <int P, typename Real, typename Store, int CG>
+constexpr bool jac2_x_inplace() {
+  return std::is_same<Real, Store>::value && CG == 0 && Stage2<P, Real>::NSTAGE == 1;
+}
+
 // The same smoothing update on the seam nodes of the 2D tile grid, once their y is complete; y is
 // reset to 0 there, so y is all zero again afterwards (the fused applies write no other entry).
 // Seam index t enumerates the vertical seam lines, then the horizontal ones (crossings once).
@@ -581,22 +598,26 @@ __device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, 
 // 80 for Q1 and 168 above (unconstrained, Q4 took 255 registers and ran one CTA of 5 warps per SM; at
 // 168 it spills 8 to 16 bytes); native FP64 unconstrained.
 // The recomputed FP32 tangent (RC) keeps the state's contractions live: 96 up to Q2 (80 spilled), 128 above.
-template <int P, typename Real, int RC = 0>
+// The CG-Lanczos epilogue (CG) keeps its dot products and a separate masked patch: FP32 80 up to Q2 (64
+// spilled 60 bytes; shared memory holds it at four CTAs per SM, which 80 keeps), 128 above; double-word Q4
+// unconstrained (one CTA per SM by shared memory; 168 spilled 200 bytes).
+template <int P, typename Real, int RC = 0, int CG = 0>
 constexpr int jac2_reg_budget() {
-  return std::is_same<Real, float>::value ? (RC ? (P <= 2 ? 96 : 128) : (P <= 2 ? 64 : 96))
-         : std::is_same<Real, df64>::value ? (P == 1 ? 80 : 168)
+  return std::is_same<Real, float>::value
+             ? (RC ? (P <= 2 ? 96 : 128) : (P <= 2 ? (CG ? 80 : 64) : (CG ? 128 : 96)))
+         : std::is_same<Real, df64>::value ? (P == 1 ? 80 : (CG && P == 4) ? 0 : 168)
                                            : 0;
 }
-template <int P, typename Real, int RC = 0>
+template <int P, typename Real, int RC = 0, int CG = 0>
 constexpr int jac2_min_blocks() {
-  return jac2_reg_budget<P, Real, RC>() ? 65536 / (Tile2<P>::NT * jac2_reg_budget<P, Real, RC>()) : 1;
+  return jac2_reg_budget<P, Real, RC, CG>() ? 65536 / (Tile2<P>::NT * jac2_reg_budget<P, Real, RC, CG>()) : 1;
 }
 
 // RC = 1 (FP32 only): the pointwise Jacobian is recomputed from the nodal state (u_x, u_y, phi, phi~;
 // qpg then points to those 4 fields of n_nodes floats each) by pw_jac_rc2 instead of read from stored
 // per-point data: the tile stages 4 state values per node instead of NV values per Gauss point.
 template <int P, typename Real, typename Store, int SPLIT, int RC, int CG>
-__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real, RC>())
+__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real, RC, CG>())
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
               Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce,
               MatConst32 mc, CgEpi<Store> cg) {
@@ -612,12 +633,14 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   constexpr int XS = NF * NPY * NPX;
   constexpr int NNODE = NPY * NPX, NIT = (NNODE + NT - 1) / NT;
   static_assert(!RC || std::is_same<Real, float>::value, "the recomputed tangent is FP32 only");
+  constexpr bool XIN = jac2_x_inplace<P, Real, Store, CG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* QPs = reinterpret_cast<Real*>(smem_raw);                  // [NS][NV][QPT]
   Store* Xs = reinterpret_cast<Store*>(QPs + NS * NV * QPT);      // [NS][NF][NPY][NPX] raw copies
   Store* Ss = Xs + NS * XS;                                       // [NS][NSF][NPY][NPX] state (RC)
-  Real* X = reinterpret_cast<Real*>(Ss + NS * NSF * NNODE);       // [NF][NPY][NPX] masked, compute type
-  Real* UB = X + XS;                                              // [NF][TY][n][QPX]
+  Real* Xc = reinterpret_cast<Real*>(Ss + NS * NSF * NNODE);
+  Real* X = XIN ? reinterpret_cast<Real*>(Xs) : Xc;               // [NF][NPY][NPX] masked, compute type
+  Real* UB = XIN ? Xc : Xc + XS;                                  // [NF][TY][n][QPX]
   Real* UD = UB + NF * TY * n * QPX;
   Real* sS = UD + NF * TY * n * QPX;
   Real* sD = sS + n * n;
@@ -649,10 +672,19 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
     cg_beta[0] = Store(cg.scal[6]);
     cg_beta[1] = Store(cg.scal[7]);
   }
-  const long long ntiles = g.ntiles;
+  // DoF indices fit in 32 bits (checked at setup); tile coordinates step by gridDim.x tiles without a
+  // division (oa.step_x along x with a carry into y, oa.step_y rows)
+  const int ntiles = int(g.ntiles), ntx = g.ntile[0], nn = int(g.nn), n1 = g.n1, ngrid = int(g.ngrid);
+  auto next_tile = [&](int& ax, int& ay) {
+    ax += oa.step_x;
+    ay += oa.step_y;
+    if (ax >= ntx) {
+      ax -= ntx;
+      ++ay;
+    }
+  };
   // node phases (copy, masking, store): this thread handles patch nodes tid + k NT, all fields
-  auto prefetch = [&](long long tile, int st) {
-    const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
+  auto prefetch = [&](int tile, int tix, int tiy, int st) {
     const int x0 = tix * TX * P, y0 = tiy * TY * P;
     Store* xs = Xs + st * XS;
 #pragma unroll
@@ -661,22 +693,22 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       if (rs >= NNODE) break;
       const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
-      const bool ok = gx < g.n1 && gy < g.n1;
-      const long long node = cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const bool ok = gx < n1 && gy < n1;
+      const int node = cut_below(g, tiy, r, NPY, gx) ? ngrid + gx : gx + n1 * gy;
       const Store* sp = src + (ok ? node : 0);
       Store* dp = xs + rs;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) cp_async_bytes(dp + f * NNODE, sp + (ok ? f * g.nn : 0), ok, (int)sizeof(Store));
+      for (int f = 0; f < NF; ++f) cp_async_bytes(dp + f * NNODE, sp + (ok ? f * nn : 0), ok, (int)sizeof(Store));
       if constexpr (RC != 0) {
         const Store* stp = reinterpret_cast<const Store*>(qpg) + (ok ? node : 0);
         Store* sdp = Ss + st * NSF * NNODE + rs;
 #pragma unroll
         for (int f = 0; f < NSF; ++f)
-          cp_async_bytes(sdp + f * NNODE, stp + (ok ? f * g.nn : 0), ok, (int)sizeof(Store));
+          cp_async_bytes(sdp + f * NNODE, stp + (ok ? f * nn : 0), ok, (int)sizeof(Store));
       }
     }
     if constexpr (RC == 0) {
-      const char* qsrc = reinterpret_cast<const char*>(qpg + tile * (long long)NV * QPT);
+      const char* qsrc = reinterpret_cast<const char*>(qpg + (long long)tile * (NV * QPT));
       char* qdst = reinterpret_cast<char*>(QPs + st * NV * QPT);
       constexpr int NCH = NV * QPT * (int)sizeof(Real) / 16;
       for (int i = tid; i < NCH; i += NT) cp_async16(qdst + 16 * i, qsrc + 16 * i);
@@ -684,20 +716,22 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   };
 
   int it = 0;
-  if ((long long)blockIdx.x < ntiles) prefetch(blockIdx.x, 0);
+  int tix = int(blockIdx.x % (unsigned)ntx), tiy = int(blockIdx.x / (unsigned)ntx);
+  if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, tix, tiy, 0);
   cp_async_commit();
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it, next_tile(tix, tiy)) {
     const int st = NS == 2 ? (it & 1) : 0;
     if constexpr (NS == 2) {
-      const long long nxt = tile + gridDim.x;
-      if (nxt < ntiles) prefetch(nxt, st ^ 1);
+      const int nxt = tile + gridDim.x;
+      int nx = tix, ny = tiy;
+      next_tile(nx, ny);
+      if (nxt < ntiles) prefetch(nxt, nx, ny, st ^ 1);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int tix = int(tile % g.ntile[0]), tiy = int(tile / g.ntile[0]);
     const int x0 = tix * TX * P, y0 = tiy * TY * P;
     // masked compute-type node patch
     const Store* xs = Xs + st * XS;
@@ -707,9 +741,9 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       if (rs >= NNODE) break;
       const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
-      const long long node = cut_below(g, tiy, r, NPY, gx) ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const int node = cut_below(g, tiy, r, NPY, gx) ? ngrid + gx : gx + n1 * gy;
       unsigned char m = 0;
-      if (oa.inmask != IN_RAW && gx < g.n1 && gy < g.n1) {
+      if (oa.inmask != IN_RAW && gx < n1 && gy < n1) {
         m = flags[node];
         if (oa.inmask == IN_DIRICHLET) m &= dirichlet_bits(2);
       }
@@ -723,21 +757,21 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         high = (s == NPX - 1 && tix < g.ntile[0] - 1) ||
                (r == NPY - 1 && tiy < g.ntile[1] - 1 && !cut_below(g, tiy, r, NPY, gx));
       }
-      if (CG != 0 && gx < g.n1 && gy < g.n1) {
+      if (CG != 0 && gx < n1 && gy < n1) {
         // CG-Lanczos: the apply's input p = z + beta p_old (z is the staged src)
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          const long long gi = f * g.nn + node;
+          const int gi = f * nn + node;
           xv[f] = xv[f] + cg_beta[f < 2 ? 0 : 1] * cg.p_old[gi];
           if (!low) cg.p_out[gi] = xv[f];
         }
       }
-      if (ce.on && ce.pp && gx < g.n1 && gy < g.n1) {
+      if (ce.on && ce.pp && gx < n1 && gy < n1) {
         // a seam node of the previous step: finish that step here from its complete seam sums
         if (low || high) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
-            const long long gi = f * g.nn + node;
+            const int gi = f * nn + node;
             const Store dk = pc1 * d_out[gi] + pc2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - ce.tp[gi]));
             xv[f] = x_out[gi] + dk;
             if (!low) {  // the owning tile writes the finished step back
@@ -887,37 +921,82 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
     __syncthreads();
     if constexpr (NS == 1) {
       // the staging buffers are free: start the next tile's copies under the store phase
-      const long long nxt = tile + gridDim.x;
-      if (nxt < ntiles) prefetch(nxt, 0);
+      const int nxt = tile + gridDim.x;
+      int nx = tix, ny = tiy;
+      next_tile(nx, ny);
+      if (nxt < ntiles) prefetch(nxt, nx, ny, 0);
       cp_async_commit();
     }
+    // Transposed x contraction, one node column per thread: thread (cx, qi) sums the n Gauss columns of
+    // its cell into the cell's node column k = qi, for every field and node row of the cell. The cell's
+    // node values then go to four arrays (in the UB buffer), by whether the node row / column is the
+    // cell's last, i.e. shared with the next cell: E00 [NF][TY P][TX P], E10 [NF][TY][TX P],
+    // E01 [NF][TY P][TX], E11 [NF][TY][TX]; each patch node sums at most one entry of each.
+    constexpr int TXP = TX * P, TYP = TY * P;
+    {
+      Real v[NF][n];
+      Real Sk[n], Dk[n];
+#pragma unroll
+      for (int q = 0; q < n; ++q) {
+        Sk[q] = sS[q * n + qi];
+        Dk[q] = sD[q * n + qi];
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          const Real* ubp = UB + ((f * TY + ty) * n + l) * QPX + cx * n;
+          const Real* udp = UD + ((f * TY + ty) * n + l) * QPX + cx * n;
+          Real a = fmac(Dk[0], udp[0], Sk[0] * ubp[0]);
+#pragma unroll
+          for (int q = 1; q < n; ++q) a = fmac(Sk[q], ubp[q], fmac(Dk[q], udp[q], a));
+          v[f][l] = a;
+        }
+      __syncthreads();  // every thread has read its cell's columns of UB and UD
+      Real* E00 = UB;
+      Real* E10 = E00 + NF * TYP * TXP;
+      Real* E01 = E10 + NF * TY * TXP;
+      Real* E11 = E01 + NF * TYP * TX;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+          Real* e;
+          if (l < P)
+            e = qi < P ? E00 + (f * TYP + ty * P + l) * TXP + cx * P + qi : E01 + (f * TYP + ty * P + l) * TX + cx;
+          else
+            e = qi < P ? E10 + (f * TY + ty) * TXP + cx * P + qi : E11 + (f * TY + ty) * TX + cx;
+          *e = v[f][l];
+        }
+    }
+    __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < NIT; ++kk) {
       const int rs = tid + kk * NT;
       if (rs >= NNODE) break;
       const int r = rs / NPX, s = rs - r * NPX;
       const int gx = x0 + s, gy = y0 + r;
-      if (gx >= g.n1 || gy >= g.n1) continue;
-      const int ylo = r == 0 ? 0 : (r - 1) / P, yhi = r / P < TY - 1 ? r / P : TY - 1;
-      const int xlo = s == 0 ? 0 : (s - 1) / P, xhi = s / P < TX - 1 ? s / P : TX - 1;
-      Real acc[NF] = {Real(0), Real(0), Real(0)};
-      for (int cy = ylo; cy <= yhi; ++cy) {
-        const int l = r - cy * P;
-        for (int cxx = xlo; cxx <= xhi; ++cxx) {
-          const int k = s - cxx * P;
+      if (gx >= n1 || gy >= n1) continue;
+      Real acc[NF];
+      {
+        const Real* E00 = UB;
+        const Real* E10 = E00 + NF * TYP * TXP;
+        const Real* E01 = E10 + NF * TY * TXP;
+        const Real* E11 = E01 + NF * TYP * TX;
+        const bool ra = r < TYP, sa = s < TXP;                    // the node row / column starts a cell
+        const bool re = r > 0 && r % P == 0, se = s > 0 && s % P == 0;  // ... or ends one
+        const int rb = r / P - 1, sb = s / P - 1;
 #pragma unroll
-          for (int q = 0; q < n; ++q) {
-            const Real sk = sS[q * n + k], dk = sD[q * n + k];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) {
-              const int o = ((f * TY + cy) * n + l) * QPX + cxx * n + q;
-              acc[f] = fmac(sk, UB[o], fmac(dk, UD[o], acc[f]));
-            }
-          }
+        for (int f = 0; f < NF; ++f) {
+          Real a = (ra && sa) ? E00[(f * TYP + r) * TXP + s] : Real(0);
+          if (re && sa) a = a + E10[(f * TY + rb) * TXP + s];
+          if (se && ra) a = a + E01[(f * TYP + r) * TX + sb];
+          if (re && se) a = a + E11[(f * TY + rb) * TX + sb];
+          acc[f] = a;
         }
       }
       const bool below = cut_below(g, tiy, r, NPY, gx);
-      const long long node = below ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+      const int node = below ? ngrid + gx : gx + n1 * gy;
       const bool low = (s == 0 && tix > 0) || (r == 0 && tiy > 0 && !cut_above(g, tiy, r, gx));
       const bool high = (s == NPX - 1 && tix < g.ntile[0] - 1) || (r == NPY - 1 && tiy < g.ntile[1] - 1 && !below);
       unsigned char m = 0;
@@ -927,7 +1006,7 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
-        const long long gi = f * g.nn + node;
+        const int gi = f * nn + node;
         const bool masked = (m >> f) & 1u;
         if constexpr (CG != 0)
           if (!masked) cg_dot[f < 2 ? 0 : 1] += cvt<double>(X[f * NNODE + rs]) * cvt<double>(acc[f]);
@@ -988,14 +1067,15 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, Ch
   cheb_seam_node<Store>(g, tpx, tpy, y, ce, t, Store(ce.c1), c2);
 }
 
-template <int P, typename Real, typename Store, int SPLIT, int RC = 0>
+template <int P, typename Real, typename Store, int SPLIT, int RC = 0, int CG = 0>
 constexpr size_t jac2_staged_smem() {
   using T = Tile2<P>;
   constexpr int NS = Stage2<P, Real>::NSTAGE;
   constexpr int XS = 3 * T::NPY * T::NPX;
   constexpr int NV = RC ? 0 : qp_nv(2, SPLIT), NSF = RC ? 4 : 0;
+  constexpr int XC = jac2_x_inplace<P, Real, Store, CG>() ? 0 : XS;
   return sizeof(Real) * (size_t)NS * NV * T::QPX * T::QPY + sizeof(Store) * (size_t)NS * (XS + NSF * T::NPY * T::NPX) +
-         sizeof(Real) * (size_t)(XS + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
+         sizeof(Real) * (size_t)(XC + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
 }
 
 // ===========================================================================================

@@ -65,6 +65,18 @@ def test_setup_rejects_bad_parameters_before_cuda(lib, field, value):
     assert not h.value
 
 
+@pytest.mark.parametrize("dim,degree,cells", [(2, 2, 18920), (2, 4, 30000), (3, 1, 1290), (3, 2, 1 << 21)])
+def test_setup_rejects_more_dofs_than_32bit_indices(lib, dim, degree, cells):
+    # 3 (2p N + 1)^2 or 4 (p N + 1)^3 DoFs above 2^31 - 1: TOO_LARGE before any CUDA call
+    from paper_2005_00331_gb300 import pff
+    p = pff.Params()
+    lib.pff_default_params(ctypes.byref(p))
+    p.dim, p.degree, p.n_cells_1d = dim, degree, cells
+    h = ctypes.c_void_p()
+    assert lib.pff_setup_mesh(ctypes.byref(h), ctypes.byref(p), None) == -8
+    assert not h.value
+
+
 def test_null_context_is_rejected(lib):
     n = ctypes.c_longlong()
     i = ctypes.c_int()
