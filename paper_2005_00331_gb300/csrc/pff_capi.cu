@@ -169,6 +169,7 @@ struct pff_ctx {
   double* dU = nullptr;
   double* scratch = nullptr;   // 4 fine-sized FP64 vectors (CG-Lanczos, residual checks)
   double* partial = nullptr;   // reduction partials
+  unsigned* kcnt = nullptr;    // CTA counter of the fused CGS2 passes (zero between launches)
   double* dres = nullptr;      // small device results
   double* hist = nullptr;      // CG alpha/beta histories
   int* cnt = nullptr;
@@ -1044,11 +1045,9 @@ int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_o
       double* wv = c->V + (long long)(j + 1) * n;
       CR(precondition(c, Vj, Zj));
       CR(apply_level<double>(c, 0, Zj, wv, JM_FULL, IN_ALL, OUT_IDENTITY));
-      CK(launch_mdot(n, j + 1, c->V, wv, c->partial, c->hdev, c->s));
-      CK(launch_maxpy(n, j + 1, c->V, c->hdev, wv, c->s));
-      CK(launch_mdot(n, j + 1, c->V, wv, c->partial, c->hdev + (m + 1), c->s));
-      CK(launch_maxpy(n, j + 1, c->V, c->hdev + (m + 1), wv, c->s));
-      CK(launch_dot2<double>(n, n, wv, wv, c->partial, c->hdev + 2 * (m + 1), c->s));
+      // CGS2: hdev = (h1 [m + 1], h2 [m + 1], <w, w>, 0, 1 / |w|)
+      CK(launch_cgs2(n, j + 1, c->V, wv, c->partial, c->hdev, c->hdev + (m + 1), c->hdev + 2 * (m + 1), c->kcnt,
+                     c->s));
       CK(cudaMemcpyAsync(c->pinned, c->hdev, sizeof(double) * (2 * (m + 1) + 2), cudaMemcpyDeviceToHost, c->s));
       CK(cudaStreamSynchronize(c->s));
       CR(prof_collect(c));
@@ -1058,7 +1057,7 @@ int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_o
       if (!std::isfinite(nw2)) return PFF_ERR_NAN;
       const double nw = std::sqrt(nw2);
       H[(j + 1) * m + j] = nw;
-      if (nw > 0.0) CK(launch_normalize(n, wv, c->hdev + 2 * (m + 1), wv, c->s));
+      if (nw > 0.0) CK(launch_normalize(n, wv, c->hdev + 2 * (m + 1) + 2, wv, c->s));
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
         H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
@@ -1260,7 +1259,10 @@ static int setup_impl(pff_ctx* c) {
   CR(dalloc(c, &c->dU, F.nd));
   CR(dalloc(c, &c->scratch, 4 * F.nd));
   const int m = P.gmres_restart;
-  CR(dalloc(c, &c->partial, std::max<long long>(2 * 152 * 2, (long long)(m + 2) * 152)));
+  CR(dalloc(c, &c->partial, std::max<long long>(std::max<long long>(2 * 152 * 2, (long long)(m + 2) * 152),
+                                                (long long)CGS_KMAX * CGS_GRID_MAX)));
+  CR(dalloc(c, &c->kcnt, 1, TAG_KRYLOV));
+  CK(cudaMemsetAsync(c->kcnt, 0, sizeof(unsigned), c->s));
   CR(dalloc(c, &c->dres, 32));
   CR(dalloc(c, &c->hist, 4 * P.eig_iters));
   CR(dalloc(c, &c->cnt, 2));

@@ -226,25 +226,31 @@ __device__ inline double theta_dd(double a, double b) {
   return a == b ? heav(a) : (pos(a) - pos(b)) / (a - b);
 }
 
-// Eigen-decomposition of a symmetric 2x2 [[a, b], [b, c]]: l[0] >= l[1], columns of V.
+// Eigen-decomposition of a symmetric 2x2 [[a, b], [b, c]]: l[0] >= l[1], columns of V. The half gap r and
+// 1 / r come from one reciprocal square root, and the half-angle cosine and sine from another (no FP64
+// division or hypot: both are long sequences on the FP64 pipe). Strains are far from the FP64 limits
+// where hypot's scaling matters; a pair with |(a - c) / 2, b| below ~1e-154 counts as degenerate.
 __device__ inline void eig_sym2(double a, double b, double c, double l[2], double V[2][2]) {
   const double m = 0.5 * (a + c), dd = 0.5 * (a - c);
-  const double r = hypot(dd, b);
-  l[0] = m + r;
-  l[1] = m - r;
-  double cs = 1.0, sn = 0.0;
-  if (r > 0.0) {
+  const double r2 = fma(dd, dd, b * b);
+  double r = 0.0, cs = 1.0, sn = 0.0;
+  if (r2 > 0.0) {
     // half-angle of (cos 2t, sin 2t) = (dd, b) / r
-    const double c2 = dd / r, s2 = b / r;
+    const double ir = rsqrt(r2);
+    r = r2 * ir;
+    const double c2 = dd * ir, s2 = b * ir;
     if (c2 >= 0.0) {
-      cs = sqrt(0.5 * (1.0 + c2));
-      sn = s2 / (2.0 * cs);
+      const double y = 0.5 * (1.0 + c2), ry = rsqrt(y);  // cos t = sqrt(y), sin t = s2 / (2 cos t)
+      cs = y * ry;
+      sn = 0.5 * s2 * ry;
     } else {
-      sn = sqrt(0.5 * (1.0 - c2));
-      if (s2 < 0.0) sn = -sn;
-      cs = s2 / (2.0 * sn);
+      const double y = 0.5 * (1.0 - c2), ry = rsqrt(y);  // sin t = sign(s2) sqrt(y), cos t = s2 / (2 sin t)
+      sn = s2 < 0.0 ? -(y * ry) : y * ry;
+      cs = 0.5 * fabs(s2) * ry;
     }
   }
+  l[0] = m + r;
+  l[1] = m - r;
   V[0][0] = cs;  V[1][0] = sn;   // v1
   V[0][1] = -sn; V[1][1] = cs;   // v2
 }

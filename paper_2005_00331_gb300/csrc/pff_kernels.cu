@@ -494,7 +494,14 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-constexpr int DOT_GRID = 152 * 2;
+// Grid of the reduction kernels: two CTAs of BLK threads per SM, fewer for short vectors (measured on
+// the 2D Q2 256^2 Newton step: eight per SM made the CG-Lanczos update slower, 24 vs 19 us).
+constexpr int RED_GRID_MAX = 152 * 2;
+inline unsigned red_grid(long long n) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > RED_GRID_MAX) g = RED_GRID_MAX;
+  return (unsigned)(g < 1 ? 1 : g);
+}
 
 template <typename Real>
 __global__ void k_dot2_part(long long n, long long nu, const Real* __restrict__ x, const Real* __restrict__ y,
@@ -531,8 +538,9 @@ __global__ void k_dot2_final(int nb, const double* __restrict__ part, double* __
 template <typename Real>
 cudaError_t launch_dot2(long long n, long long nu, const Real* x, const Real* y, double* partial, double* res,
                         cudaStream_t s) {
-  count_launch(); k_dot2_part<Real><<<DOT_GRID, BLK, 0, s>>>(n, nu, x, y, partial);
-  count_launch(); k_dot2_final<<<1, BLK, 0, s>>>(DOT_GRID, partial, res);
+  const unsigned g = red_grid(n);
+  count_launch(); k_dot2_part<Real><<<g, BLK, 0, s>>>(n, nu, x, y, partial);
+  count_launch(); k_dot2_final<<<1, BLK, 0, s>>>((int)g, partial, res);
   return cudaGetLastError();
 }
 template cudaError_t launch_dot2<double>(long long, long long, const double*, const double*, double*, double*,
@@ -597,16 +605,165 @@ cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y,
   return cudaGetLastError();
 }
 
-__global__ void k_normalize(long long n, const double* __restrict__ x, const double* __restrict__ nrm2,
+__global__ void k_normalize(long long n, const double* __restrict__ x, const double* __restrict__ inv,
                             double* __restrict__ y) {
-  const double inv = 1.0 / sqrt(nrm2[0] + nrm2[1]);
+  const double a = inv[0];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    y[e] = x[e] * inv;
+    y[e] = x[e] * a;
 }
-cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s) {
+cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, nrm2, y);
+  count_launch(); k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, inv, y);
+  return cudaGetLastError();
+}
+
+// ===========================================================================================
+// Classical Gram-Schmidt with reorthogonalisation (CGS2) of a new FGMRES direction w against the basis
+// V_0 .. V_{k-1} (one instantiation per k <= CGS_KMAX), in three passes over the vectors:
+//   MODE 0: h_i = <V_i, w>;
+//   MODE 1: w -= sum_i V_i h_i, then h'_i = <V_i, w> of the updated w;
+//   MODE 2: w -= sum_i V_i h_i, then out = (<w, w>, 0, 1 / |w|) of the updated w (1 / |w| = 0 for w = 0).
+// Per element the update and the products are those of the separate passes. Each CTA leaves its partial
+// sums in part; the last CTA to finish (counted in cnt, which it resets) adds them in CTA order, one warp
+// per basis vector, so the results do not depend on timing.
+constexpr int CGS_GRID = CGS_GRID_MAX;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(BLK) k_cgs_pass(long long n, const double* __restrict__ V,
+                                                  const double* __restrict__ h, double* __restrict__ w,
+                                                  double* __restrict__ part, double* __restrict__ out,
+                                                  unsigned* __restrict__ cnt) {
+  constexpr int NS = MODE == 2 ? 1 : K;  // sums per thread
+  constexpr int KA = K > 0 ? K : 1;
+  constexpr int NW = BLK / 32;
+  __shared__ double sh[NS > 0 ? NS : 1][NW];
+  __shared__ double shh[KA];
+  __shared__ int last;
+  if constexpr (MODE != 0 && K > 0)
+    if ((int)threadIdx.x < K) shh[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double s[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int i = 0; i < NS; ++i) s[i] = 0.0;
+  // one element: the update (MODE 1, 2), then this thread's products
+  auto element = [&](const double* vv, double we) -> double {
+    if constexpr (MODE != 0) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc += vv[i] * shh[i];
+      we -= acc;
+    }
+    if constexpr (MODE == 2) {
+      s[0] += we * we;
+    } else {
+#pragma unroll
+      for (int i = 0; i < K; ++i) s[i] += vv[i] * we;
+    }
+    return we;
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // two elements per iteration, their loads issued before the arithmetic; the products are added in
+  // element order, as one element per iteration would
+  for (; e + stride < n; e += 2 * stride) {
+    double v0[KA], v1[KA];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      v0[i] = V[(long long)i * n + e];
+      v1[i] = V[(long long)i * n + e + stride];
+    }
+    const double w0 = w[e], w1 = w[e + stride];
+    const double u0 = element(v0, w0);
+    const double u1 = element(v1, w1);
+    if constexpr (MODE != 0) {
+      w[e] = u0;
+      w[e + stride] = u1;
+    }
+  }
+  if (e < n) {
+    double v0[KA];
+#pragma unroll
+    for (int i = 0; i < K; ++i) v0[i] = V[(long long)i * n + e];
+    const double u0 = element(v0, w[e]);
+    if constexpr (MODE != 0) w[e] = u0;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const double v = warp_sum(s[i]);
+    if (lane == 0) sh[i][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NS) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) t += sh[threadIdx.x][q];
+    part[(long long)threadIdx.x * gridDim.x + blockIdx.x] = t;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = wid; i < NS; i += NW) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + (long long)i * gridDim.x + b);
+    t = warp_sum(t);
+    if (lane == 0) {
+      if constexpr (MODE == 2) {
+        out[0] = t;
+        out[1] = 0.0;
+        out[2] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+      } else {
+        out[i] = t;
+      }
+    }
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
+static unsigned cgs_grid(long long n) {
+  long long g = (n + BLK - 1) / BLK;
+  if (g > CGS_GRID) g = CGS_GRID;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+template <int K>
+static cudaError_t cgs_passes(long long n, const double* V, double* w, double* part, double* h1, double* h2,
+                              double* nrm, unsigned* cnt, cudaStream_t s) {
+  const unsigned g = cgs_grid(n);
+  count_launch(); k_cgs_pass<K, 0><<<g, BLK, 0, s>>>(n, V, nullptr, w, part, h1, cnt);
+  count_launch(); k_cgs_pass<K, 1><<<g, BLK, 0, s>>>(n, V, h1, w, part, h2, cnt);
+  count_launch(); k_cgs_pass<K, 2><<<g, BLK, 0, s>>>(n, V, h2, w, part, nrm, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cgs2(long long n, int k, const double* V, double* w, double* part, double* h1, double* h2,
+                        double* nrm, unsigned* cnt, cudaStream_t s) {
+  switch (k) {
+#define PFF_CASE(K) \
+  case K: return cgs_passes<K>(n, V, w, part, h1, h2, nrm, cnt, s);
+    PFF_CASE(1) PFF_CASE(2) PFF_CASE(3) PFF_CASE(4) PFF_CASE(5) PFF_CASE(6) PFF_CASE(7) PFF_CASE(8)
+    PFF_CASE(9) PFF_CASE(10) PFF_CASE(11) PFF_CASE(12) PFF_CASE(13) PFF_CASE(14) PFF_CASE(15) PFF_CASE(16)
+#undef PFF_CASE
+    default: break;
+  }
+  static_assert(CGS_KMAX == 16, "one instantiation per basis size up to CGS_KMAX");
+  // larger bases: the separate multi-dot and update passes, then the norm pass with no basis vector
+  cudaError_t e = launch_mdot(n, k, V, w, part, h1, s);
+  if (e == cudaSuccess) e = launch_maxpy(n, k, V, h1, w, s);
+  if (e == cudaSuccess) e = launch_mdot(n, k, V, w, part, h2, s);
+  if (e == cudaSuccess) e = launch_maxpy(n, k, V, h2, w, s);
+  if (e != cudaSuccess) return e;
+  count_launch(); k_cgs_pass<0, 2><<<cgs_grid(n), BLK, 0, s>>>(n, V, h2, w, part, nrm, cnt);
   return cudaGetLastError();
 }
 
@@ -661,7 +818,6 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
 // partial sums, and the CTA that finishes last (counted on *cnt) adds the partials in a fixed order
 // and performs the scalar step, so one iteration takes the apply and three kernels.
 // scal: [rz0 rz1 pAp0 pAp1 alpha0 alpha1 beta0 beta1 rzn0 rzn1 dead0 dead1 | counter]
-constexpr int CG_GRID = DOT_GRID;
 
 __device__ __forceinline__ bool cg_reduce_last(double s0, double s1, double* __restrict__ part, unsigned* cnt,
                                                double& r0, double& r1) {
@@ -782,20 +938,20 @@ template <typename Real>
 cudaError_t launch_cg_init(long long n, long long nu, unsigned long long seed, const unsigned char* flags,
                            long long nn, const Real* dinv, Real* r, Real* z, Real* pv, double* part, double* scal,
                            cudaStream_t s) {
-  count_launch(); k_cg_init<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, seed, flags, nn, dinv, r, z, pv, part, scal);
+  count_launch(); k_cg_init<Real><<<red_grid(n), BLK, 0, s>>>(n, nu, seed, flags, nn, dinv, r, z, pv, part, scal);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_cg_pap(long long n, long long nu, const Real* pv, const Real* Ap, double* part, double* scal,
                           double* alpha_hist, int it, int iters, cudaStream_t s) {
-  count_launch(); k_cg_pap<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, pv, Ap, part, scal, alpha_hist, it, iters);
+  count_launch(); k_cg_pap<Real><<<red_grid(n), BLK, 0, s>>>(n, nu, pv, Ap, part, scal, alpha_hist, it, iters);
   return cudaGetLastError();
 }
 template <typename Real>
 cudaError_t launch_cg_update(long long n, long long nu, Real* Ap, const Real* dinv, double* scal, Real* r, Real* z,
                              double* part, double* beta_hist, int it, int iters, cudaStream_t s) {
   count_launch();
-  k_cg_update<Real><<<CG_GRID, BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z, part, beta_hist, it, iters);
+  k_cg_update<Real><<<red_grid(n), BLK, 0, s>>>(n, nu, Ap, dinv, scal, r, z, part, beta_hist, it, iters);
   return cudaGetLastError();
 }
 template <typename Real>

@@ -85,8 +85,15 @@ cudaError_t launch_mdot(long long n, int k, const double* V, const double* w, do
 cudaError_t launch_maxpy(long long n, int k, const double* V, const double* h, double* w, cudaStream_t s);
 // x += sum_i Z_i y[i]
 cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y, double* x, cudaStream_t s);
-// y = x / sqrt(nrm2[0])
-cudaError_t launch_normalize(long long n, const double* x, const double* nrm2, double* y, cudaStream_t s);
+// y = x * inv[0]
+cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, cudaStream_t s);
+// CGS2 of w against V_0 .. V_{k-1}: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2; nrm = (<w, w>, 0, 1 / |w|).
+// Three fused passes for k <= CGS_KMAX, else the separate passes; part >= max(CGS_KMAX, k) * CGS_GRID
+// doubles; cnt: one zero-initialised counter (left zero).
+constexpr int CGS_KMAX = 16;
+constexpr int CGS_GRID_MAX = 152 * 4;  // four CTAs per SM (eight were slower for bases of 1 to 4 vectors)
+cudaError_t launch_cgs2(long long n, int k, const double* V, double* w, double* part, double* h1, double* h2,
+                        double* nrm, unsigned* cnt, cudaStream_t s);
 
 // ---- Chebyshev-Jacobi and eigenvalue estimation -----------------------------------------
 // step 0: x = d = dinv f / theta_b; step k: d = c1 d + (2 rho_k / delta_b) dinv (f - Ax), x += d,

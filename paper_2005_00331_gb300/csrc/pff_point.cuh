@@ -94,8 +94,81 @@ __device__ void eval_state(const CellQP<DIM, P>& cq, const double* U, const Geom
   }
 }
 
+// eval_state and the value of a scalar nodal field f at the point. In 2D the cell's node rows are first
+// contracted along x (value and x-derivative weights of the point), then along y: 7 (p+1)^2 + 8 (p+1)
+// FMAs instead of 9 (p+1)^2 FMAs and 3 (p+1)^2 shape products; in 3D one shape evaluation per node.
+template <int DIM, int P>
+__device__ void eval_state_scalar(const CellQP<DIM, P>& cq, const double* U, const double* f, const Geom& g,
+                                  const Tab<double>& tb, double gu[DIM][DIM], double& ph, double gph[DIM],
+                                  double& fv) {
+  if constexpr (DIM == 2) {
+    constexpr int n = P + 1;
+    const int qx = cq.q[0], qy = cq.q[1];
+    double u0s[n], u0d[n], u1s[n], u1d[n], ps[n], pd[n], fs[n];
+    for (int ay = 0; ay < n; ++ay) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0, a5 = 0.0, a6 = 0.0;
+      for (int ax = 0; ax < n; ++ax) {
+        const long long nd = cq.node(ax + n * ay, g);
+        const double Sv = tb.S[qx][ax], Dv = tb.D[qx][ax];
+        const double v0 = U[nd], v1 = U[g.nn + nd], v2 = U[2 * g.nn + nd];
+        a0 = fma(Sv, v0, a0);
+        a1 = fma(Dv, v0, a1);
+        a2 = fma(Sv, v1, a2);
+        a3 = fma(Dv, v1, a3);
+        a4 = fma(Sv, v2, a4);
+        a5 = fma(Dv, v2, a5);
+        a6 = fma(Sv, f[nd], a6);
+      }
+      u0s[ay] = a0; u0d[ay] = a1; u1s[ay] = a2; u1d[ay] = a3; ps[ay] = a4; pd[ay] = a5; fs[ay] = a6;
+    }
+    gu[0][0] = gu[0][1] = gu[1][0] = gu[1][1] = 0.0;
+    ph = gph[0] = gph[1] = fv = 0.0;
+    for (int ay = 0; ay < n; ++ay) {
+      const double Sv = tb.S[qy][ay], Dv = tb.D[qy][ay];
+      gu[0][0] = fma(Sv, u0d[ay], gu[0][0]);
+      gu[0][1] = fma(Dv, u0s[ay], gu[0][1]);
+      gu[1][0] = fma(Sv, u1d[ay], gu[1][0]);
+      gu[1][1] = fma(Dv, u1s[ay], gu[1][1]);
+      ph = fma(Sv, ps[ay], ph);
+      gph[0] = fma(Sv, pd[ay], gph[0]);
+      gph[1] = fma(Dv, ps[ay], gph[1]);
+      fv = fma(Sv, fs[ay], fv);
+    }
+    return;
+  }
+  constexpr int NA = ipow<DIM>(P + 1);
+  for (int k = 0; k < DIM; ++k)
+    for (int j = 0; j < DIM; ++j) gu[k][j] = 0.0;
+  ph = 0.0;
+  fv = 0.0;
+  for (int j = 0; j < DIM; ++j) gph[j] = 0.0;
+  for (int a = 0; a < NA; ++a) {
+    double N, dN[DIM];
+    cq.shape(a, tb, N, dN);
+    const long long nd = cq.node(a, g);
+    for (int k = 0; k < DIM; ++k) {
+      const double uk = U[k * g.nn + nd];
+      for (int j = 0; j < DIM; ++j) gu[k][j] += uk * dN[j];
+    }
+    const double pv = U[DIM * g.nn + nd];
+    ph += pv * N;
+    for (int j = 0; j < DIM; ++j) gph[j] += pv * dN[j];
+    fv += f[nd] * N;
+  }
+}
+
 template <int DIM, int P>
 __device__ double eval_scalar(const CellQP<DIM, P>& cq, const double* f, const Geom& g, const Tab<double>& tb) {
+  if constexpr (DIM == 2) {  // contracted along x, then y
+    constexpr int n = P + 1;
+    double v = 0.0;
+    for (int ay = 0; ay < n; ++ay) {
+      double a = 0.0;
+      for (int ax = 0; ax < n; ++ax) a = fma(tb.S[cq.q[0]][ax], f[cq.node(ax + n * ay, g)], a);
+      v = fma(tb.S[cq.q[1]][ay], a, v);
+    }
+    return v;
+  }
   constexpr int NA = ipow<DIM>(P + 1);
   double v = 0.0;
   for (int a = 0; a < NA; ++a) {

@@ -15,6 +15,18 @@ namespace pff {
 // part QP_ALL: everything. Miehe split, in two passes: QP_STRAIN (what depends on u only: the
 // eigen-decomposition, the tangent, the phase-field coefficients, and sigma+ / E_s+ into sp64 for the
 // residual), then QP_PHASE (the coupling g'(phi) sigma+ from sp64 and phi, after each phi change).
+// FP32 and double-word copies of a per-point value (the FP32 copy is the double-word pair's high part:
+// one FP64 -> FP32 rounding fewer).
+__device__ __forceinline__ void store_lower(float* qp32, df64* qpdf, long long o, double v) {
+  if (qpdf) {
+    const df64 d = df_from(v);
+    qpdf[o] = d;
+    if (qp32) qp32[o] = d.hi;
+  } else if (qp32) {
+    qp32[o] = (float)v;
+  }
+}
+
 template <int DIM, int P, int SPLIT>
 __global__ void k_qp_setup(const double* __restrict__ U, const double* __restrict__ phit,
                            const double* __restrict__ gcf, const double* __restrict__ lamf,
@@ -29,7 +41,11 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
   if (t >= ncell * NQ) return;
   CellQP<DIM, P> cq;
   cq.set(t / NQ, int(t % NQ), g);
-  const double pt = eval_scalar<DIM, P>(cq, phit, g, tb);
+  // the state passes evaluate U and phi~ together (one shape evaluation per node)
+  const bool state_pass = qp64 && !(SPLIT == 1 && part == QP_PHASE);
+  double gu[DIM][DIM], ph, gph[DIM], pt;
+  if (state_pass) eval_state_scalar<DIM, P>(cq, U, phit, g, tb, gu, ph, gph, pt);
+  else pt = eval_scalar<DIM, P>(cq, phit, g, tb);
   const double gc = gcf ? eval_scalar<DIM, P>(cq, gcf, g, tb) : mc.gc;
   const double lam = lamf ? eval_scalar<DIM, P>(cq, lamf, g, tb) : mc.lambda;
   const double mu = muf ? eval_scalar<DIM, P>(cq, muf, g, tb) : mc.mu;
@@ -52,13 +68,10 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
       const double v = dgp * sp[m * g.qpt] * jxw;
       const long long o = base + (OB + m) * g.qpt;
       qp64[o] = v;
-      if (qp32) qp32[o] = (float)v;
-      if (qpdf) qpdf[o] = df_from(v);
+      store_lower(qp32, qpdf, o, v);
     }
     return;
   }
-  double gu[DIM][DIM], ph, gph[DIM];
-  eval_state<DIM, P>(cq, U, g, tb, gu, ph, gph);
   const double dgp = deg_dg(ph, mc.kappa), ddg = deg_ddg(mc.kappa);
 
   double e[DIM][DIM], tr = 0.0;
@@ -82,33 +95,70 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
     vals[2 + NM] = (ddg * Es + gc / mc.eps) * jxw;
     vals[3 + NM] = gc * mc.eps * jxw;
   } else {
-    double l[DIM], V[DIM][DIM];
-    eig_sym<DIM>(e, l, V);
-    double trs = tr;
-    snap_zero<DIM>(l, trs);
-    const double H = heav(trs), trp = pos(trs);
-    double sl2 = 0.0;
-    for (int t2 = 0; t2 < DIM; ++t2) sl2 += pos(l[t2]) * pos(l[t2]);
-    const double Esp = 0.5 * lam * trp * trp + mu * sl2;
-    // P+ = sum_i H(l_i) E_ii E_ii^T + sum_{i<j} theta_ij E_ij E_ij^T (orthonormal Mandel basis)
-    double Pp[NM][NM];
-    for (int a = 0; a < NM; ++a)
-      for (int b = 0; b < NM; ++b) Pp[a][b] = 0.0;
-    double epm[NM];
-    for (int m = 0; m < NM; ++m) epm[m] = 0.0;
-    for (int i = 0; i < DIM; ++i) {
-      for (int j = i; j < DIM; ++j) {
-        double vi[DIM], vj[DIM], Em[NM];
-        for (int k = 0; k < DIM; ++k) {
-          vi[k] = V[k][i];
-          vj[k] = V[k][j];
+    double Pp[NM][NM], epm[NM], H, trp, Esp;  // P+ (upper triangle), e+ (Mandel), H(tr), <tr>+, E_s+
+    if constexpr (DIM == 2) {
+      // Closed form in the eigen-angle t of e: (c2, s2) = (cos 2t, sin 2t), l1,2 = m +- r. With the
+      // orthonormal Mandel vectors u = I / sqrt2, w = R / sqrt2, z = J / sqrt2 (R, J as in the FP32 tangent),
+      // E_11 = (u + w) / sqrt2, E_22 = (u - w) / sqrt2 and E_12 = z, so
+      // P+ = Hs (u u^T + w w^T) + Hd (u w^T + w u^T) + theta z z^T, Hs,d = (H(l1) +- H(l2)) / 2, and
+      // e+ = Ep I + Em R, Ep,m = (<l1>+ +- <l2>+) / 2. No eigenvector and one reciprocal square root.
+      const double m = 0.5 * (e[0][0] + e[1][1]), dd = 0.5 * (e[0][0] - e[1][1]), b = e[0][1];
+      const double r2 = fma(dd, dd, b * b);
+      double r = 0.0, c2 = 1.0, s2 = 0.0;  // a degenerate pair keeps the coordinate axes, as eig_sym2
+      if (r2 > 0.0) {
+        const double ir = rsqrt(r2);
+        r = r2 * ir;
+        c2 = dd * ir;
+        s2 = b * ir;
+      }
+      double l[2] = {m + r, m - r};
+      double trs = tr;
+      snap_zero<2>(l, trs);
+      H = heav(trs);
+      trp = pos(trs);
+      const double p1 = pos(l[0]), p2 = pos(l[1]);
+      Esp = 0.5 * lam * trp * trp + mu * (p1 * p1 + p2 * p2);
+      const double th = theta_dd(l[0], l[1]);
+      const double Hs = 0.5 * (heav(l[0]) + heav(l[1])), Hd = 0.5 * (heav(l[0]) - heav(l[1]));
+      const double cc = c2 * c2, ss = s2 * s2, cs = c2 * s2;
+      Pp[0][0] = 0.5 * Hs * (1.0 + cc) + Hd * c2 + 0.5 * th * ss;
+      Pp[0][1] = 0.5 * Hs * (1.0 - cc) - 0.5 * th * ss;
+      Pp[0][2] = RS2 * (Hs * cs + Hd * s2 - th * cs);
+      Pp[1][1] = 0.5 * Hs * (1.0 + cc) - Hd * c2 + 0.5 * th * ss;
+      Pp[1][2] = RS2 * (Hd * s2 + th * cs - Hs * cs);
+      Pp[2][2] = Hs * ss + th * cc;
+      const double Ep = 0.5 * (p1 + p2), Em = 0.5 * (p1 - p2);
+      epm[0] = Ep + Em * c2;
+      epm[1] = Ep - Em * c2;
+      epm[2] = 1.4142135623730951 * Em * s2;
+    } else {
+      double l[DIM], V[DIM][DIM];
+      eig_sym<DIM>(e, l, V);
+      double trs = tr;
+      snap_zero<DIM>(l, trs);
+      H = heav(trs);
+      trp = pos(trs);
+      double sl2 = 0.0;
+      for (int t2 = 0; t2 < DIM; ++t2) sl2 += pos(l[t2]) * pos(l[t2]);
+      Esp = 0.5 * lam * trp * trp + mu * sl2;
+      // P+ = sum_i H(l_i) E_ii E_ii^T + sum_{i<j} theta_ij E_ij E_ij^T (orthonormal Mandel basis)
+      for (int a = 0; a < NM; ++a)
+        for (int b = 0; b < NM; ++b) Pp[a][b] = 0.0;
+      for (int mm = 0; mm < NM; ++mm) epm[mm] = 0.0;
+      for (int i = 0; i < DIM; ++i) {
+        for (int j = i; j < DIM; ++j) {
+          double vi[DIM], vj[DIM], Em[NM];
+          for (int k = 0; k < DIM; ++k) {
+            vi[k] = V[k][i];
+            vj[k] = V[k][j];
+          }
+          mandel_dyad<DIM>(vi, vj, i == j, Em);
+          const double th = (i == j) ? heav(l[i]) : theta_dd(l[i], l[j]);
+          for (int a = 0; a < NM; ++a)  // upper triangle (the tangent below reads b >= a)
+            for (int b = a; b < NM; ++b) Pp[a][b] += th * Em[a] * Em[b];
+          if (i == j)
+            for (int mm = 0; mm < NM; ++mm) epm[mm] += pos(l[i]) * Em[mm];
         }
-        mandel_dyad<DIM>(vi, vj, i == j, Em);
-        const double th = (i == j) ? heav(l[i]) : theta_dd(l[i], l[j]);
-        for (int a = 0; a < NM; ++a)
-          for (int b = 0; b < NM; ++b) Pp[a][b] += th * Em[a] * Em[b];
-        if (i == j)
-          for (int m = 0; m < NM; ++m) epm[m] += pos(l[i]) * Em[m];
       }
     }
     const double aH = gt * H + 1.0 - H;
@@ -133,8 +183,7 @@ __global__ void k_qp_setup(const double* __restrict__ U, const double* __restric
   for (int v = 0; v < NV; ++v) {
     if (SPLIT == 1 && part == QP_STRAIN && v >= OB && v < OB + NM) continue;
     qp64[base + v * g.qpt] = vals[v];
-    if (qp32) qp32[base + v * g.qpt] = (float)vals[v];
-    if (qpdf) qpdf[base + v * g.qpt] = df_from(vals[v]);
+    store_lower(qp32, qpdf, base + v * g.qpt, vals[v]);
   }
 }
 
