@@ -275,13 +275,16 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
     a0 = Real(cs.c0s) * cs.inv_lam[0];
     a1 = Real(cs.c0s) * cs.inv_lam[1];
   }
+  Real di[DIM + 1];  // loaded before the stores below, which the compiler cannot tell apart from them
+#pragma unroll
+  for (int f = 0; f <= DIM; ++f) di[f] = cs.on ? cs.dinv[f * gc.nn + nd] : Real(0);
 #pragma unroll
   for (int f = 0; f <= DIM; ++f) {
     const long long gi = f * gc.nn + nd;
     const Real v = ((fc >> f) & 1u) ? Real(0) : acc[f];
     yc[gi] = v;
     if (cs.on) {
-      const Real de = (f < DIM ? a0 : a1) * (cs.dinv[gi] * v);
+      const Real de = (f < DIM ? a0 : a1) * (di[f] * v);
       cs.d[gi] = de;
       cs.x[gi] = de;
     }

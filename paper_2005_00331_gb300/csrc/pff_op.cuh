@@ -580,13 +580,25 @@ __device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, 
   Store* const d_out = ce.d_out ? ce.d_out : ce.d;
   for (int k = 0; k < (both ? 2 : 1); ++k) {
     const long long node = k ? cut_copy(g, gx, 0) : gx + (long long)g.n1 * gy;
+    // all loads before the stores (the compiler cannot tell that the arrays do not alias)
+    Store yv[3], dv[3], iv[3], fv[3], xv[3], av[3];
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
       const long long gi = f * g.nn + node;
-      const Store yv = y[gi];
-      const Store dn = c1 * ce.d[gi] + c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - yv));
+      yv[f] = y[gi];
+      dv[f] = ce.d[gi];
+      iv[f] = ce.dinv[gi];
+      fv[f] = ce.f[gi];
+      xv[f] = ce.x[gi];
+      av[f] = ce.acc ? ce.acc[gi] : Store(0);
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const long long gi = f * g.nn + node;
+      const Store dn = c1 * dv[f] + c2[f < 2 ? 0 : 1] * (iv[f] * (fv[f] - yv[f]));
       d_out[gi] = dn;
-      if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
-      else x_out[gi] = ce.x[gi] + dn;
+      if (ce.acc) ce.acc[gi] = av[f] + (xv[f] + dn);
+      else x_out[gi] = xv[f] + dn;
       y[gi] = Store(0);
       if (ce.tz) ce.tz[gi] = Store(0);  // the previous step's seam sums (two-buffer scheme)
     }
@@ -757,23 +769,37 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         high = (s == NPX - 1 && tix < g.ntile[0] - 1) ||
                (r == NPY - 1 && tiy < g.ntile[1] - 1 && !cut_below(g, tiy, r, NPY, gx));
       }
+      // (Below, every field's loads come before the stores: the compiler cannot tell that the output
+      // arrays do not alias the inputs, and would otherwise wait for one round trip per field.)
       if (CG != 0 && gx < n1 && gy < n1) {
         // CG-Lanczos: the apply's input p = z + beta p_old (z is the staged src)
+        Store po[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) po[f] = cg.p_old[f * nn + node];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-          const int gi = f * nn + node;
-          xv[f] = xv[f] + cg_beta[f < 2 ? 0 : 1] * cg.p_old[gi];
-          if (!low) cg.p_out[gi] = xv[f];
+          xv[f] = xv[f] + cg_beta[f < 2 ? 0 : 1] * po[f];
+          if (!low) cg.p_out[f * nn + node] = xv[f];
         }
       }
       if (ce.on && ce.pp && gx < n1 && gy < n1) {
         // a seam node of the previous step: finish that step here from its complete seam sums
         if (low || high) {
+          Store dO[NF], dI[NF], fF[NF], tP[NF], xO[NF];
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             const int gi = f * nn + node;
-            const Store dk = pc1 * d_out[gi] + pc2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - ce.tp[gi]));
-            xv[f] = x_out[gi] + dk;
+            dO[f] = d_out[gi];
+            dI[f] = ce.dinv[gi];
+            fF[f] = ce.f[gi];
+            tP[f] = ce.tp[gi];
+            xO[f] = x_out[gi];
+          }
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const int gi = f * nn + node;
+            const Store dk = pc1 * dO[f] + pc2[f < 2 ? 0 : 1] * (dI[f] * (fF[f] - tP[f]));
+            xv[f] = xO[f] + dk;
             if (!low) {  // the owning tile writes the finished step back
               ce.d[gi] = dk;
               ce.x[gi] = xv[f];
@@ -1004,25 +1030,43 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         m = flags[node];
         if (oa.outmask == OUT_ZERO_DIRICHLET) m &= dirichlet_bits(2);
       }
+      if constexpr (CG != 0) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        const int gi = f * nn + node;
-        const bool masked = (m >> f) & 1u;
-        if constexpr (CG != 0)
-          if (!masked) cg_dot[f < 2 ? 0 : 1] += cvt<double>(X[f * NNODE + rs]) * cvt<double>(acc[f]);
-        if (ce.on && !low && !high) {
-          // node of this tile only: finish the smoothing step here
-          const Store y = masked ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
-          const Store dn = ch_c1 * ce.d[gi] + ch_c2[f < 2 ? 0 : 1] * (ce.dinv[gi] * (ce.f[gi] - y));
+        for (int f = 0; f < NF; ++f)
+          if (!((m >> f) & 1u)) cg_dot[f < 2 ? 0 : 1] += cvt<double>(X[f * NNODE + rs]) * cvt<double>(acc[f]);
+      }
+      if (ce.on && !low && !high) {
+        // node of this tile only: finish the smoothing step here (all loads first, as above)
+        Store cD[NF], cI[NF], cF[NF], cX[NF], cY[NF], cA[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const int gi = f * nn + node;
+          cD[f] = ce.d[gi];
+          cI[f] = ce.dinv[gi];
+          cF[f] = ce.f[gi];
+          cX[f] = ce.x[gi];
+          cY[f] = ((m >> f) & 1u) ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
+          cA[f] = ce.acc ? ce.acc[gi] : Store(0);
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const int gi = f * nn + node;
+          const Store dn = ch_c1 * cD[f] + ch_c2[f < 2 ? 0 : 1] * (cI[f] * (cF[f] - cY[f]));
           d_out[gi] = dn;
-          if (ce.acc) ce.acc[gi] += ce.x[gi] + dn;
-          else x_out[gi] = ce.x[gi] + dn;
-        } else if (masked) {
-          if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
-        } else if (low || high) {
-          atomicAdd(dst + gi, cvt<Store>(acc[f]));
-        } else {
-          dst[gi] = cvt<Store>(acc[f]);
+          if (ce.acc) ce.acc[gi] = cA[f] + (cX[f] + dn);
+          else x_out[gi] = cX[f] + dn;
+        }
+      } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const int gi = f * nn + node;
+          if ((m >> f) & 1u) {
+            if (!low) dst[gi] = oa.outmask == OUT_IDENTITY ? src[gi] : Store(0);
+          } else if (low || high) {
+            atomicAdd(dst + gi, cvt<Store>(acc[f]));
+          } else {
+            dst[gi] = cvt<Store>(acc[f]);
+          }
         }
       }
     }
