@@ -4,13 +4,12 @@
 
 namespace pff {
 
-template <int P, int SPLIT, int RC, int CG>
-static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
-                             const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
-                             const ChebEpi<float>& ce, const MatConst32& mc, const CgEpi<float>& cg) {
-  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC, CG>();
+// CTAs of one kernel instantiation resident on the device at once (occupancy times SMs, queried once).
+template <int P, int SPLIT, int RC, int CG, int ES>
+static cudaError_t jac2_slots(long long* slots) {
+  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC, CG, ES>();
   static int grid_per_sm = 0;
-  auto kern = k_jac2_staged<P, float, float, SPLIT, RC, CG>;
+  auto kern = k_jac2_staged<P, float, float, SPLIT, RC, CG, ES>;
   if (!grid_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -24,12 +23,39 @@ static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  long long grid = (long long)sms * grid_per_sm;
+  *slots = (long long)sms * grid_per_sm;
+  return cudaSuccess;
+}
+
+template <int P, int SPLIT, int RC, int CG, int ES = 0>
+static cudaError_t run_jac2(const float* x, float* y, const unsigned char* flags, const Geom& g, const Tab<float>& tb,
+                             const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
+                             const ChebEpi<float>& ce, const MatConst32& mc, const CgEpi<float>& cg) {
+  constexpr size_t smem = jac2_staged_smem<P, float, float, SPLIT, RC, CG, ES>();
+  long long grid = 0;
+  cudaError_t e = jac2_slots<P, SPLIT, RC, CG, ES>(&grid);
+  if (e != cudaSuccess) return e;
   if (grid > g.ntiles) grid = g.ntiles;
   const OpArgs oa = op_args(inmask, outmask, grid, g.ntile[0]);
   const dim3 blk(Tile2<P>::QPX, Tile2<P>::TY);
-  if (grid > 0) return launch_k(kern, dim3((unsigned)grid), blk, smem, s, x, y, flags, g, tb, qp, mode, oa, ce, mc, cg);
+  if (grid > 0)
+    return launch_k(k_jac2_staged<P, float, float, SPLIT, RC, CG, ES>, dim3((unsigned)grid), blk, smem, s, x, y, flags,
+                    g, tb, qp, mode, oa, ce, mc, cg);
   return cudaSuccess;
+}
+
+// A Chebyshev step (stored tangent) on a level whose tiles fit one wave of the staged-epilogue kernel: that
+// kernel (its copies also stage the step's operands) when they do, else the plain one.
+template <int P, int SPLIT>
+static cudaError_t run_cheb_step(const float* x, float* y, const unsigned char* flags, const Geom& g,
+                                 const Tab<float>& tb, const float* qp, int mode, int inmask, int outmask, cudaStream_t s,
+                                 const ChebEpi<float>& ce, const CgEpi<float>& cg) {
+  long long slots = 0;
+  cudaError_t e = jac2_slots<P, SPLIT, 0, 0, 1>(&slots);
+  if (e != cudaSuccess) return e;
+  if (g.ntiles <= slots)
+    return run_jac2<P, SPLIT, 0, 0, 1>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, MatConst32{}, cg);
+  return run_jac2<P, SPLIT, 0, 0, 0>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, ce, MatConst32{}, cg);
 }
 
 cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, const unsigned char* flags, const Geom& g,
@@ -49,6 +75,7 @@ cudaError_t launch_jac_d2(int dim, int p, int split, const float* x, float* y, c
     if (rc && cgo) return run_jac2<PP, SS, 1, 1>(x, y, flags, g, tb, rc->state, mode, inmask, outmask, s, e, rc->mc, cgr); \
     if (rc) return run_jac2<PP, SS, 1, 0>(x, y, flags, g, tb, rc->state, mode, inmask, outmask, s, e, rc->mc, cgr);        \
     if (cgo) return run_jac2<PP, SS, 0, 1>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, MatConst32{}, cgr);        \
+    if (e.on) return run_cheb_step<PP, SS>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, cgr);                     \
     return run_jac2<PP, SS, 0, 0>(x, y, flags, g, tb, qp, mode, inmask, outmask, s, e, MatConst32{}, cgr);                 \
   }
   PFF_CASE(1, 0) PFF_CASE(2, 0) PFF_CASE(3, 0) PFF_CASE(4, 0)

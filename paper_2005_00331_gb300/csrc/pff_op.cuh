@@ -628,8 +628,11 @@ constexpr int jac2_min_blocks() {
 // RC = 1 (FP32 only): the pointwise Jacobian is recomputed from the nodal state (u_x, u_y, phi, phi~;
 // qpg then points to those 4 fields of n_nodes floats each) by pw_jac_rc2 instead of read from stored
 // per-point data: the tile stages 4 state values per node instead of NV values per Gauss point.
-template <int P, typename Real, typename Store, int SPLIT, int RC, int CG>
-__global__ void __launch_bounds__(Tile2<P>::NT, jac2_min_blocks<P, Real, RC, CG>())
+// ES = 1 (for grids with at most one tile per CTA, where nothing hides a global round trip): the tile's
+// copies also stage the Chebyshev step's operands d, D^{-1}, f, x of the patch into shared memory, which the
+// store phase then reads instead of global memory.
+template <int P, typename Real, typename Store, int SPLIT, int RC, int CG, int ES = 0>
+__global__ void __launch_bounds__(Tile2<P>::NT, ES ? 1 : jac2_min_blocks<P, Real, RC, CG>())
 k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __restrict__ flags,
               Geom g, Tab<Real> tb, const Real* __restrict__ qpg, int mode, OpArgs oa, ChebEpi<Store> ce,
               MatConst32 mc, CgEpi<Store> cg) {
@@ -650,7 +653,9 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
   Real* QPs = reinterpret_cast<Real*>(smem_raw);                  // [NS][NV][QPT]
   Store* Xs = reinterpret_cast<Store*>(QPs + NS * NV * QPT);      // [NS][NF][NPY][NPX] raw copies
   Store* Ss = Xs + NS * XS;                                       // [NS][NSF][NPY][NPX] state (RC)
-  Real* Xc = reinterpret_cast<Real*>(Ss + NS * NSF * NNODE);
+  constexpr int NES = ES ? 4 : 0;                                 // staged epilogue arrays
+  Store* Es = Ss + NS * NSF * NNODE;                              // [NS][NES][NF][NPY][NPX] d, dinv, f, x
+  Real* Xc = reinterpret_cast<Real*>(Es + NS * NES * XS);
   Real* X = XIN ? reinterpret_cast<Real*>(Xs) : Xc;               // [NF][NPY][NPX] masked, compute type
   Real* UB = XIN ? Xc : Xc + XS;                                  // [NF][TY][n][QPX]
   Real* UD = UB + NF * TY * n * QPX;
@@ -711,6 +716,17 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
       Store* dp = xs + rs;
 #pragma unroll
       for (int f = 0; f < NF; ++f) cp_async_bytes(dp + f * NNODE, sp + (ok ? f * nn : 0), ok, (int)sizeof(Store));
+      if constexpr (ES != 0) {
+        if (ce.on) {
+          const Store* ea[4] = {ce.d, ce.dinv, ce.f, ce.x};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int f = 0; f < NF; ++f)
+              cp_async_bytes(Es + ((st * NES + a) * NF + f) * NNODE + rs, ea[a] + (ok ? f * nn + node : 0), ok,
+                             (int)sizeof(Store));
+        }
+      }
       if constexpr (RC != 0) {
         const Store* stp = reinterpret_cast<const Store*>(qpg) + (ok ? node : 0);
         Store* sdp = Ss + st * NSF * NNODE + rs;
@@ -945,7 +961,7 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
         UD[((f * TY + ty) * n + l) * QPX + tx] = ud[f][l];
       }
     __syncthreads();
-    if constexpr (NS == 1) {
+    if constexpr (NS == 1 && ES == 0) {
       // the staging buffers are free: start the next tile's copies under the store phase
       const int nxt = tile + gridDim.x;
       int nx = tix, ny = tiy;
@@ -1041,10 +1057,18 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           const int gi = f * nn + node;
-          cD[f] = ce.d[gi];
-          cI[f] = ce.dinv[gi];
-          cF[f] = ce.f[gi];
-          cX[f] = ce.x[gi];
+          if constexpr (ES != 0) {  // staged with the tile's copies
+            const Store* e = Es + st * NES * XS + f * NNODE + rs;
+            cD[f] = e[0];
+            cI[f] = e[XS];
+            cF[f] = e[2 * XS];
+            cX[f] = e[3 * XS];
+          } else {
+            cD[f] = ce.d[gi];
+            cI[f] = ce.dinv[gi];
+            cF[f] = ce.f[gi];
+            cX[f] = ce.x[gi];
+          }
           cY[f] = ((m >> f) & 1u) ? (oa.outmask == OUT_IDENTITY ? src[gi] : Store(0)) : cvt<Store>(acc[f]);
           cA[f] = ce.acc ? ce.acc[gi] : Store(0);
         }
@@ -1069,6 +1093,15 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
           }
         }
       }
+    }
+    if constexpr (NS == 1 && ES != 0) {
+      // the next tile's copies, once the store phase has read the staged operands
+      __syncthreads();
+      const int nxt = tile + gridDim.x;
+      int nx = tix, ny = tiy;
+      next_tile(nx, ny);
+      if (nxt < ntiles) prefetch(nxt, nx, ny, 0);
+      cp_async_commit();
     }
   }
   cp_async_wait<0>();
@@ -1111,14 +1144,15 @@ __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, Ch
   cheb_seam_node<Store>(g, tpx, tpy, y, ce, t, Store(ce.c1), c2);
 }
 
-template <int P, typename Real, typename Store, int SPLIT, int RC = 0, int CG = 0>
+template <int P, typename Real, typename Store, int SPLIT, int RC = 0, int CG = 0, int ES = 0>
 constexpr size_t jac2_staged_smem() {
   using T = Tile2<P>;
   constexpr int NS = Stage2<P, Real>::NSTAGE;
   constexpr int XS = 3 * T::NPY * T::NPX;
-  constexpr int NV = RC ? 0 : qp_nv(2, SPLIT), NSF = RC ? 4 : 0;
+  constexpr int NV = RC ? 0 : qp_nv(2, SPLIT), NSF = RC ? 4 : 0, NES = ES ? 4 : 0;
   constexpr int XC = jac2_x_inplace<P, Real, Store, CG>() ? 0 : XS;
-  return sizeof(Real) * (size_t)NS * NV * T::QPX * T::QPY + sizeof(Store) * (size_t)NS * (XS + NSF * T::NPY * T::NPX) +
+  return sizeof(Real) * (size_t)NS * NV * T::QPX * T::QPY +
+         sizeof(Store) * (size_t)NS * (XS + NSF * T::NPY * T::NPX + NES * XS) +
          sizeof(Real) * (size_t)(XC + 2 * 3 * T::TY * T::n * T::QPX + 2 * T::n * T::n);
 }
 
