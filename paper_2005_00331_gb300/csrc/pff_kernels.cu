@@ -291,6 +291,112 @@ __global__ void k_restrict(const Real* __restrict__ xf, Real* __restrict__ yc, c
   }
 }
 
+// 2D restriction by tiles of coarse nodes (RCX x RCY coarse cells' nodes per CTA): the fine window that
+// the tile's coarse functions touch is staged in shared memory (masked; a cut slit's copy is added to its
+// grid node, which carries the same coarse weights), then contracted along x and along y. The restriction
+// is the transpose of the tensor-product prolongation, so each coarse value takes 2 (4p+1) products
+// instead of (4p+1)^2 gathers, and the CTA's loads are coalesced and independent of one another.
+template <int P>
+struct RTile2 {
+  static constexpr int CXC = P == 1 ? 16 : P == 2 ? 8 : 4, CYC = P == 1 ? 8 : P == 2 ? 4 : P == 3 ? 3 : 2;
+  static constexpr int CX = CXC * P, CY = CYC * P;                        // coarse nodes per CTA
+  static constexpr int FX = 2 * CX + 4 * P - 1, FY = 2 * CY + 4 * P - 1;  // fine window
+};
+constexpr int RT_THREADS = 128;
+
+template <int P, typename Real>
+__global__ void __launch_bounds__(RT_THREADS)
+k_restrict2(const Real* __restrict__ xf, Real* __restrict__ yc, const unsigned char* __restrict__ flf,
+            const unsigned char* __restrict__ flc, Geom gf, Geom gc, XferTab xt, int mask_fine, ChebStart<Real> cs) {
+  using T = RTile2<P>;
+  constexpr int NW = 4 * P + 1, CX = T::CX, CY = T::CY, FX = T::FX, FY = T::FY;
+  __shared__ Real W[P][NW];
+  __shared__ Real F[3][FY][FX];   // masked fine window
+  __shared__ Real Tx[3][FY][CX];  // the window contracted along x
+  for (int i = threadIdx.x; i < P * NW; i += blockDim.x) {
+    const int k = i / NW, o = i % NW - 2 * P;
+    W[k][i % NW] = o >= 0 ? Real(xt.E[o][k]) : (k == 0 ? Real(xt.E[o + 2 * P][P]) : Real(0));
+  }
+  pdl_wait();
+  const int ntx = (gc.n1 + CX - 1) / CX;
+  const int J0 = int(blockIdx.x % (unsigned)ntx) * CX, I0 = int(blockIdx.x / (unsigned)ntx) * CY;
+  const int fx0 = 2 * J0 - 2 * P, fy0 = 2 * I0 - 2 * P;  // window origin on the fine grid
+  for (int i = threadIdx.x; i < FX * FY; i += blockDim.x) {
+    const int wy = i / FX, wx = i - wy * FX;
+    const int ix = fx0 + wx, iy = fy0 + wy;
+    Real v[3] = {Real(0), Real(0), Real(0)};
+    if (ix >= 0 && iy >= 0 && ix < gf.n1 && iy < gf.n1) {
+      const long long fn = ix + (long long)gf.n1 * iy;
+      const unsigned char ff = mask_fine ? flf[fn] : 0;
+      Real x3[3];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) x3[f] = xf[f * gf.nn + fn];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) v[f] = ((ff >> f) & 1u) ? Real(0) : x3[f];
+      if (gf.cut && iy == gf.cut_row && ix < gf.cut_x) {
+        const long long fcp = cut_copy(gf, ix, 0);
+        const unsigned char fcm = mask_fine ? flf[fcp] : 0;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+          if (!((fcm >> f) & 1u)) v[f] += xf[f * gf.nn + fcp];
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) F[f][wy][wx] = v[f];
+  }
+  __syncthreads();
+  // coarse column jc (node J0 + jc, local basis k = jc mod P since J0 is a multiple of P) sees the fine
+  // window columns 2P (jc / P) + o, o in [0, 4P]
+  for (int i = threadIdx.x; i < FY * CX; i += blockDim.x) {
+    const int wy = i / CX, jc = i - wy * CX;
+    const int k = jc % P, wb = 2 * P * (jc / P);
+    Real a[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int o = 0; o < NW; ++o) {
+      const Real w = W[k][o];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) a[f] += w * F[f][wy][wb + o];
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) Tx[f][wy][jc] = a[f];
+  }
+  __syncthreads();
+  Real a0 = Real(0), a1 = Real(0);
+  if (cs.on) {
+    a0 = Real(cs.c0s) * cs.inv_lam[0];
+    a1 = Real(cs.c0s) * cs.inv_lam[1];
+  }
+  for (int i = threadIdx.x; i < CY * CX; i += blockDim.x) {
+    const int ic = i / CX, jc = i - ic * CX;
+    const int J = J0 + jc, I = I0 + ic;
+    if (J >= gc.n1 || I >= gc.n1) continue;
+    const int k = ic % P, wb = 2 * P * (ic / P);
+    Real acc[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+    for (int o = 0; o < NW; ++o) {
+      const Real w = W[k][o];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) acc[f] += w * Tx[f][wb + o][jc];
+    }
+    const long long nd = J + (long long)gc.n1 * I;
+    const unsigned char fc = flc[nd];
+    Real di[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) di[f] = cs.on ? cs.dinv[f * gc.nn + nd] : Real(0);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const long long gi = f * gc.nn + nd;
+      const Real v = ((fc >> f) & 1u) ? Real(0) : acc[f];
+      yc[gi] = v;
+      if (cs.on) {
+        const Real de = (f < 2 ? a0 : a1) * (di[f] * v);
+        cs.d[gi] = de;
+        cs.x[gi] = de;
+      }
+    }
+  }
+}
+
 template <typename Real>
 cudaError_t launch_prolong(int dim, int p, const Real* xc, Real* yf, const unsigned char* flags_f, const Geom& gc,
                            const Geom& gf, const XferTab& xt, bool accumulate, cudaStream_t s) {
@@ -313,6 +419,17 @@ cudaError_t launch_restrict(int dim, int p, const Real* xf, Real* yc, const unsi
   ChebStart<Real> off{};
   off.on = 0;
   const ChebStart<Real>& st = cs ? *cs : off;
+  if (dim == 2 && !gc.cut) {  // coarse levels carry no slit copies
+#define PFF_CASE2(PP)                                                                                    \
+  if (p == PP) {                                                                                         \
+    using T = RTile2<PP>;                                                                                \
+    const unsigned g2 = (unsigned)(((gc.n1 + T::CX - 1) / T::CX) * ((gc.n1 + T::CY - 1) / T::CY));       \
+    return launch_k(k_restrict2<PP, Real>, dim3(g2), dim3(RT_THREADS), 0, s, xf, yc, flags_f, flags_c, gf, \
+                    gc, xt, mask_fine ? 1 : 0, st);                                                      \
+  }
+    PFF_CASE2(1) PFF_CASE2(2) PFF_CASE2(3) PFF_CASE2(4)
+#undef PFF_CASE2
+  }
 #define PFF_CASE(DD, PP)                                                                                 \
   if (dim == DD && p == PP)                                                                              \
     return launch_k(k_restrict<DD, PP, Real>, dim3(gr), dim3(128), 0, s, xf, yc, flags_f, flags_c, gf, gc, \
