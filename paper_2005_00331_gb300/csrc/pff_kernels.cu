@@ -153,19 +153,21 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
   for (int i = threadIdx.x; i < NO * NK; i += blockDim.x) E[i / NK][i % NK] = Real(xt.E[i / NK][i % NK]);
   pdl_wait();
   __syncthreads();
-  const long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // 32-bit index arithmetic (node counts fit in 32 bits, checked at setup)
+  const int nd = int(blockIdx.x * blockDim.x + threadIdx.x);
   if (nd >= gf.nn) return;
-  long long rem = nd;
+  const unsigned n1 = (unsigned)gf.n1;
+  unsigned rem = (unsigned)nd;
   if (nd >= gf.ngrid) {  // copy of a cut slit node: the coarse function's value at its grid point
-    const long long k = nd - gf.ngrid;
-    const long long x = k % gf.cut_x, y = k / gf.cut_x;
-    rem = x + (long long)gf.n1 * (DIM == 2 ? gf.cut_row : y + (long long)gf.n1 * gf.cut_row);
+    const unsigned k = unsigned(nd - gf.ngrid);
+    const unsigned x = k % (unsigned)gf.cut_x, y = k / (unsigned)gf.cut_x;
+    rem = x + n1 * (DIM == 2 ? (unsigned)gf.cut_row : y + n1 * (unsigned)gf.cut_row);
   }
   int C[3] = {0, 0, 0}, o[3] = {0, 0, 0};
 #pragma unroll
   for (int t = 0; t < DIM; ++t) {
-    const int i = int(rem % gf.n1);
-    rem /= gf.n1;
+    const int i = int(rem % n1);
+    rem /= n1;
     int c = i / (2 * P);
     if (c > gc.N - 1) c = gc.N - 1;
     C[t] = c;

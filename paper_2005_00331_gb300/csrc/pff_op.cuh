@@ -561,16 +561,18 @@ constexpr bool jac2_x_inplace() {
 // Seam index t enumerates the vertical seam lines, then the horizontal ones (crossings once).
 template <typename Store>
 __device__ __forceinline__ void cheb_seam_node(const Geom& g, int tpx, int tpy, Store* y, const ChebEpi<Store>& ce,
-                                               long long t, Store c1, const Store c2[2]) {
-  const long long nv = (long long)(g.ntile[0] - 1) * g.n1;
+                                               int t, Store c1, const Store c2[2]) {
+  // 32-bit index arithmetic (node counts fit in 32 bits, checked at setup)
+  const unsigned n1 = (unsigned)g.n1;
+  const int nv = (g.ntile[0] - 1) * g.n1;
   int gx, gy;
   if (t < nv) {
-    gx = int(t / g.n1 + 1) * tpx;
-    gy = int(t % g.n1);
+    gx = int((unsigned)t / n1 + 1) * tpx;
+    gy = int((unsigned)t % n1);
   } else {
-    const long long u = t - nv;
-    gy = int(u / g.n1 + 1) * tpy;
-    gx = int(u % g.n1);
+    const unsigned u = (unsigned)(t - nv);
+    gy = int(u / n1 + 1) * tpy;
+    gx = int(u % n1);
     if (gx % tpx == 0 && gx > 0 && gx < g.n1 - 1) return;  // already done on a vertical seam line
     // a cut slit's nodes are shared along x only: the tiles finished them, except on vertical seams
     if (g.cut && gy == g.cut_row && gx < g.cut_x) return;
@@ -1137,8 +1139,8 @@ k_jac2_staged(const Store* src, Store* __restrict__ dst, const unsigned char* __
 template <typename Store>
 __global__ void k_cheb_seam2(Geom g, int tpx, int tpy, Store* __restrict__ y, ChebEpi<Store> ce) {
   pdl_wait();
-  const long long nseam = (long long)(g.ntile[0] - 1 + g.ntile[1] - 1) * g.n1;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nseam = (g.ntile[0] - 1 + g.ntile[1] - 1) * g.n1;
+  const int t = int(blockIdx.x * blockDim.x + threadIdx.x);
   if (t >= nseam) return;
   const Store c2[2] = {Store(ce.c2s) * ce.inv_lam[0], Store(ce.c2s) * ce.inv_lam[1]};
   cheb_seam_node<Store>(g, tpx, tpy, y, ce, t, Store(ce.c1), c2);
