@@ -1019,7 +1019,32 @@ __global__ void __launch_bounds__(BLK) k_cg_update(long long n, long long nu, Re
                                                    double* __restrict__ bh, int it, int iters) {
   const Real a0 = Real(scal[4]), a1 = Real(scal[5]);
   double s0 = 0.0, s1 = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // four elements per iteration, all loads first (the stores below would otherwise hold back the next
+  // element's loads); the products are added in element order, as one element per iteration would
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    Real rv[4], av[4], dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rv[u] = r[e + u * stride];
+      av[u] = Ap[e + u * stride];
+      dv[u] = dinv[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = e + u * stride;
+      const Real rr = rv[u] - (i < nu ? a0 : a1) * av[u];
+      r[i] = rr;
+      const Real zz = dv[u] * rr;
+      z[i] = zz;
+      Ap[i] = Real(0);
+      const double q = (double)rr * (double)zz;
+      if (i < nu) s0 += q;
+      else s1 += q;
+    }
+  }
+  for (; e < n; e += stride) {
     const Real al = e < nu ? a0 : a1;
     const Real rr = r[e] - al * Ap[e];
     r[e] = rr;
