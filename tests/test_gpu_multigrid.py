@@ -199,6 +199,23 @@ def test_fgmres_solve(prec, fp64_mode, dim, p, N, split):
     assert rel(x, xd) <= 1e-3
 
 
+def test_fgmres_beyond_sixteen_basis_vectors():
+    """FGMRES whose Krylov basis grows past 16 vectors in one cycle. There, CGS2 leaves its fused
+    passes (one instantiation per basis size up to 16) for the separate multi-dot and update kernels.
+    A one-step smoother and a tight tolerance force the iterations. The solution must match the
+    direct solve, and the true residual must meet the tolerance."""
+    pr = Problem(2, 2, 8, split=1, seed=7, active_frac=0.1)
+    ctx = pr.context(mg_precision=64, cheb_degree=1, lin_rtol=1e-11, gmres_restart=30)
+    Gm = fe.masked(pr.G(), pr.mask)
+    b = np.where(pr.mask, 0.0, np.random.default_rng(13).normal(size=pr.mesh.n_dofs))
+    x, its, relres = ctx.solve_linear(cuda(b))
+    x = x.cpu().numpy()
+    assert its > 16 and relres <= 1e-11
+    assert np.linalg.norm(Gm @ x - b) <= 1e-8 * np.linalg.norm(b)
+    xd = spla.spsolve(Gm.tocsc(), b)
+    assert rel(x, xd) <= 1e-6
+
+
 @pytest.mark.parametrize("split", [0, 1])
 def test_newton_step_c1(split):
     """The tension test of the paper at 32 x 32 Q1 (3267 DoFs): one primal-dual active-set step with
