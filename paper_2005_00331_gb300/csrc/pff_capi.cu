@@ -170,6 +170,8 @@ struct pff_ctx {
   double* scratch = nullptr;   // 4 fine-sized FP64 vectors (CG-Lanczos, residual checks)
   double* partial = nullptr;   // reduction partials
   unsigned* kcnt = nullptr;    // CTA counter of the fused CGS2 passes (zero between launches)
+  cudaEvent_t hcol = nullptr;  // recorded after the copy of an FGMRES Hessenberg column to the host
+  const double* w32_of = nullptr;  // the FP64 vector whose FP32 copy the finest w32[0] holds, if any
   double* dres = nullptr;      // small device results
   double* hist = nullptr;      // CG alpha/beta histories
   int* cnt = nullptr;
@@ -976,7 +978,9 @@ int precondition(pff_ctx* c, const double* r, double* z) {
   LevelData& L = c->lv[0];
   if (c->prm.mg_precision == 32) {
     CR(ensure_work<float>(c, 0));
-    CK(launch_cast<double, float>(L.nd, r, L.w32[0], c->s));
+    // FGMRES writes the FP32 copy of its next basis vector when it normalises it
+    if (c->w32_of != r) CK(launch_cast<double, float>(L.nd, r, L.w32[0], c->s));
+    c->w32_of = nullptr;
     CR(vcycle_exec<float>(c));
     CK(launch_cast<float, double>(L.nd, L.w32[1], z, c->s));
   } else {
@@ -1001,6 +1005,7 @@ int norm2_host(pff_ctx* c, const double* x, long long n, double* out) {
 // Right-preconditioned flexible GMRES(m), x0 = 0, CGS2 orthogonalisation in FP64.
 int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_out) {
   CR(mg_setup(c));
+  c->w32_of = nullptr;
   LevelData& L = c->lv[0];
   const long long n = L.nd;
   const int m = c->prm.gmres_restart;
@@ -1049,7 +1054,18 @@ int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_o
       CK(launch_cgs2(n, j + 1, c->V, wv, c->partial, c->hdev, c->hdev + (m + 1), c->hdev + 2 * (m + 1), c->kcnt,
                      c->s));
       CK(cudaMemcpyAsync(c->pinned, c->hdev, sizeof(double) * (2 * (m + 1) + 2), cudaMemcpyDeviceToHost, c->s));
-      CK(cudaStreamSynchronize(c->s));
+      CK(cudaEventRecord(c->hcol, c->s));
+      // V_{j+1} = w / |w| on the device (1/|w| from the CGS2 pass, 0 for w = 0), with the FP32 copy the
+      // next V-cycle starts from, while the host waits for the column and applies the rotations (after
+      // the last iteration this is one small kernel for nothing)
+      float* w32 = nullptr;
+      if (c->prm.mg_precision == 32) {
+        CR(ensure_work<float>(c, 0));
+        w32 = L.w32[0];
+      }
+      CK(launch_normalize(n, wv, c->hdev + 2 * (m + 1) + 2, wv, w32, c->s));
+      c->w32_of = w32 ? wv : nullptr;
+      CK(cudaEventSynchronize(c->hcol));
       CR(prof_collect(c));
       const double* hh = c->pinned;
       for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i] + hh[(m + 1) + i];
@@ -1057,7 +1073,6 @@ int fgmres(pff_ctx* c, const double* b, double* x, int* iters_out, double* rel_o
       if (!std::isfinite(nw2)) return PFF_ERR_NAN;
       const double nw = std::sqrt(nw2);
       H[(j + 1) * m + j] = nw;
-      if (nw > 0.0) CK(launch_normalize(n, wv, c->hdev + 2 * (m + 1) + 2, wv, c->s));
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
         H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
@@ -1182,6 +1197,7 @@ void pff_destroy(pff_ctx* c) {
   for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->hcol) cudaEventDestroy(c->hcol);
   for (auto& L : c->lv) {
     if (L.aux) cudaStreamDestroy(L.aux);
     if (L.join) cudaEventDestroy(L.join);
@@ -1263,6 +1279,7 @@ static int setup_impl(pff_ctx* c) {
                                                 (long long)CGS_KMAX * CGS_GRID_MAX)));
   CR(dalloc(c, &c->kcnt, 1, TAG_KRYLOV));
   CK(cudaMemsetAsync(c->kcnt, 0, sizeof(unsigned), c->s));
+  CK(cudaEventCreateWithFlags(&c->hcol, cudaEventDisableTiming));
   CR(dalloc(c, &c->dres, 32));
   CR(dalloc(c, &c->hist, 4 * P.eig_iters));
   CR(dalloc(c, &c->cnt, 2));

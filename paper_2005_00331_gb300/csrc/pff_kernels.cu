@@ -182,10 +182,12 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
   }
   const unsigned char fl = flf[nd];
   const long long cbase = (long long)C[0] * P + (long long)gc.n1 * (C[1] * P + (DIM == 3 ? (long long)gc.n1 * C[2] * P : 0));
+  // the coarse values are loaded whatever the fine node's mask (applied below), so that the loads do not
+  // wait for the flag byte
 #pragma unroll
   for (int f = 0; f <= DIM; ++f) {
     Real v = Real(0);
-    if (!((fl >> f) & 1u)) {
+    {
       const Real* xb = xc + f * gc.nn + cbase;
 #pragma unroll
       for (int kz = 0; kz < (DIM == 3 ? NK : 1); ++kz)
@@ -198,6 +200,7 @@ __global__ void k_prolong(const Real* __restrict__ xc, Real* __restrict__ yf, co
           v += wz[kz] * wy[ky] * sx;
         }
     }
+    if ((fl >> f) & 1u) v = Real(0);
     Real* y = yf + f * gf.nn + nd;
     *y = accumulate ? *y + v : v;
   }
@@ -728,15 +731,19 @@ cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y,
 }
 
 __global__ void k_normalize(long long n, const double* __restrict__ x, const double* __restrict__ inv,
-                            double* __restrict__ y) {
+                            double* __restrict__ y, float* __restrict__ y32) {
   const double a = inv[0];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    y[e] = x[e] * a;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = x[e] * a;
+    y[e] = v;
+    if (y32) y32[e] = (float)v;
+  }
 }
-cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, cudaStream_t s) {
+cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, float* y32,
+                             cudaStream_t s) {
   long long g = (n + BLK - 1) / BLK;
   if (g > 152 * 16) g = 152 * 16;
-  count_launch(); k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, inv, y);
+  count_launch(); k_normalize<<<(unsigned)g, BLK, 0, s>>>(n, x, inv, y, y32);
   return cudaGetLastError();
 }
 

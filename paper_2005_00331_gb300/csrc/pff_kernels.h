@@ -85,8 +85,9 @@ cudaError_t launch_mdot(long long n, int k, const double* V, const double* w, do
 cudaError_t launch_maxpy(long long n, int k, const double* V, const double* h, double* w, cudaStream_t s);
 // x += sum_i Z_i y[i]
 cudaError_t launch_zupdate(long long n, int k, const double* Z, const double* y, double* x, cudaStream_t s);
-// y = x * inv[0]
-cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, cudaStream_t s);
+// y = x * inv[0]; with y32 != NULL also y32 = (float) y
+cudaError_t launch_normalize(long long n, const double* x, const double* inv, double* y, float* y32,
+                             cudaStream_t s);
 // CGS2 of w against V_0 .. V_{k-1}: h1 = V^T w; w -= V h1; h2 = V^T w; w -= V h2; nrm = (<w, w>, 0, 1 / |w|).
 // Three fused passes for k <= CGS_KMAX, else the separate passes; part >= max(CGS_KMAX, k) * CGS_GRID
 // doubles; cnt: one zero-initialised counter (left zero).
